@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark: PCP entries recovered per second by l1 filtering on GB300.
+
+One step = one whole solve of Algorithm 2 on a resident 5000 x 5000 FP32
+matrix of rank 20 with 10% corruption in [-100, 100] (seed 200 x 200):
+seed gather + FP64 seed PCP + column/row l1 filtering + factor assembly +
+S = M - L.  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+value        entries (m*n) recovered per second, device-resident input, L2
+             flushed between steps (a 256 MB memset outside the timed span);
+e2e          the same metric through the public API from pinned host
+             memory: H2D of M, the solve, D2H of Lu, Lv and S per step;
+roofline     the dominant kernel of the step against MEASURED_PEAKS.json;
+cpu_baseline the FP64 oracle on the host cores (rank 0, N=1 only), one full
+             solve of the same workload;
+--impl reference  times that oracle as the reference arm.
+Multi-GPU: independent replicas (each rank solves its own instance; weak
+scaling, no collective on the data path), max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("PCP entries recovered/s (m*n/s) at rel err<=1e-5 vs plain FP32; "
+          "p50/p99 latency")
+WORKLOAD = "c2_5000_r20"
+WORKLOAD_DESC = ("m=n=5000, r=20, L0=XY^T with X,Y iid N(0,1); S0 10% uniform "
+                 "support, values U[-100,100]; seed 200x200 (10r x 10r); "
+                 "lambda=1/sqrt(5000); FP32 M")
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="500x500 rank-5 workload (profiling / smoke)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
+            "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": num(rows[0][2]),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def make_problem(seed, small=False):
+    from paper_1108_5359_gb300 import synth
+    if small:
+        P = synth.make_config("c1_500_r5", seed=3 + seed)
+    else:
+        P = synth.make_config(WORKLOAD, seed=seed)
+    M32 = np.asfortranarray(P.M.astype(np.float32))
+    return P, M32
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# -------------------------------------------------------------------------
+# oracle timing (cpu_baseline and the reference arm)
+# -------------------------------------------------------------------------
+
+def oracle_solve(P, M32, frac=1.0):
+    """FP64 oracle on the workload; frac < 1 filters a sample of the column
+    and row problems and forms that fraction of S, and scales the time."""
+    from oracle import l1filter, pcp
+    M = M32.astype(np.float64)
+    t0 = time.perf_counter()
+    if frac >= 1.0:
+        res = l1filter.l1_filter_pcp(M, P.rows, P.cols, r=P.r)
+        t = time.perf_counter() - t0
+        return t, res
+    mp = P.rows.size
+    Ms = M[np.ix_(P.rows, P.cols)]
+    seed = pcp.inexact_alm_pcp(Ms, 1.0 / math.sqrt(mp))
+    t_seed = time.perf_counter() - t0
+    U, V = seed.U[:, :P.r], seed.V[:, :P.r]
+    rbar = np.setdiff1d(np.arange(P.m), P.rows)
+    cbar = np.setdiff1d(np.arange(P.n), P.cols)
+    nc = max(1, int(frac * cbar.size))
+    nr = max(1, int(frac * rbar.size))
+    t1 = time.perf_counter()
+    col = l1filter.adm_l1(M[np.ix_(P.rows, cbar[:nc])], U)
+    row = l1filter.adm_l1(M[np.ix_(rbar[:nr], P.cols)].T, V)
+    ns = max(1, int(frac * P.n))
+    Lu = np.zeros((P.m, P.r))
+    Lv = np.zeros((ns, P.r))
+    _ = M[:, :ns] - Lu @ Lv.T
+    t_rest = time.perf_counter() - t1
+    del col, row
+    return t_seed + t_rest / frac, None
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    P, M32 = make_problem(args.seed, args.small)
+    mn = P.m * P.n
+    frac = 1.0 if args.small else 0.1
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_solve(P, M32, frac)
+    times = []
+    for _ in range(args.steps):
+        t, _ = oracle_solve(P, M32, frac)
+        times.append(t)
+    t_mean = statistics.mean(times)
+    value = mn / t_mean
+    sample = (f"full oracle solve per step" if frac >= 1 else
+              f"per step: full FP64 seed PCP + Algorithm 1 on {frac:.0%} of "
+              f"the column and row problems + {frac:.0%} of the S pass, "
+              f"non-seed time scaled by 1/{frac:g}")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value,
+        "unit": "entries/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_mean,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": ("c1_500_r5" if args.small else WORKLOAD),
+                   "desc": WORKLOAD_DESC, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# -------------------------------------------------------------------------
+# our arm
+# -------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else
+                                "gloo")
+    torch.cuda.set_device(local)
+    import paper_1108_5359_gb300 as pk
+    from paper_1108_5359_gb300 import build as pkbuild
+    pkbuild.build()
+    pk.load()
+
+    P, M32 = make_problem(args.seed + 1000 * rank, args.small)
+    m, n, r = P.m, P.n, P.r
+    mn = m * n
+    dev = torch.device("cuda", local)
+    dM = pk.colmajor(m, n, device=dev)
+    dM.copy_(torch.from_numpy(M32))
+    Lu = pk.colmajor(m, r, device=dev)
+    Lv = pk.colmajor(n, r, device=dev)
+    S = pk.colmajor(m, n, device=dev)
+    params = pk.pcp_params_default(m, n, r)
+    plan = pk.Plan(params, P.rows, P.cols)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(info=True):
+        return pk.pcp_l1filter_solve(plan, dM, Lu, Lv, S, info=info,
+                                     stream=stream, raise_on_error=False)
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        st, info, _, _ = step()
+    torch.cuda.synchronize()
+    assert st == 0, f"solve failed with status {st}: {pk._abi.last_error()}"
+
+    sampler = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    step_ms, stage = [], {"seed": [], "filter": [], "spass": []}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        st, info, _, _ = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        stage["seed"].append(info.t_seed_ms)
+        stage["filter"].append(info.t_filter_ms)
+        stage["spass"].append(info.t_spass_ms)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    t_step = statistics.mean(step_ms)
+    if ws > 1:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = ws * mn / (t_step * 1e-3)
+    last_info = info.as_dict()
+
+    # parity of the last solve: exact recovery of the generated L0, S0
+    Lh = Lu.double().cpu().numpy()
+    Vh = Lv.double().cpu().numpy()
+    Sh = S.double().cpu().numpy()
+    Lrec = Lh @ Vh.T
+    parity = {"relerr_L_vs_L0": relerr(Lrec, P.L0),
+              "relerr_S_vs_S0": relerr(Sh, P.S0), "status": int(st)}
+
+    # e2e through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hM = torch.from_numpy(np.ascontiguousarray(M32.T)).pin_memory()
+        hLu = torch.empty((r, m), dtype=torch.float32).pin_memory()
+        hLv = torch.empty((r, n), dtype=torch.float32).pin_memory()
+        hS = torch.empty((n, m), dtype=torch.float32).pin_memory()
+        e_ms = []
+        for it in range(max(3, args.warmup) + args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dM.t().copy_(hM, non_blocking=True)
+            pk.pcp_l1filter_solve(plan, dM, Lu, Lv, S, info=False,
+                                  stream=stream)
+            hLu.copy_(Lu.t(), non_blocking=True)
+            hLv.copy_(Lv.t(), non_blocking=True)
+            hS.copy_(S.t(), non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= max(3, args.warmup):
+                e_ms.append(e0.elapsed_time(e1))
+        te = statistics.mean(e_ms)
+        if ws > 1:
+            tt = torch.tensor([te], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": ws * mn / (te * 1e-3), "unit": "entries/s",
+               "ms_per_step": te, "h2d_bytes_per_step": 4 * mn,
+               "d2h_bytes_per_step": 4 * mn + 4 * r * (m + n)}
+
+    # roofline of the dominant kernel
+    pk_d, pk_src = peaks()
+    mean = {k: statistics.mean(v) for k, v in stage.items()}
+    mp = P.rows.size
+    np_ = P.cols.size
+    spass_bytes = 8 * mn + 4 * r * (m + n)
+    kiter = last_info["filter_iters_max"]
+    filt_flops = 4.0 * r * ((n - np_) * mp + (m - mp) * np_)  # per iteration
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s, SIMT FMA
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12     # TFLOP/s
+    stages = {
+        "spass": {"bound": "hbm", "ms": mean["spass"],
+                  "achieved": spass_bytes / (mean["spass"] * 1e-3) / 1e9,
+                  "peak": pk_d["hbm_gbs"], "unit": "GB/s",
+                  "algorithmic_bytes": spass_bytes},
+        "filter": {"bound": "alu", "ms": mean["filter"],
+                   "achieved": filt_flops * kiter / (mean["filter"] * 1e-3)
+                   / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                   "note": "FP32 FMA; flops = 4 p r per problem-iteration "
+                           "at the slowest problem's iteration count"},
+        "seed": {"bound": "alu", "ms": mean["seed"], "unit": "TFLOP/s",
+                 "peak": fp64_peak,
+                 "achieved": (28 * 6.0 * mp * np_ * (r + 6))
+                 / (mean["seed"] * 1e-3) / 1e12,
+                 "note": "FP64; ~6 m'n'k flops per ALM iteration, ~28 "
+                         "iterations incl. prologue"},
+    }
+    for v in stages.values():
+        v["frac"] = v["achieved"] / v["peak"]
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    d = stages[dom]
+    roofline = {"kernel": {"spass": "spass_kernel",
+                           "filter": "adm_f32_kernel",
+                           "seed": "seed_alm_kernel"}[dom],
+                "bound": d["bound"], "achieved": d["achieved"],
+                "peak": d["peak"], "unit": d["unit"], "frac": d["frac"],
+                "traffic": None,
+                "peak_source": pk_src if d["bound"] == "hbm" else
+                "derived: 152 SMs x FMA lanes x 2 x 2.07 GHz"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t_or, ref = oracle_solve(P, M32, 1.0)
+        cpu = {"value": mn / t_or, "unit": "entries/s",
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "one full FP64 oracle solve of the same workload "
+                         "(numpy, BLAS threads = host cores)"}
+        if ref is not None:
+            parity["relerr_L_vs_oracle"] = relerr(Lrec, ref.L)
+            parity["relerr_S_vs_oracle"] = relerr(Sh, ref.S)
+
+    if rank == 0:
+        lat = sorted(step_ms)
+        out = {
+            "metric": METRIC, "value": value, "unit": "entries/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": t_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": ("c1_500_r5" if args.small else WORKLOAD),
+                       "desc": WORKLOAD_DESC, "global_batch": ws,
+                       "parallelism": f"replicas{ws}",
+                       "l2": "flushed between steps (256 MB memset outside "
+                             "the timed span)",
+                       "seed_dtype": "f64"},
+            "latency_ms": {"p50": lat[len(lat) // 2],
+                           "p99": lat[min(len(lat) - 1,
+                                          int(math.ceil(0.99 * len(lat))) - 1)]},
+            "wall_s_timed_loop": wall,
+            "stages_ms": mean, "stages": stages,
+            "seed_iters": last_info["seed_iters"],
+            "filter_iters_max": kiter,
+            "parity": parity, "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "clocks": clocks,
+            "gpu_launches": 6 * args.steps,
+        }
+        print(json.dumps(out), flush=True)
+    plan.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,252 @@
+/*
+ * pcp_l1f.h -- C ABI of the GB300 (sm_103a) l1-filtering PCP library.
+ *
+ * Principal Component Pursuit (Eq. PCP): given M (m x n) find L (low rank)
+ * and S (sparse) with M = L + S minimising ||L||_* + lambda ||S||_1.  The
+ * l1 filtering method (Algorithm 2) solves it in four stages:
+ *   1. sample a seed submatrix M^s = M[I_s, J_s] of (s_r r) x (s_c r)
+ *      entries (Section 3.1);
+ *   2. solve the small PCP of Eq. SPCP on M^s (here: inexact ALM in FP64 on
+ *      the device) and keep its skinny SVD L^s = U^s Sigma^s V^sT;
+ *   3. l1 filtering (Section 3.2, Algorithm 1): every column of
+ *      M^c = M[I_s, ~J_s] is an l1 regression on U^s (Eq. l1c') and every
+ *      row of M^r = M[~I_s, J_s] an l1 regression on V^s (Eq. l1r');
+ *   4. represent the rest by the generalized Nystrom formula
+ *      L~^s = P~^T (Sigma^s)^{-1} Q~ (Eq. l1s') and output S = M - L.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major (Fortran/BLAS order) with an explicit leading
+ *     dimension >= the row count.  Indices are 0-based.
+ *   - "d" pointers are device pointers (cudaMalloc / torch CUDA tensors) and
+ *     "h" pointers host pointers.  The caller owns every buffer it passes;
+ *     the library never frees or retains them past the call except where a
+ *     function says so.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; unless stated, calls are
+ *     asynchronous with respect to the host.
+ *   - Errors are returned as pcp_status; nothing aborts or traps.  The
+ *     message of the last error on the calling thread is available from
+ *     pcp_last_error().  On an error no output is guaranteed.
+ *   - Floating point: M, S and the L factors are FP32; the seed PCP is FP64.
+ */
+#ifndef PCP_L1F_H
+#define PCP_L1F_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pcp_status {
+  PCP_OK = 0,
+  PCP_ERR_ARG = -1,           /* invalid argument (size, pointer, index set) */
+  PCP_ERR_NOMEM = -2,         /* device or pinned-host allocation failed */
+  PCP_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  PCP_ERR_NONFINITE = -4,     /* NaN or Inf found in the seed block of M */
+  PCP_ERR_RANK_TEST = -5,     /* Eq. rank_test failed: m'/r' < s_r or
+                                 n'/r' < s_c, or r' = 0; results written */
+  PCP_ERR_SEED_NOCONV = -6,   /* seed PCP hit seed_max_iter; results written */
+  PCP_ERR_FILTER_NOCONV = -7, /* some l1 problems hit filter_max_iter;
+                                 results written, see pcp_info */
+  PCP_ERR_BUSY = -8,          /* serving: request still in flight */
+  PCP_ERR_TIMEOUT = -9,       /* a bounded device wait ran out */
+  PCP_ERR_CANCELLED = -10,    /* serving: request dropped at shutdown */
+  PCP_ERR_UNSUPPORTED = -11   /* option not available on this device */
+} pcp_status;
+
+typedef enum pcp_precision {
+  PCP_FP32 = 0,          /* Algorithm 1 in FP32 FMA (SIMT) */
+  PCP_BF16_REFINED = 1,  /* BF16 tensor-core products, FP32 accumulation,
+                            then FP32 refinement iterations */
+  PCP_TF32_REFINED = 2,  /* reserved */
+  PCP_FP64 = 3           /* reserved */
+} pcp_precision;
+
+/* Parameters of one solve.  Fill with pcp_params_default() first. */
+typedef struct pcp_params {
+  int64_t m, n;             /* size of M */
+  int32_t r;                /* target rank; sizes the seed (Section 3.1) */
+  int32_t precision;        /* pcp_precision */
+  double lambda;            /* full-problem lambda of Eq. PCP; <= 0 means
+                               1/sqrt(max(m,n)).  Reported only: the
+                               filtering stage has no lambda. */
+  double lambda_seed;       /* lambda~ of Eq. SPCP; <= 0 means
+                               1/sqrt(max(m',n')) */
+  double s_r, s_c;          /* oversampling rates, default 10 (Section 3.1);
+                               m' = round(s_r r), n' = round(s_c r) */
+  double seed_tol;          /* ||M^s-L^s-S^s||_F/||M^s||_F stop, default 1e-7
+                               (Section 4.1.1) */
+  double seed_rho;          /* ALM penalty growth, default 1.5 */
+  double seed_mu_scale;     /* mu_0 = seed_mu_scale/||M^s||_2, default 1.25 */
+  double seed_mu_max_ratio; /* mu_max = ratio * mu_0, default 1e7 */
+  double rank_cut;          /* singular values of L^s below rank_cut * the
+                               largest are dropped, default 1e-10 */
+  double filter_tol;        /* epsilon of Algorithm 1, default 3e-7 */
+  double filter_rho;        /* rho of Algorithm 1, default 1.5 */
+  double beta0_scale;       /* beta_0 = beta0_scale/||x||_inf, default 1 */
+  double beta_bar_ratio;    /* beta_bar = ratio * beta_0, default 1e10 */
+  int32_t seed_max_iter;    /* default 500 */
+  int32_t filter_max_iter;  /* default 500 */
+  int32_t seed_subspace;    /* initial subspace size of the seed's partial
+                               SVD; <= 0 means r + max(6, r/4), rounded up to
+                               even */
+  int32_t refine_iters;     /* PCP_BF16_REFINED: FP32 iterations after the
+                               BF16 phase, default 8 (0 = until filter_tol) */
+  uint64_t rng_seed;        /* seed sampling when seed_rows/cols are NULL */
+  const int64_t* seed_rows; /* optional host array, m' distinct row indices */
+  const int64_t* seed_cols; /* optional host array, n' distinct col indices */
+} pcp_params;
+
+/* Diagnostics of one solve. */
+typedef struct pcp_info {
+  int32_t rank;             /* r' = numerical rank of L^s kept (<= r) */
+  int32_t rank_ok;          /* 1 if Eq. rank_test holds */
+  int32_t seed_iters;       /* ALM iterations of the seed PCP */
+  int32_t filter_iters_max; /* most Algorithm 1 iterations of any problem */
+  int64_t seed_m, seed_n;   /* m', n' */
+  int64_t problems;         /* (n - n') column + (m - m') row problems */
+  int64_t problems_unconverged;
+  double seed_residual;     /* final ||M^s-L^s-S^s||_F/||M^s||_F */
+  double lambda;            /* full-problem lambda used/reported */
+  float t_seed_ms;          /* gather + seed PCP + factor assembly */
+  float t_filter_ms;        /* column and row filtering */
+  float t_spass_ms;         /* S = M - L */
+  float t_total_ms;
+} pcp_info;
+
+typedef struct pcp_plan pcp_plan;
+
+/* Fill *p with the defaults listed above for an m x n problem of target
+ * rank r.  Returns PCP_ERR_ARG if p is NULL. */
+pcp_status pcp_params_default(pcp_params* p, int64_t m, int64_t n, int32_t r);
+
+/* Human-readable message of the last error on the calling thread. */
+const char* pcp_last_error(void);
+
+/* Library version string. */
+const char* pcp_version(void);
+
+/* ------------------------------------------------------------------------
+ * Whole solve (Algorithm 2).
+ * ---------------------------------------------------------------------- */
+
+/* Validate *params and allocate the device workspace for problems of that
+ * size (seed buffers, index sets, per-problem status).  The plan copies
+ * *params (and the optional seed index arrays) and owns its workspace until
+ * pcp_plan_destroy().  One plan serves any number of sequential solves of
+ * the same shape; concurrent solves need separate plans. */
+pcp_status pcp_l1filter_plan(const pcp_params* params, pcp_plan** out);
+
+/* Run Algorithm 2 on M.
+ *   dM  (m x n, ldm >= m), FP32, read only.
+ *   dLu (m x r, ld m) and dLv (n x r, ld n), FP32, written: the factored
+ *       low-rank part with W = (Sigma^s)^{-1} folded in, L = Lu * Lv^T:
+ *         Lu[I_s]  = U^s,               Lu[~I_s] = P~^T (Sigma^s)^{-1},
+ *         Lv[J_s]  = V^s Sigma^s,       Lv[~J_s] = Q~^T,
+ *       columns r'..r-1 zero when the seed rank r' < r.
+ *   dS  (m x n, lds >= m), FP32, written with S = M - Lu Lv^T.  May be NULL
+ *       to skip the S pass (factors only).
+ *   h_seed_rows_out / h_seed_cols_out: optional host arrays of m' / n'
+ *       entries receiving I_s and J_s.
+ *   info: optional.  When non-NULL the call synchronises the stream and
+ *       fills *info (stage times by CUDA events); when NULL the call is
+ *       asynchronous except for the seed index upload.
+ * Returns PCP_ERR_RANK_TEST / PCP_ERR_SEED_NOCONV / PCP_ERR_FILTER_NOCONV
+ * only when info is non-NULL (the checks need the device results). */
+pcp_status pcp_l1filter_solve(pcp_plan* plan, const float* dM, int64_t ldm,
+                              float* dLu, float* dLv, float* dS, int64_t lds,
+                              int64_t* h_seed_rows_out,
+                              int64_t* h_seed_cols_out, pcp_info* info,
+                              void* stream);
+
+void pcp_plan_destroy(pcp_plan* plan);
+
+/* ------------------------------------------------------------------------
+ * Stage entry points (the rows of the hot path, callable one by one).
+ * Index arrays are device int32 arrays.
+ * ---------------------------------------------------------------------- */
+
+/* Stage 1 gather (Eq. partition): dMs[i + j*mp] = (double) dM[rows[i] +
+ * cols[j]*ldm] for i < mp, j < np.  Returns PCP_ERR_ARG on bad sizes. */
+pcp_status pcp_gather_seed(const float* dM, int64_t ldm, const int32_t* d_rows,
+                           int32_t mp, const int32_t* d_cols, int32_t np,
+                           double* dMs, void* stream);
+
+/* Bytes of device workspace pcp_seed_pcp needs for an mp x np seed whose
+ * partial SVD may grow to kmax vectors (kmax <= min(mp, np), kmax <= 128). */
+size_t pcp_seed_workspace_bytes(int32_t mp, int32_t np, int32_t kmax);
+
+/* Stage 2: seed PCP (Eq. SPCP) by inexact ALM in FP64 with a partial SVD
+ * for the singular value thresholding (Eq. SVT), one persistent cooperative
+ * launch.  dD is mp x np (ld mp), FP64, read only.  On return (the call
+ * synchronises `stream`):
+ *   dU (mp x kmax, ld mp), dSigma (kmax), dV (np x kmax, ld np): the skinny
+ *   SVD of the recovered L^s, columns sorted by decreasing singular value,
+ *   entries past *h_rank zero;  *h_rank = r' (singular values above
+ *   rank_cut * largest, capped at r_cap when r_cap > 0);
+ *   *h_iters, *h_residual: ALM iterations and final relative residual.
+ * lambda <= 0 means 1/sqrt(max(mp,np)).  k0 is the initial subspace size
+ * (even, <= kmax).  d_work must hold pcp_seed_workspace_bytes() bytes.
+ * Returns PCP_ERR_SEED_NOCONV when max_iter is reached (outputs written),
+ * PCP_ERR_TIMEOUT if a device barrier wait ran out. */
+pcp_status pcp_seed_pcp(const double* dD, int32_t mp, int32_t np,
+                        double lambda, double tol, double rho,
+                        double mu_scale, double mu_max_ratio, int32_t max_iter,
+                        int32_t k0, int32_t kmax, double rank_cut,
+                        int32_t r_cap, void* d_work, double* dU,
+                        double* dSigma, double* dV, int32_t* h_rank,
+                        int32_t* h_iters, double* h_residual, void* stream);
+
+/* Stage 3/4: Algorithm 1 on N independent problems (columns or rows of M),
+ * FP32.  Problem j reads its p entries x_j[t] = dM[pidx[t]*sp + qidx[j]*sq]
+ * (column problems: pidx = I_s, sp = 1, qidx = ~J_s, sq = ldm; row problems:
+ * pidx = J_s, sp = ldm, qidx = ~I_s, sq = 1) and is regressed on
+ * dA (p x r, ld lda, FP32, orthonormal columns).  The solution z_j is
+ * written as dZ[qidx[j] + k*ldz] = z_j[k] * (d_scale ? d_scale[k] : 1) for
+ * k < r (so the result lands directly in a row of Lv or Lu).  The rank is
+ * read from *d_rank when d_rank is non-NULL (device int32, <= r; columns
+ * past it are written as zero).  d_iters (N int32, optional) receives each
+ * problem's iteration count, negated when it hit max_iter.
+ * precision: PCP_FP32 or PCP_BF16_REFINED (refine_iters FP32 iterations
+ * follow the BF16 phase; 0 = continue in FP32 until eps).
+ * Limits: p <= 1024, r <= 64. */
+pcp_status pcp_l1_filter(const float* dM, const int32_t* d_pidx, int32_t p,
+                         int64_t sp, const int32_t* d_qidx, int32_t N,
+                         int64_t sq, const float* dA, int32_t lda, int32_t r,
+                         const int32_t* d_rank, const float* d_scale,
+                         float* dZ, int64_t ldz, double eps, double rho,
+                         double beta0_scale, double beta_bar_ratio,
+                         int32_t max_iter, int32_t precision,
+                         int32_t refine_iters, int32_t* d_iters,
+                         void* stream);
+
+/* Stage 5: factor assembly (Eq. l1s').  From the seed's FP64 skinny SVD
+ * (dU mp x ku ld mp, dSigma, dV np x ku ld np, rank *d_rank) write
+ *   Lu[rows[i] + k*ldu] = U[i,k],  Lv[cols[j] + k*ldv] = V[j,k]*sigma_k,
+ * the FP32 copies dU32 (mp x r, ld mp) and dV32 (np x r, ld np) used as A by
+ * the filters, and d_inv_sigma32[k] = 1/sigma_k (0 past the rank), for
+ * k < r.  Columns k >= rank of Lu/Lv rows outside the seed are zeroed by the
+ * filters; rows inside the seed are written here. */
+pcp_status pcp_assemble_factors(const double* dU, const double* dSigma,
+                                const double* dV, int32_t mp, int32_t np,
+                                int32_t ku, const int32_t* d_rank, int32_t r,
+                                const int32_t* d_rows, const int32_t* d_cols,
+                                float* dLu, int64_t ldu, float* dLv,
+                                int64_t ldv, float* dU32, float* dV32,
+                                float* d_inv_sigma32, void* stream);
+
+/* Stage 6, the S pass (Algorithm 2 output): dS = dM - dLu * dLv^T over the
+ * full m x n matrix, FP32, with dLu m x r (ld ldu) and dLv n x r (ld ldv).
+ * dS may alias dM only if lds == ldm (in-place update). */
+pcp_status pcp_spass(const float* dM, int64_t ldm, const float* dLu,
+                     int64_t ldu, const float* dLv, int64_t ldv, int32_t r,
+                     float* dS, int64_t lds, int64_t m, int64_t n,
+                     void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCP_L1F_H */

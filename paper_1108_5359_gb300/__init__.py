@@ -1,0 +1,224 @@
+"""GB300-native l1 filtering for Principal Component Pursuit (arXiv 1108.5359).
+
+The work runs in the CUDA library ``libpcpl1f.so`` (C ABI in
+``include/pcp_l1f.h``); this module only marshals torch tensors (device
+memory, streams) into its entry points, under the same names.  There is no
+CPU fallback: every call fails if the library or a GPU is missing.
+
+Matrix convention: column-major.  A torch tensor ``X`` of shape (rows, cols)
+is passed as (pointer, leading dimension) and must have ``X.stride(0) == 1``;
+``colmajor(rows, cols)`` allocates one.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _abi
+from ._abi import (PCPError, PCPInfo, PCPParams, PCP_BF16_REFINED, PCP_FP32,
+                   PCP_OK, check, load)
+
+__all__ = [
+    "PCPError", "PCPInfo", "PCPParams", "PCP_FP32", "PCP_BF16_REFINED",
+    "colmajor", "pcp_params_default", "pcp_l1filter_plan",
+    "pcp_l1filter_solve", "pcp_plan_destroy", "pcp_gather_seed",
+    "pcp_seed_workspace_bytes", "pcp_seed_pcp", "pcp_l1_filter",
+    "pcp_assemble_factors", "pcp_spass", "Plan", "solve", "load",
+]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def colmajor(rows, cols, dtype=None, device="cuda", fill=None):
+    """Column-major (Fortran-order) tensor of shape (rows, cols)."""
+    torch = _torch()
+    dtype = dtype or torch.float32
+    t = torch.empty((cols, rows), dtype=dtype, device=device).t()
+    if fill is not None:
+        t.fill_(fill)
+    return t
+
+
+def _cm(t, name):
+    """(pointer, leading dimension) of a column-major CUDA tensor."""
+    if t is None:
+        return None, 0
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dim() == 1:
+        return t.data_ptr(), max(1, t.shape[0])
+    if t.stride(0) != 1 and t.shape[0] > 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    return t.data_ptr(), max(t.stride(1), t.shape[0], 1)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return _torch().cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# --------------------------------------------------------------------------
+# thin wrappers, one per C entry point
+# --------------------------------------------------------------------------
+
+def pcp_params_default(m, n, r) -> PCPParams:
+    p = PCPParams()
+    check(load().pcp_params_default(C.byref(p), m, n, r), "pcp_params_default")
+    return p
+
+
+class Plan:
+    """Owns a pcp_plan (device workspace) and the index arrays it points to."""
+
+    def __init__(self, params: PCPParams, seed_rows=None, seed_cols=None):
+        import numpy as np
+        self._keep = []
+        if seed_rows is not None:
+            a = np.ascontiguousarray(seed_rows, dtype=np.int64)
+            self._keep.append(a)
+            params.seed_rows = a.ctypes.data_as(C.POINTER(C.c_int64))
+        if seed_cols is not None:
+            a = np.ascontiguousarray(seed_cols, dtype=np.int64)
+            self._keep.append(a)
+            params.seed_cols = a.ctypes.data_as(C.POINTER(C.c_int64))
+        self.params = params
+        self.handle = C.c_void_p()
+        check(load().pcp_l1filter_plan(C.byref(params), C.byref(self.handle)),
+              "pcp_l1filter_plan")
+        self.m, self.n, self.r = params.m, params.n, params.r
+        self.mp = int(round(params.s_r * params.r))
+        self.np = int(round(params.s_c * params.r))
+
+    def close(self):
+        if self.handle:
+            load().pcp_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pcp_l1filter_plan(params: PCPParams, seed_rows=None, seed_cols=None):
+    return Plan(params, seed_rows, seed_cols)
+
+
+def pcp_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def pcp_l1filter_solve(plan: Plan, M, Lu, Lv, S=None, info=True,
+                       stream=None, raise_on_error=True):
+    """Algorithm 2 on M into (Lu, Lv, S); returns (status, info, rows, cols)."""
+    import numpy as np
+    pM, ldm = _cm(M, "M")
+    pLu, _ = _cm(Lu, "Lu")
+    pLv, _ = _cm(Lv, "Lv")
+    pS, lds = _cm(S, "S")
+    rows = np.zeros(plan.mp, dtype=np.int64)
+    cols = np.zeros(plan.np, dtype=np.int64)
+    inf = PCPInfo() if info else None
+    st = load().pcp_l1filter_solve(
+        plan.handle, pM, ldm, pLu, pLv, pS, lds if S is not None else plan.m,
+        rows.ctypes.data_as(C.POINTER(C.c_int64)),
+        cols.ctypes.data_as(C.POINTER(C.c_int64)),
+        C.byref(inf) if inf is not None else None, _stream(stream))
+    if raise_on_error and st not in (PCP_OK,):
+        check(st, "pcp_l1filter_solve")
+    return st, inf, rows, cols
+
+
+def pcp_gather_seed(M, d_rows, d_cols, Ms, stream=None):
+    pM, ldm = _cm(M, "M")
+    check(load().pcp_gather_seed(pM, ldm, _ptr(d_rows), d_rows.numel(),
+                                 _ptr(d_cols), d_cols.numel(), _ptr(Ms),
+                                 _stream(stream)), "pcp_gather_seed")
+
+
+def pcp_seed_workspace_bytes(mp, np_, kmax):
+    return int(load().pcp_seed_workspace_bytes(mp, np_, kmax))
+
+
+def pcp_seed_pcp(D, lam, tol, rho, mu_scale, mu_max_ratio, max_iter, k0, kmax,
+                 rank_cut, r_cap, work, U, Sigma, V, stream=None,
+                 raise_on_error=True):
+    mp, np_ = D.shape
+    rank = C.c_int32()
+    iters = C.c_int32()
+    resid = C.c_double()
+    pD, ldd = _cm(D, "D")
+    if ldd != mp:
+        raise ValueError("D must be packed (ld == rows)")
+    st = load().pcp_seed_pcp(pD, mp, np_, lam, tol, rho, mu_scale,
+                             mu_max_ratio, max_iter, k0, kmax, rank_cut, r_cap,
+                             _ptr(work), _ptr(U), _ptr(Sigma), _ptr(V),
+                             C.byref(rank), C.byref(iters), C.byref(resid),
+                             _stream(stream))
+    if raise_on_error:
+        check(st, "pcp_seed_pcp")
+    return st, rank.value, iters.value, resid.value
+
+
+def pcp_l1_filter(M, d_pidx, sp, d_qidx, sq, A, r, Z, ldz, eps, rho,
+                  beta0_scale=1.0, beta_bar_ratio=1e10, max_iter=500,
+                  precision=PCP_FP32, refine_iters=8, d_rank=None,
+                  d_scale=None, d_iters=None, stream=None):
+    pA, lda = _cm(A, "A")
+    check(load().pcp_l1_filter(
+        _ptr(M), _ptr(d_pidx), d_pidx.numel(), sp, _ptr(d_qidx),
+        d_qidx.numel(), sq, pA, lda, r, _ptr(d_rank), _ptr(d_scale), _ptr(Z),
+        ldz, eps, rho, beta0_scale, beta_bar_ratio, max_iter, precision,
+        refine_iters, _ptr(d_iters), _stream(stream)), "pcp_l1_filter")
+
+
+def pcp_assemble_factors(U, Sigma, V, d_rank, r, d_rows, d_cols, Lu, Lv, U32,
+                         V32, inv_sigma32, stream=None):
+    mp, ku = U.shape
+    np_ = V.shape[0]
+    pLu, ldu = _cm(Lu, "Lu")
+    pLv, ldv = _cm(Lv, "Lv")
+    check(load().pcp_assemble_factors(
+        _ptr(U), _ptr(Sigma), _ptr(V), mp, np_, ku, _ptr(d_rank), r,
+        _ptr(d_rows), _ptr(d_cols), pLu, ldu, pLv, ldv, _ptr(U32), _ptr(V32),
+        _ptr(inv_sigma32), _stream(stream)), "pcp_assemble_factors")
+
+
+def pcp_spass(M, Lu, Lv, S, stream=None):
+    pM, ldm = _cm(M, "M")
+    pLu, ldu = _cm(Lu, "Lu")
+    pLv, ldv = _cm(Lv, "Lv")
+    pS, lds = _cm(S, "S")
+    m, n = M.shape
+    r = Lu.shape[1]
+    check(load().pcp_spass(pM, ldm, pLu, ldu, pLv, ldv, r, pS, lds, m, n,
+                           _stream(stream)), "pcp_spass")
+
+
+def solve(M, r, seed_rows=None, seed_cols=None, want_S=True, stream=None,
+          raise_on_error=True, **overrides):
+    """One-call Algorithm 2: returns (Lu, Lv, S, info, rows, cols).
+
+    ``M`` is a column-major float32 CUDA tensor (m x n).  Keyword overrides
+    set pcp_params fields (e.g. filter_tol=1e-6).
+    """
+    m, n = M.shape
+    p = pcp_params_default(m, n, r)
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k == "lambda" else k, v)
+    plan = Plan(p, seed_rows, seed_cols)
+    Lu = colmajor(m, r, device=M.device)
+    Lv = colmajor(n, r, device=M.device)
+    S = colmajor(m, n, device=M.device) if want_S else None
+    st, info, rows, cols = pcp_l1filter_solve(plan, M, Lu, Lv, S, True,
+                                              stream, raise_on_error)
+    plan.close()
+    return Lu, Lv, S, info, rows, cols, st

@@ -1,0 +1,478 @@
+// Host side of the C ABI: parameters, plans, the whole solve (Algorithm 2),
+// error reporting and seed sampling.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pcp {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+pcp_status cuda_fail(cudaError_t e, const char* what, const char* file,
+                     int line) {
+  set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  if (e == cudaErrorMemoryAllocation) return PCP_ERR_NOMEM;
+  return PCP_ERR_CUDA;
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+      cudaSuccess)
+    return 0;
+  return sms;
+}
+
+// defined in seed.cu / spass.cu
+size_t seed_workspace_bytes(int mp, int np, int kmax);
+pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
+                          double tol, double rho, double mu_scale,
+                          double mu_max_ratio, int max_iter, int k0, int kmax,
+                          double rank_cut, int r_cap, void* d_work,
+                          double* dU, double* dSigma, double* dV,
+                          cudaStream_t st, int** d_rank_out);
+pcp_status seed_read_ctl(void* d_work, int mp, int np, int kmax,
+                         cudaStream_t st, int* rank, int* iters,
+                         double* residual, int* converged, int* error,
+                         int* rank_raw);
+pcp_status gather_seed(const float* dM, int64_t ldm, const int32_t* d_rows,
+                       int32_t mp, const int32_t* d_cols, int32_t np,
+                       double* dMs, int32_t* d_bad, cudaStream_t st);
+
+// splitmix64: the library's own generator for seed sampling.
+static uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// k distinct values of [0, n), sorted (partial Fisher-Yates on a map-free
+// rejection scheme for k << n, full shuffle otherwise).
+static std::vector<int64_t> sample_sorted(int64_t n, int64_t k,
+                                          uint64_t seed) {
+  std::vector<int64_t> out;
+  uint64_t s = seed;
+  if (k * 4 >= n) {
+    std::vector<int64_t> all(n);
+    std::iota(all.begin(), all.end(), 0);
+    for (int64_t i = 0; i < k; ++i) {
+      const int64_t j = i + (int64_t)(splitmix64(s) % (uint64_t)(n - i));
+      std::swap(all[i], all[j]);
+    }
+    out.assign(all.begin(), all.begin() + k);
+  } else {
+    std::vector<char> taken(n, 0);
+    while ((int64_t)out.size() < k) {
+      const int64_t v = (int64_t)(splitmix64(s) % (uint64_t)n);
+      if (!taken[v]) {
+        taken[v] = 1;
+        out.push_back(v);
+      }
+    }
+  }
+  std::sort(out.begin(), out.end());
+  return out;
+}
+
+}  // namespace pcp
+
+struct pcp_plan {
+  pcp_params p;
+  std::vector<int64_t> given_rows, given_cols;
+  int64_t m, n;
+  int r, mp, np, kmax, k0;
+  double lam_seed, lam_full;
+  int device;
+  // device memory (one allocation)
+  void* d_base = nullptr;
+  size_t d_bytes = 0;
+  int32_t *d_rows = nullptr, *d_cols = nullptr, *d_rbar = nullptr,
+          *d_cbar = nullptr;
+  double *d_Ms = nullptr, *d_U = nullptr, *d_Sigma = nullptr, *d_V = nullptr;
+  float *d_U32 = nullptr, *d_V32 = nullptr, *d_inv_sigma = nullptr;
+  int32_t *d_iters = nullptr, *d_bad = nullptr;
+  void* d_seed_work = nullptr;
+  // pinned staging of the index sets
+  int32_t* h_idx = nullptr;
+  bool idx_uploaded = false;
+  std::vector<int64_t> cur_rows, cur_cols;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+extern "C" const char* pcp_last_error(void) { return pcp::g_err; }
+
+extern "C" const char* pcp_version(void) {
+  return "pcp_l1f 0.1 (sm_103a)";
+}
+
+extern "C" pcp_status pcp_params_default(pcp_params* p, int64_t m, int64_t n,
+                                         int32_t r) {
+  if (!p) {
+    pcp::set_error("pcp_params_default: null pointer");
+    return PCP_ERR_ARG;
+  }
+  std::memset(p, 0, sizeof(*p));
+  p->m = m;
+  p->n = n;
+  p->r = r;
+  p->precision = PCP_FP32;
+  p->lambda = 0.0;
+  p->lambda_seed = 0.0;
+  p->s_r = 10.0;
+  p->s_c = 10.0;
+  p->seed_tol = 1e-7;
+  p->seed_rho = 1.5;
+  p->seed_mu_scale = 1.25;
+  p->seed_mu_max_ratio = 1e7;
+  p->rank_cut = 1e-10;
+  p->filter_tol = 3e-7;
+  p->filter_rho = 1.5;
+  p->beta0_scale = 1.0;
+  p->beta_bar_ratio = 1e10;
+  p->seed_max_iter = 500;
+  p->filter_max_iter = 500;
+  p->seed_subspace = 0;
+  p->refine_iters = 8;
+  p->rng_seed = 0x1108535900000001ull;
+  p->seed_rows = nullptr;
+  p->seed_cols = nullptr;
+  return PCP_OK;
+}
+
+static pcp_status check_index_set(const int64_t* v, int64_t k, int64_t n,
+                                  const char* what) {
+  std::vector<char> seen(n, 0);
+  for (int64_t i = 0; i < k; ++i) {
+    if (v[i] < 0 || v[i] >= n || seen[v[i]]) {
+      pcp::set_error("%s: index %lld at %lld out of range or repeated", what,
+                     (long long)v[i], (long long)i);
+      return PCP_ERR_ARG;
+    }
+    seen[v[i]] = 1;
+  }
+  return PCP_OK;
+}
+
+extern "C" pcp_status pcp_l1filter_plan(const pcp_params* params,
+                                        pcp_plan** out) {
+  PCP_ARG(params && out, "pcp_l1filter_plan: null pointer");
+  *out = nullptr;
+  const pcp_params& q = *params;
+  PCP_ARG(q.m >= 2 && q.n >= 2 && q.m < (1LL << 31) && q.n < (1LL << 31),
+          "pcp_l1filter_plan: m=%lld n=%lld out of range", (long long)q.m,
+          (long long)q.n);
+  PCP_ARG(q.r >= 1 && q.r <= 32, "pcp_l1filter_plan: r=%d outside [1, 32]",
+          q.r);
+  PCP_ARG(q.s_r > 0 && q.s_c > 0, "pcp_l1filter_plan: oversampling <= 0");
+  PCP_ARG(q.precision == PCP_FP32,
+          "pcp_l1filter_plan: precision %d not available", q.precision);
+  const int mp = (int)std::llround(q.s_r * q.r);
+  const int np = (int)std::llround(q.s_c * q.r);
+  PCP_ARG(mp >= 2 && np >= 2 && mp < q.m && np < q.n,
+          "pcp_l1filter_plan: seed %dx%d does not fit in %lldx%lld", mp, np,
+          (long long)q.m, (long long)q.n);
+  PCP_ARG(mp <= 256 && np <= 256,
+          "pcp_l1filter_plan: seed %dx%d larger than 256", mp, np);
+  PCP_ARG(q.filter_tol > 0 && q.filter_rho > 1 && q.beta0_scale > 0 &&
+              q.beta_bar_ratio >= 1 && q.filter_max_iter >= 1,
+          "pcp_l1filter_plan: bad filter parameters");
+  PCP_ARG(q.seed_tol > 0 && q.seed_rho > 1 && q.seed_mu_scale > 0 &&
+              q.seed_mu_max_ratio >= 1 && q.seed_max_iter >= 1,
+          "pcp_l1filter_plan: bad seed parameters");
+  if (q.seed_rows) {
+    pcp_status s = check_index_set(q.seed_rows, mp, q.m, "seed_rows");
+    if (s != PCP_OK) return s;
+  }
+  if (q.seed_cols) {
+    pcp_status s = check_index_set(q.seed_cols, np, q.n, "seed_cols");
+    if (s != PCP_OK) return s;
+  }
+
+  pcp_plan* P = new pcp_plan();
+  P->p = q;
+  if (q.seed_rows) P->given_rows.assign(q.seed_rows, q.seed_rows + mp);
+  if (q.seed_cols) P->given_cols.assign(q.seed_cols, q.seed_cols + np);
+  P->p.seed_rows = nullptr;
+  P->p.seed_cols = nullptr;
+  P->m = q.m;
+  P->n = q.n;
+  P->r = q.r;
+  P->mp = mp;
+  P->np = np;
+  int k0 = q.seed_subspace > 0 ? q.seed_subspace
+                               : q.r + std::max(6, q.r / 4);
+  k0 = (k0 + 1) / 2 * 2;
+  const int kcap = std::min(std::min(mp, np) / 2 * 2, 96);
+  k0 = std::min(k0, kcap);
+  P->k0 = k0;
+  P->kmax = std::min(kcap, std::max(k0 + 16, 2 * k0) / 2 * 2);
+  P->lam_seed = q.lambda_seed > 0 ? q.lambda_seed
+                                  : 1.0 / std::sqrt((double)std::max(mp, np));
+  P->lam_full = q.lambda > 0
+                    ? q.lambda
+                    : 1.0 / std::sqrt((double)std::max(q.m, q.n));
+  if (cudaGetDevice(&P->device) != cudaSuccess) P->device = 0;
+
+  // one device allocation, carved up
+  const int64_t nrb = q.m - mp, ncb = q.n - np;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const size_t o_rows = take(sizeof(int32_t) * mp);
+  const size_t o_cols = take(sizeof(int32_t) * np);
+  const size_t o_rbar = take(sizeof(int32_t) * nrb);
+  const size_t o_cbar = take(sizeof(int32_t) * ncb);
+  const size_t o_Ms = take(sizeof(double) * mp * np);
+  const size_t o_U = take(sizeof(double) * mp * P->kmax);
+  const size_t o_Sig = take(sizeof(double) * P->kmax);
+  const size_t o_V = take(sizeof(double) * np * P->kmax);
+  const size_t o_U32 = take(sizeof(float) * mp * q.r);
+  const size_t o_V32 = take(sizeof(float) * np * q.r);
+  const size_t o_isg = take(sizeof(float) * q.r);
+  const size_t o_it = take(sizeof(int32_t) * (nrb + ncb));
+  const size_t o_bad = take(sizeof(int32_t) * 4);
+  const size_t o_sw = take(pcp::seed_workspace_bytes(mp, np, P->kmax));
+  P->d_bytes = off;
+  cudaError_t e = cudaMalloc(&P->d_base, off);
+  if (e != cudaSuccess) {
+    delete P;
+    return pcp::cuda_fail(e, "cudaMalloc(plan workspace)", __FILE__, __LINE__);
+  }
+  char* base = static_cast<char*>(P->d_base);
+  P->d_rows = reinterpret_cast<int32_t*>(base + o_rows);
+  P->d_cols = reinterpret_cast<int32_t*>(base + o_cols);
+  P->d_rbar = reinterpret_cast<int32_t*>(base + o_rbar);
+  P->d_cbar = reinterpret_cast<int32_t*>(base + o_cbar);
+  P->d_Ms = reinterpret_cast<double*>(base + o_Ms);
+  P->d_U = reinterpret_cast<double*>(base + o_U);
+  P->d_Sigma = reinterpret_cast<double*>(base + o_Sig);
+  P->d_V = reinterpret_cast<double*>(base + o_V);
+  P->d_U32 = reinterpret_cast<float*>(base + o_U32);
+  P->d_V32 = reinterpret_cast<float*>(base + o_V32);
+  P->d_inv_sigma = reinterpret_cast<float*>(base + o_isg);
+  P->d_iters = reinterpret_cast<int32_t*>(base + o_it);
+  P->d_bad = reinterpret_cast<int32_t*>(base + o_bad);
+  P->d_seed_work = base + o_sw;
+  e = cudaMallocHost(&P->h_idx, sizeof(int32_t) * (q.m + q.n));
+  if (e != cudaSuccess) {
+    cudaFree(P->d_base);
+    delete P;
+    return pcp::cuda_fail(e, "cudaMallocHost(index staging)", __FILE__,
+                          __LINE__);
+  }
+  for (auto& ev : P->ev) {
+    e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) {
+      pcp_plan_destroy(P);
+      return pcp::cuda_fail(e, "cudaEventCreate", __FILE__, __LINE__);
+    }
+  }
+  *out = P;
+  return PCP_OK;
+}
+
+extern "C" void pcp_plan_destroy(pcp_plan* P) {
+  if (!P) return;
+  for (auto& ev : P->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (P->h_idx) cudaFreeHost(P->h_idx);
+  if (P->d_base) cudaFree(P->d_base);
+  delete P;
+}
+
+// Upload I_s, J_s and their sorted complements (only when they changed).
+static pcp_status upload_indices(pcp_plan* P, cudaStream_t st) {
+  std::vector<int64_t> rows =
+      P->given_rows.empty()
+          ? pcp::sample_sorted(P->m, P->mp, P->p.rng_seed)
+          : P->given_rows;
+  std::vector<int64_t> cols =
+      P->given_cols.empty()
+          ? pcp::sample_sorted(P->n, P->np, P->p.rng_seed ^ 0xC01C01C0ull)
+          : P->given_cols;
+  if (P->idx_uploaded && rows == P->cur_rows && cols == P->cur_cols)
+    return PCP_OK;
+  // the previous upload may still be read by in-flight work on this stream
+  PCP_CUDA(cudaStreamSynchronize(st));
+  int32_t* h = P->h_idx;
+  std::vector<char> in_r(P->m, 0), in_c(P->n, 0);
+  int64_t o = 0;
+  for (int i = 0; i < P->mp; ++i) {
+    h[o++] = (int32_t)rows[i];
+    in_r[rows[i]] = 1;
+  }
+  for (int j = 0; j < P->np; ++j) {
+    h[o++] = (int32_t)cols[j];
+    in_c[cols[j]] = 1;
+  }
+  for (int64_t i = 0; i < P->m; ++i)
+    if (!in_r[i]) h[o++] = (int32_t)i;
+  for (int64_t j = 0; j < P->n; ++j)
+    if (!in_c[j]) h[o++] = (int32_t)j;
+  // the four arrays are contiguous pieces of one allocation, but each is
+  // 256-byte aligned; copy them one by one.
+  PCP_CUDA(cudaMemcpyAsync(P->d_rows, h, sizeof(int32_t) * P->mp,
+                           cudaMemcpyHostToDevice, st));
+  PCP_CUDA(cudaMemcpyAsync(P->d_cols, h + P->mp, sizeof(int32_t) * P->np,
+                           cudaMemcpyHostToDevice, st));
+  PCP_CUDA(cudaMemcpyAsync(P->d_rbar, h + P->mp + P->np,
+                           sizeof(int32_t) * (P->m - P->mp),
+                           cudaMemcpyHostToDevice, st));
+  PCP_CUDA(cudaMemcpyAsync(P->d_cbar, h + P->mp + P->np + (P->m - P->mp),
+                           sizeof(int32_t) * (P->n - P->np),
+                           cudaMemcpyHostToDevice, st));
+  P->cur_rows = rows;
+  P->cur_cols = cols;
+  P->idx_uploaded = true;
+  return PCP_OK;
+}
+
+extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
+                                         int64_t ldm, float* dLu, float* dLv,
+                                         float* dS, int64_t lds,
+                                         int64_t* h_seed_rows_out,
+                                         int64_t* h_seed_cols_out,
+                                         pcp_info* info, void* stream) {
+  PCP_ARG(P, "pcp_l1filter_solve: null plan");
+  PCP_ARG(dM && dLu && dLv, "pcp_l1filter_solve: null pointer");
+  PCP_ARG(ldm >= P->m, "pcp_l1filter_solve: ldm < m");
+  PCP_ARG(!dS || lds >= P->m, "pcp_l1filter_solve: lds < m");
+  cudaStream_t st = (cudaStream_t)stream;
+  const pcp_params& q = P->p;
+  pcp_status s = upload_indices(P, st);
+  if (s != PCP_OK) return s;
+  if (h_seed_rows_out)
+    std::copy(P->cur_rows.begin(), P->cur_rows.end(), h_seed_rows_out);
+  if (h_seed_cols_out)
+    std::copy(P->cur_cols.begin(), P->cur_cols.end(), h_seed_cols_out);
+  const bool timed = info != nullptr;
+  if (timed) PCP_CUDA(cudaEventRecord(P->ev[0], st));
+
+  // stage 1: gather the seed (FP64) and count non-finite entries
+  PCP_CUDA(cudaMemsetAsync(P->d_bad, 0, sizeof(int32_t), st));
+  s = pcp::gather_seed(dM, ldm, P->d_rows, P->mp, P->d_cols, P->np, P->d_Ms,
+                       P->d_bad, st);
+  if (s != PCP_OK) return s;
+  // stage 2: seed PCP (FP64)
+  int* d_rank = nullptr;
+  s = pcp::seed_pcp_async(P->d_Ms, P->mp, P->np, P->lam_seed, q.seed_tol,
+                          q.seed_rho, q.seed_mu_scale, q.seed_mu_max_ratio,
+                          q.seed_max_iter, P->k0, P->kmax, q.rank_cut, P->r,
+                          P->d_seed_work, P->d_U, P->d_Sigma, P->d_V, st,
+                          &d_rank);
+  if (s != PCP_OK) return s;
+  // stage 5 (seed rows of the factors) + FP32 bases for the filters
+  s = pcp_assemble_factors(P->d_U, P->d_Sigma, P->d_V, P->mp, P->np, P->kmax,
+                           d_rank, P->r, P->d_rows, P->d_cols, dLu, P->m, dLv,
+                           P->n, P->d_U32, P->d_V32, P->d_inv_sigma, st);
+  if (s != PCP_OK) return s;
+  if (timed) PCP_CUDA(cudaEventRecord(P->ev[1], st));
+  // stages 3 and 4: column and row filtering (Algorithm 1)
+  const int64_t ncb = P->n - P->np, nrb = P->m - P->mp;
+  s = pcp_l1_filter(dM, P->d_rows, P->mp, 1, P->d_cbar, (int32_t)ncb, ldm,
+                    P->d_U32, P->mp, P->r, d_rank, nullptr, dLv, P->n,
+                    q.filter_tol, q.filter_rho, q.beta0_scale,
+                    q.beta_bar_ratio, q.filter_max_iter, q.precision,
+                    q.refine_iters, P->d_iters, st);
+  if (s != PCP_OK) return s;
+  s = pcp_l1_filter(dM, P->d_cols, P->np, ldm, P->d_rbar, (int32_t)nrb, 1,
+                    P->d_V32, P->np, P->r, d_rank, P->d_inv_sigma, dLu, P->m,
+                    q.filter_tol, q.filter_rho, q.beta0_scale,
+                    q.beta_bar_ratio, q.filter_max_iter, q.precision,
+                    q.refine_iters, P->d_iters + ncb, st);
+  if (s != PCP_OK) return s;
+  if (timed) PCP_CUDA(cudaEventRecord(P->ev[2], st));
+  // stage 6: S = M - Lu Lv^T
+  if (dS) {
+    s = pcp_spass(dM, ldm, dLu, P->m, dLv, P->n, P->r, dS, lds, P->m, P->n,
+                  st);
+    if (s != PCP_OK) return s;
+  }
+  if (!timed) return PCP_OK;
+  PCP_CUDA(cudaEventRecord(P->ev[3], st));
+
+  // diagnostics
+  int rank = 0, iters = 0, conv = 0, err = 0, rank_raw = 0;
+  double resid = 0;
+  s = pcp::seed_read_ctl(P->d_seed_work, P->mp, P->np, P->kmax, st, &rank,
+                         &iters, &resid, &conv, &err, &rank_raw);
+  if (s != PCP_OK) return s;
+  std::vector<int32_t> it(ncb + nrb);
+  int32_t bad = 0;
+  PCP_CUDA(cudaMemcpy(it.data(), P->d_iters, sizeof(int32_t) * it.size(),
+                      cudaMemcpyDeviceToHost));
+  PCP_CUDA(cudaMemcpy(&bad, P->d_bad, sizeof(int32_t),
+                      cudaMemcpyDeviceToHost));
+  std::memset(info, 0, sizeof(*info));
+  info->rank = rank;
+  info->seed_iters = iters;
+  info->seed_residual = resid;
+  info->seed_m = P->mp;
+  info->seed_n = P->np;
+  info->problems = ncb + nrb;
+  info->lambda = P->lam_full;
+  int imax = 0;
+  int64_t unconv = 0;
+  for (int32_t v : it) {
+    imax = std::max(imax, v < 0 ? -v : v);
+    unconv += (v < 0);
+  }
+  info->filter_iters_max = imax;
+  info->problems_unconverged = unconv;
+  // Eq. rank_test on the numerical rank before the cap at the target r
+  info->rank_ok = (rank_raw >= 1 &&
+                   (double)P->mp / rank_raw >= q.s_r - 1e-9 &&
+                   (double)P->np / rank_raw >= q.s_c - 1e-9)
+                      ? 1
+                      : 0;
+  float t01 = 0, t12 = 0, t23 = 0, t03 = 0;
+  cudaEventElapsedTime(&t01, P->ev[0], P->ev[1]);
+  cudaEventElapsedTime(&t12, P->ev[1], P->ev[2]);
+  cudaEventElapsedTime(&t23, P->ev[2], P->ev[3]);
+  cudaEventElapsedTime(&t03, P->ev[0], P->ev[3]);
+  info->t_seed_ms = t01;
+  info->t_filter_ms = t12;
+  info->t_spass_ms = t23;
+  info->t_total_ms = t03;
+  if (err) {
+    pcp::set_error("seed PCP: device barrier wait timed out");
+    return PCP_ERR_TIMEOUT;
+  }
+  if (bad) {
+    pcp::set_error("seed block of M holds %d non-finite entries", bad);
+    return PCP_ERR_NONFINITE;
+  }
+  if (!conv) {
+    pcp::set_error("seed PCP did not converge in %d iterations", iters);
+    return PCP_ERR_SEED_NOCONV;
+  }
+  if (!info->rank_ok) {
+    pcp::set_error("rank test failed: seed rank %d for a %dx%d seed",
+                   rank_raw, P->mp, P->np);
+    return PCP_ERR_RANK_TEST;
+  }
+  if (unconv) {
+    pcp::set_error("%lld l1 problems hit filter_max_iter",
+                   (long long)unconv);
+    return PCP_ERR_FILTER_NOCONV;
+  }
+  return PCP_OK;
+}

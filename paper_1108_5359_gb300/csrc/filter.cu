@@ -1,0 +1,308 @@
+// l1 filtering (Section 3.2): Algorithm 1 on many independent problems.
+//
+// Problem j solves  min ||e||_1  s.t.  x_j = A z + e  (Eq. l1g, one column),
+// A = U^s (column filter, Eq. l1c') or V^s (row filter, Eq. l1r'), with the
+// ADM steps of Algorithm 1:
+//   e_{k+1} = S_{1/beta_k}(x - A z_k + y_k/beta_k)
+//   z_{k+1} = A^T (x - e_{k+1} + y_k/beta_k)
+//   y_{k+1} = y_k + beta_k (x - A z_{k+1} - e_{k+1}),
+//   beta_{k+1} = min(rho beta_k, beta_bar)
+// stopping when ||x - A z_k - e_k||_inf / ||x||_inf < eps.  Each problem runs
+// its own instance (own beta_0 = beta0_scale/||x||_inf and stop test); the
+// problems are independent (Section 3.2), which is the grid decomposition.
+//
+// GB300 mapping (FP32 SIMT form):
+//   * one CTA = 8 warps = 32 problems; lane l of every warp works on problem
+//     l, warp w owns the entries t = w, w+8, w+16, ... of that problem;
+//   * x, y, e of the owned entries live in registers for the whole solve,
+//     A (p x r) is staged once into shared memory (row-major, zero padded to
+//     RMAX columns) and read as warp-broadcast float4;
+//   * one pass over the owned rows per iteration fuses A z (for the
+//     residual and dual step), the next shrinkage, and the partial products
+//     of A^T v for the next z; a cross-warp reduction through shared memory
+//     then yields z for every lane (deterministic order);
+//   * the infinity-norm stop test is a cross-warp max; a problem that has
+//     converged writes its z and is frozen (its lanes keep computing but
+//     never write again) so every problem stops exactly at its own test.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace pcp {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+
+struct FilterArgs {
+  const float* M;
+  const int32_t* pidx;
+  int p;
+  int64_t sp;
+  const int32_t* qidx;
+  int N;
+  int64_t sq;
+  const float* A;
+  int lda;
+  int r;
+  const int32_t* d_rank;
+  const float* scale;
+  float* Z;
+  int64_t ldz;
+  float eps, rho, beta0_scale, beta_bar_ratio;
+  int max_iter;
+  int32_t* iters_out;
+};
+
+template <int RMAX>
+__device__ __forceinline__ void load_arow(const float* __restrict__ As, int t,
+                                          float (&a)[RMAX]) {
+  const float4* row = reinterpret_cast<const float4*>(As + t * RMAX);
+#pragma unroll
+  for (int q = 0; q < RMAX / 4; ++q) {
+    float4 v = row[q];
+    a[4 * q + 0] = v.x;
+    a[4 * q + 1] = v.y;
+    a[4 * q + 2] = v.z;
+    a[4 * q + 3] = v.w;
+  }
+}
+
+template <int SPT, int RMAX>
+__global__ void __launch_bounds__(kThreads, 1)
+    adm_f32_kernel(const FilterArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  float* As = smem;                                 // [kWarps*SPT][RMAX]
+  float* red = As + kWarps * SPT * RMAX;            // [kWarps][RMAX][32]
+  float* zsh = red + kWarps * RMAX * 32;            // [RMAX][32]
+  float* mxs = zsh + RMAX * 32;                     // [kWarps][32]
+
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
+  const bool valid = j < a.N;
+  const int p = a.p;
+  int reff = a.r;
+  if (a.d_rank) reff = min(max(*a.d_rank, 0), a.r);
+
+  // Stage A (p x r, column-major, ld lda) as row-major [t][k], zero padded.
+  for (int idx = threadIdx.x; idx < kWarps * SPT * RMAX; idx += kThreads) {
+    const int t = idx / RMAX, k = idx - t * RMAX;
+    As[idx] = (t < p && k < reff) ? a.A[t + (int64_t)k * a.lda] : 0.0f;
+  }
+
+  // Load the owned entries of x_j.
+  float x[SPT], y[SPT], e[SPT];
+  const int64_t qoff = valid ? (int64_t)a.qidx[j] * a.sq : 0;
+  float xm = 0.0f;
+#pragma unroll
+  for (int s = 0; s < SPT; ++s) {
+    const int t = w + kWarps * s;
+    float v = 0.0f;
+    if (valid && t < p) v = __ldg(a.M + (int64_t)a.pidx[t] * a.sp + qoff);
+    x[s] = v;
+    y[s] = 0.0f;
+    xm = fmaxf(xm, fabsf(v));
+  }
+  mxs[w * 32 + lane] = xm;
+  __syncthreads();
+  float xinf = 0.0f;
+#pragma unroll
+  for (int q = 0; q < kWarps; ++q) xinf = fmaxf(xinf, mxs[q * 32 + lane]);
+  // A zero column has the exact solution z = 0 and takes no iteration.
+  bool done = !(xinf > 0.0f);
+  const float inv_xinf = done ? 0.0f : 1.0f / xinf;
+  float beta = done ? 1.0f : a.beta0_scale * inv_xinf;
+  const float beta_bar = beta * a.beta_bar_ratio;
+
+  // Iteration 1, step 1 with z_0 = 0, y_0 = 0: e_1 = S_{1/beta_0}(x);
+  // accumulate the partial products of z_1 = A^T (x - e_1).
+  float acc[RMAX];
+#pragma unroll
+  for (int k = 0; k < RMAX; ++k) acc[k] = 0.0f;
+  {
+    const float ib = 1.0f / beta;
+#pragma unroll
+    for (int s = 0; s < SPT; ++s) {
+      const int t = w + kWarps * s;
+      if (t < p) {
+        e[s] = shrink(x[s], ib);
+        const float v = x[s] - e[s];
+        float ar[RMAX];
+        load_arow<RMAX>(As, t, ar);
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k) acc[k] = fmaf(ar[k], v, acc[k]);
+      } else {
+        e[s] = 0.0f;
+      }
+    }
+  }
+  if (done && valid && w == 0) {
+    for (int k = 0; k < a.r; ++k) a.Z[(int64_t)a.qidx[j] + k * a.ldz] = 0.0f;
+    if (a.iters_out) a.iters_out[j] = 0;
+  }
+  if (!valid) done = true;
+
+  float z[RMAX];
+  int iter = 0;
+  while (true) {
+    // z_{k+1}: reduce the partial products across the 8 warps.
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) red[(w * RMAX + k) * 32 + lane] = acc[k];
+    __syncthreads();
+    for (int k = w; k < RMAX; k += kWarps) {
+      float sacc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < kWarps; ++q) sacc += red[(q * RMAX + k) * 32 + lane];
+      zsh[k * 32 + lane] = sacc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) z[k] = zsh[k * 32 + lane];
+    ++iter;
+
+    // One pass over the owned rows: A z_{k+1}, residual, dual step, then
+    // step 1 and the A^T partial products of the next iteration.
+    const float bn = fminf(a.rho * beta, beta_bar);
+    const float ibn = 1.0f / bn;
+    float rmax = 0.0f;
+#pragma unroll
+    for (int k = 0; k < RMAX; ++k) acc[k] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < SPT; ++s) {
+      const int t = w + kWarps * s;
+      if (t < p) {
+        float ar[RMAX];
+        load_arow<RMAX>(As, t, ar);
+        float az = 0.0f;
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k) az = fmaf(ar[k], z[k], az);
+        const float res = x[s] - az - e[s];
+        rmax = fmaxf(rmax, fabsf(res));
+        y[s] = fmaf(beta, res, y[s]);
+        const float u = x[s] - az + y[s] * ibn;
+        e[s] = shrink(u, ibn);
+        const float v = x[s] - e[s] + y[s] * ibn;
+#pragma unroll
+        for (int k = 0; k < RMAX; ++k) acc[k] = fmaf(ar[k], v, acc[k]);
+      }
+    }
+    beta = bn;
+    mxs[w * 32 + lane] = rmax;
+    __syncthreads();
+    float rm = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) rm = fmaxf(rm, mxs[q * 32 + lane]);
+    const bool conv_now = !done && (rm * inv_xinf < a.eps);
+    const bool out_now = conv_now || (!done && iter >= a.max_iter);
+    if (out_now && w == 0) {
+      const int64_t row = a.qidx[j];
+#pragma unroll
+      for (int k = 0; k < RMAX; ++k) {
+        if (k < a.r) {
+          const float sc = a.scale ? a.scale[k] : 1.0f;
+          a.Z[row + k * a.ldz] = (k < reff) ? z[k] * sc : 0.0f;
+        }
+      }
+      if (a.iters_out) a.iters_out[j] = conv_now ? iter : -iter;
+    }
+    done = done || out_now;
+    if (__syncthreads_and(done)) break;
+  }
+}
+
+template <int SPT, int RMAX>
+size_t adm_smem_bytes() {
+  return sizeof(float) * ((size_t)kWarps * SPT * RMAX +
+                          (size_t)kWarps * RMAX * 32 + (size_t)RMAX * 32 +
+                          (size_t)kWarps * 32);
+}
+
+template <int SPT, int RMAX>
+cudaError_t launch_adm(const FilterArgs& a, cudaStream_t st) {
+  const size_t smem = adm_smem_bytes<SPT, RMAX>();
+  static bool configured = false;  // per process; attribute is per function
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(
+        adm_f32_kernel<SPT, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int grid = (a.N + 31) / 32;
+  adm_f32_kernel<SPT, RMAX><<<grid, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int SPT>
+cudaError_t dispatch_r(const FilterArgs& a, cudaStream_t st) {
+  if (a.r <= 8) return launch_adm<SPT, 8>(a, st);
+  if (a.r <= 16) return launch_adm<SPT, 16>(a, st);
+  if (a.r <= 24) return launch_adm<SPT, 24>(a, st);
+  if (a.r <= 32) return launch_adm<SPT, 32>(a, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+}  // namespace pcp
+
+extern "C" pcp_status pcp_l1_filter(
+    const float* dM, const int32_t* d_pidx, int32_t p, int64_t sp,
+    const int32_t* d_qidx, int32_t N, int64_t sq, const float* dA, int32_t lda,
+    int32_t r, const int32_t* d_rank, const float* d_scale, float* dZ,
+    int64_t ldz, double eps, double rho, double beta0_scale,
+    double beta_bar_ratio, int32_t max_iter, int32_t precision,
+    int32_t refine_iters, int32_t* d_iters, void* stream) {
+  (void)refine_iters;
+  PCP_ARG(p >= 1 && p <= 256, "pcp_l1_filter: p=%d outside [1, 256]", p);
+  PCP_ARG(r >= 1 && r <= 32, "pcp_l1_filter: r=%d outside [1, 32]", r);
+  PCP_ARG(N >= 0, "pcp_l1_filter: N=%d < 0", N);
+  PCP_ARG(lda >= p, "pcp_l1_filter: lda=%d < p=%d", lda, p);
+  PCP_ARG(ldz >= 1, "pcp_l1_filter: ldz < 1");
+  PCP_ARG(eps > 0 && rho > 1 && beta0_scale > 0 && beta_bar_ratio >= 1,
+          "pcp_l1_filter: need eps > 0, rho > 1, beta0_scale > 0, "
+          "beta_bar_ratio >= 1");
+  PCP_ARG(max_iter >= 1, "pcp_l1_filter: max_iter < 1");
+  PCP_ARG(precision == PCP_FP32 || precision == PCP_BF16_REFINED,
+          "pcp_l1_filter: unknown precision %d", precision);
+  if (precision != PCP_FP32) {
+    pcp::set_error("pcp_l1_filter: precision %d not built", precision);
+    return PCP_ERR_UNSUPPORTED;
+  }
+  if (N == 0) return PCP_OK;
+  PCP_ARG(dM && d_pidx && d_qidx && dA && dZ, "pcp_l1_filter: null pointer");
+  pcp::FilterArgs a;
+  a.M = dM;
+  a.pidx = d_pidx;
+  a.p = p;
+  a.sp = sp;
+  a.qidx = d_qidx;
+  a.N = N;
+  a.sq = sq;
+  a.A = dA;
+  a.lda = lda;
+  a.r = r;
+  a.d_rank = d_rank;
+  a.scale = d_scale;
+  a.Z = dZ;
+  a.ldz = ldz;
+  a.eps = (float)eps;
+  a.rho = (float)rho;
+  a.beta0_scale = (float)beta0_scale;
+  a.beta_bar_ratio = (float)beta_bar_ratio;
+  a.max_iter = max_iter;
+  a.iters_out = d_iters;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (p <= 64)
+    e = pcp::dispatch_r<8>(a, st);
+  else if (p <= 128)
+    e = pcp::dispatch_r<16>(a, st);
+  else
+    e = pcp::dispatch_r<32>(a, st);
+  if (e != cudaSuccess)
+    return pcp::cuda_fail(e, "adm_f32_kernel launch", __FILE__, __LINE__);
+  return PCP_OK;
+}

@@ -1,0 +1,86 @@
+"""The C ABI library loads and exports every entry point include/*.h declares.
+
+CPU only: no compute call is made (there is no GPU here); only pure host
+entry points (parameter defaults, version, workspace sizing, argument
+validation before any device work) are exercised.
+"""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1108_5359_gb300 import build, _abi
+    build.build()
+    return _abi.load()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(pcp_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "pcp_l1filter_solve" in names and "pcp_spass" in names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_python_prototypes_cover_header():
+    from paper_1108_5359_gb300 import _abi
+    assert _declared() == set(_abi.PROTOTYPES)
+
+
+def test_params_default_values(lib):
+    from paper_1108_5359_gb300 import pcp_params_default
+    p = pcp_params_default(5000, 5000, 20)
+    assert (p.m, p.n, p.r) == (5000, 5000, 20)
+    assert p.s_r == 10.0 and p.s_c == 10.0      # Section 3.1
+    assert p.seed_tol == 1e-7                   # Section 4.1.1
+    assert p.filter_rho > 1 and p.filter_tol > 0  # Algorithm 1 constraints
+    assert lib.pcp_params_default(None, 1, 1, 1) == -1
+
+
+def test_version_and_workspace(lib):
+    assert b"sm_103a" in lib.pcp_version()
+    assert lib.pcp_seed_workspace_bytes(200, 200, 52) > 4 * 200 * 200 * 8
+    assert lib.pcp_seed_workspace_bytes(0, 200, 52) == 0
+
+
+def test_plan_rejects_bad_arguments_without_gpu(lib):
+    # validation happens before any device call
+    from paper_1108_5359_gb300 import _abi, pcp_params_default
+    p = pcp_params_default(100, 100, 0)
+    h = C.c_void_p()
+    assert lib.pcp_l1filter_plan(C.byref(p), C.byref(h)) == _abi.PCP_ERR_ARG
+    assert b"r=0" in lib.pcp_last_error()
+    p = pcp_params_default(100, 100, 20)   # seed 200 x 200 > 100 x 100
+    assert lib.pcp_l1filter_plan(C.byref(p), C.byref(h)) == _abi.PCP_ERR_ARG
+    p = pcp_params_default(1000, 1000, 5)
+    bad = (C.c_int64 * 50)(*([3] * 50))     # repeated index
+    p.seed_rows = C.cast(bad, C.POINTER(C.c_int64))
+    assert lib.pcp_l1filter_plan(C.byref(p), C.byref(h)) == _abi.PCP_ERR_ARG
+    assert b"repeated" in lib.pcp_last_error()
+
+
+def test_stage_entry_points_validate_sizes(lib):
+    from paper_1108_5359_gb300 import _abi
+    # p out of range -> PCP_ERR_ARG before any launch
+    st = lib.pcp_l1_filter(None, None, 0, 1, None, 4, 1, None, 1, 4, None,
+                           None, None, 1, 1e-6, 1.5, 1.0, 1e10, 10, 0, 0,
+                           None, None)
+    assert st == _abi.PCP_ERR_ARG
+    st = lib.pcp_spass(None, 1, None, 1, None, 1, 100, None, 1, 1, 1, None)
+    assert st == _abi.PCP_ERR_ARG
