@@ -178,14 +178,14 @@ def l1_filter_pcp(M, rows, cols, r=None, seed_tol=1e-7, lam_seed=None,
     if lam_seed is None:
         lam_seed = 1.0 / math.sqrt(max(mp, np_))
     seed = inexact_alm_pcp(Ms, lam_seed, tol=seed_tol, **seed_kw)
-    rk = numerical_rank(seed.sigma, rank_cut)
-    if r is not None:
-        rk = min(rk, int(r))
+    rk_raw = numerical_rank(seed.sigma, rank_cut)
+    rk = rk_raw if r is None else min(rk_raw, int(r))
     order = np.argsort(-seed.sigma)[:rk]
     U = seed.U[:, order]
     sigma = seed.sigma[order]
     V = seed.V[:, order]
-    ok = rank_test(mp, np_, rk, s_r, s_c)
+    # Eq. rank_test on the seed's own numerical rank (before the cap at r)
+    ok = rank_test(mp, np_, rk_raw, s_r, s_c)
     rbar = np.setdiff1d(np.arange(m), rows)
     cbar = np.setdiff1d(np.arange(n), cols)
     # step 3: column filtering, M^c = U^s Q~ + S^c (Eq. l1c')
