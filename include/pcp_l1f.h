@@ -199,6 +199,22 @@ pcp_status pcp_seed_pcp(const double* dD, int32_t mp, int32_t np,
                         double* dSigma, double* dV, int32_t* h_rank,
                         int32_t* h_iters, double* h_residual, void* stream);
 
+/* Tracing of the seed stage: copy block 0's phase records of the last seed
+ * solve that ran in d_work (pcp_seed_pcp's workspace) into h_out, up to
+ * `cap` records of two uint64 each: (globaltimer ns, phase code).  Phase
+ * codes: 1 prologue norms, 2 T = G^T Omega, 3 Gram of T, 4 Cholesky QR of T,
+ * 5 P = G Psi, 6 Gram of P, 7 power-step orthonormalisation, 8 Jacobi
+ * eigen-solve, 9 rotation to Ritz vectors, 10 ALM start, 11 ALM update,
+ * 12 set-up of the eigen-solve.
+ * Synchronises `stream`.  Returns the number of records, -1 on error. */
+int32_t pcp_seed_trace(const void* d_work, int32_t mp, int32_t np,
+                       int32_t kmax, uint64_t* h_out, int32_t cap,
+                       void* stream);
+
+/* Same for the seed stage of the last pcp_l1filter_solve on this plan. */
+int32_t pcp_plan_seed_trace(const pcp_plan* plan, uint64_t* h_out,
+                            int32_t cap, void* stream);
+
 /* Stage 3/4: Algorithm 1 on N independent problems (columns or rows of M),
  * FP32.  Problem j reads its p entries x_j[t] = dM[pidx[t]*sp + qidx[j]*sq]
  * (column problems: pidx = I_s, sp = 1, qidx = ~J_s, sq = ldm; row problems:

@@ -22,7 +22,8 @@ __all__ = [
     "colmajor", "pcp_params_default", "pcp_l1filter_plan",
     "pcp_l1filter_solve", "pcp_plan_destroy", "pcp_gather_seed",
     "pcp_seed_workspace_bytes", "pcp_seed_pcp", "pcp_l1_filter",
-    "pcp_assemble_factors", "pcp_spass", "Plan", "solve", "load",
+    "pcp_assemble_factors", "pcp_spass", "pcp_plan_seed_trace", "Plan",
+    "solve", "load", "SEED_PHASES",
 ]
 
 
@@ -166,6 +167,24 @@ def pcp_seed_pcp(D, lam, tol, rho, mu_scale, mu_max_ratio, max_iter, k0, kmax,
     if raise_on_error:
         check(st, "pcp_seed_pcp")
     return st, rank.value, iters.value, resid.value
+
+
+def pcp_plan_seed_trace(plan, cap=4096, stream=None):
+    """(timestamp_ns, phase) records of the plan's last seed solve."""
+    import numpy as np
+    buf = np.zeros(2 * cap, dtype=np.uint64)
+    n = load().pcp_plan_seed_trace(plan.handle,
+                                   buf.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                   cap, _stream(stream))
+    if n < 0:
+        raise PCPError(n, "pcp_plan_seed_trace failed")
+    return buf[:2 * n].reshape(n, 2)
+
+
+SEED_PHASES = {1: "prologue", 2: "T=G^T Omega", 3: "gram(T)", 4: "cholqr(T)",
+               5: "P=G Psi", 6: "gram(P)", 7: "power orth", 8: "jacobi",
+               9: "rotate", 10: "alm start", 11: "alm update",
+               12: "jacobi setup"}
 
 
 def pcp_l1_filter(M, d_pidx, sp, d_qidx, sq, A, r, Z, ldz, eps, rho,

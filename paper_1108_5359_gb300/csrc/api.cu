@@ -217,7 +217,7 @@ extern "C" pcp_status pcp_l1filter_plan(const pcp_params* params,
   int k0 = q.seed_subspace > 0 ? q.seed_subspace
                                : q.r + std::max(6, q.r / 4);
   k0 = (k0 + 1) / 2 * 2;
-  const int kcap = std::min(std::min(mp, np) / 2 * 2, 96);
+  const int kcap = std::min(std::min(mp, np) / 2 * 2, 64);
   k0 = std::min(k0, kcap);
   P->k0 = k0;
   P->kmax = std::min(kcap, std::max(k0 + 16, 2 * k0) / 2 * 2);
@@ -475,4 +475,11 @@ extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
     return PCP_ERR_FILTER_NOCONV;
   }
   return PCP_OK;
+}
+
+extern "C" int32_t pcp_plan_seed_trace(const pcp_plan* P, uint64_t* h_out,
+                                       int32_t cap, void* stream) {
+  if (!P) return -1;
+  return pcp_seed_trace(P->d_seed_work, P->mp, P->np, P->kmax, h_out, cap,
+                        stream);
 }

@@ -11,22 +11,30 @@
 //
 // The SVT needs only the singular triplets above 1/mu.  They come from a
 // warm-started subspace iteration with Rayleigh-Ritz on G = D - S + Y/mu:
-//   T = G^T Omega,  Psi = orth(T),  P = G Psi,  C = P^T P = Vb diag(s^2) Vb^T,
-//   SVT(G Psi Psi^T) = (P Vb) diag(max(1 - tau/s, 0)) (Psi Vb)^T,
-//   Omega_next = P Vb diag(1/s)  (the left Ritz vectors),
+//   T = G^T Omega,  Psi = orth(T),  P = G Psi,  C = P^T P ~ V diag(s^2) V^T,
+//   Pt = P V,  s_c^2 = ||Pt e_c||^2 (FP64 Rayleigh quotients),
+//   SVT(G Psi Psi^T) = Pt diag(max(1 - tau/s, 0)) (Psi V)^T,
+//   Omega_next = Pt diag(1/s)  (the left Ritz vectors),
 // where orth() is a column-normalised Cholesky QR.  The subspace size k
 // starts at k0 and grows while every Ritz value exceeds tau.  At the exit
-// the skinny SVD of L^s is read off directly: U^s = P Vb diag(1/s),
-// Sigma^s = s - tau, V^s = Psi Vb (Section 3.2 uses exactly these factors).
+// the skinny SVD of L^s is read off directly: U^s = Pt diag(1/s),
+// Sigma^s = s - tau, V^s = Psi V (Section 3.2 uses exactly these factors).
+//
+// Precision: D, S, Y, G, every product and the Ritz values are FP64.  The
+// k x k rotation V that diagonalises the Rayleigh-Ritz matrix is found by a
+// Jacobi eigen-solve in FP32 (the matrix is scaled to unit diagonal maximum
+// first); V enters the FP64 products as exact FP64 numbers, so the only
+// effect of its FP32 accuracy is a ~1e-7 loss of orthogonality of the
+// rotated bases, well below the ALM tolerance.
 //
 // GB300 form: one cooperative persistent launch (grid = one CTA per SM) runs
 // the whole ALM loop.  Phases are separated by a software grid barrier whose
 // spin is bounded by %globaltimer (on expiry every CTA sets an error word and
 // returns).  The m' x n' state (S, Y, G and G^T) stays in L2.  Small k x k
-// factorisations (Cholesky, Jacobi eigen-solve) run redundantly in every CTA
-// so that they need no barrier; their inputs and code are identical, so
-// every CTA obtains bit-identical factors.  All cross-CTA data is read with
-// L2-only loads (ld.global.cg) so no CTA sees a stale L1 line.
+// factorisations (Cholesky, Jacobi) run redundantly in every CTA so that
+// they need no barrier; inputs and code are identical, so every CTA obtains
+// bit-identical factors.  Cross-CTA data is read with L2-only loads
+// (ld.global.cg) so no CTA sees a stale L1 line.
 #include <algorithm>
 
 #include "common.cuh"
@@ -34,7 +42,8 @@
 namespace pcp {
 
 constexpr int kSeedThreads = 256;
-constexpr int kSeedKmaxLimit = 96;
+constexpr int kSeedKmaxLimit = 64;
+constexpr int kSeedTraceCap = 4096;  // (timestamp, phase) records
 
 struct SeedCtl {
   unsigned int bar_count;
@@ -45,16 +54,20 @@ struct SeedCtl {
   int converged;
   int k_final;
   int rank_raw;
+  int ntrace;
+  int jsweeps;     // total Jacobi sweeps (block 0), for tracing
+  long long jcyc[4];  // block 0 Jacobi cycles: angles, A, V, end-of-round
   double residual;
   double sigma1;
   double pad[4];
 };
 
 struct SeedLayout {
-  size_t ctl, part, S, Y, G, Gt, Om, P, Pt, T, Psi, PsiT, Gam, total;
+  size_t ctl, part, colsq, S, Y, G, Gt, Om, P, Pt, T, Psi, PsiT, Gam, Gam2,
+      trace, total;
 };
 
-static SeedLayout seed_layout(int mp, int np, int kmax) {
+SeedLayout seed_layout(int mp, int np, int kmax) {
   SeedLayout L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -65,6 +78,7 @@ static SeedLayout seed_layout(int mp, int np, int kmax) {
   const size_t mn = (size_t)mp * np * sizeof(double);
   L.ctl = take(sizeof(SeedCtl));
   L.part = take((size_t)kMaxCoopBlocks * 4 * sizeof(double));
+  L.colsq = take((size_t)kMaxCoopBlocks * kmax * sizeof(double));
   L.S = take(mn);
   L.Y = take(mn);
   L.G = take(mn);
@@ -76,6 +90,8 @@ static SeedLayout seed_layout(int mp, int np, int kmax) {
   L.Psi = take((size_t)np * kmax * sizeof(double));
   L.PsiT = take((size_t)np * kmax * sizeof(double));
   L.Gam = take((size_t)kmax * kmax * sizeof(double));
+  L.Gam2 = take((size_t)kmax * kmax * sizeof(double));
+  L.trace = take((size_t)kSeedTraceCap * 2 * sizeof(unsigned long long));
   L.total = off;
   return L;
 }
@@ -94,10 +110,13 @@ struct SeedArgs {
   unsigned long long timeout_ns;
   SeedCtl* ctl;
   double* part;
+  double* colsq;           // [block][kmax] partial column sums of Pt^2
   double *S, *Y, *G, *Gt;
-  double *Om, *P, *Pt;  // mp x kmax, row-major (row stride kmax)
+  double *Om, *P, *Pt;     // mp x kmax, row-major (row stride kmax)
   double *T, *Psi, *PsiT;  // np x kmax, row-major
   double* Gam;             // kmax x kmax
+  double* Gam2;            // kmax x kmax: Psi1^T Psi1
+  unsigned long long* trace;  // block 0's phase timestamps
   double *U, *Sigma, *V;   // outputs (column-major, ld mp / np)
 };
 
@@ -127,7 +146,7 @@ __device__ bool grid_sync(SeedCtl* ctl, unsigned int nblocks,
           atomicExch(&ctl->error, (int)PCP_ERR_TIMEOUT);
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     __threadfence();
@@ -135,6 +154,18 @@ __device__ bool grid_sync(SeedCtl* ctl, unsigned int nblocks,
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Block 0 records (globaltimer, phase) after the phase ends.
+__device__ __forceinline__ void trace_mark(const SeedArgs& a, int phase) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int i = a.ctl->ntrace;
+    if (i < kSeedTraceCap) {
+      a.trace[2 * i] = globaltimer_ns();
+      a.trace[2 * i + 1] = (unsigned long long)phase;
+      a.ctl->ntrace = i + 1;
+    }
+  }
 }
 
 // Deterministic N(0,1) from a counter (splitmix64 + Box-Muller).
@@ -152,20 +183,68 @@ __device__ double hash_normal(unsigned long long a, unsigned long long b) {
   return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
 }
 
+// Fixed-order (deterministic) block reduction of v over all threads.
+__device__ double block_reduce_sum(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int q = 0; q < kSeedThreads / 32; ++q) s += red[q];
+  __syncthreads();
+  return s;
+}
+
+__device__ double block_reduce_max(double v, double* red) {
+  v = warp_max(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int q = 0; q < kSeedThreads / 32; ++q) s = fmax(s, red[q]);
+  __syncthreads();
+  return s;
+}
+
+// sum over blocks q < nb of src[q * stride + off]; every thread gets it.
+__device__ double sum_partials(const double* src, int nb, int stride, int off,
+                               double* red) {
+  double acc = 0.0;
+  for (int q = threadIdx.x; q < nb; q += kSeedThreads)
+    acc += ldg_cg(src + (size_t)q * stride + off);
+  return block_reduce_sum(acc, red);
+}
+
 // out[task*kmax + c] = sum_t X[t + task*ldx] * B[t*kmax + c], c < k.
+// The task's column of X is staged in shared memory; each thread owns one
+// c and a slice of t, with four independent accumulators so that its
+// loads of B overlap.
 __device__ void tall_gemm_t(const double* X, int ldx, int len, int ntask,
                             const double* B, int k, int kmax, double* out,
-                            double* red) {
+                            double* red, double* xs) {
   const int tid = threadIdx.x;
   const int nparts = kSeedThreads / k;
   const int c = tid % k, part = tid / k;
   for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
     const double* x = X + (size_t)task * ldx;
-    double acc = 0.0;
+    for (int t = tid; t < len; t += kSeedThreads) xs[t] = ldg_cg(x + t);
+    __syncthreads();
     if (part < nparts) {
-      for (int t = part; t < len; t += nparts)
-        acc = fma(ldg_cg(x + t), ldg_cg(B + (size_t)t * kmax + c), acc);
-      red[part * k + c] = acc;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int t = part;
+      for (; t + 3 * nparts < len; t += 4 * nparts) {
+        const double b0 = ldg_cg(B + (size_t)t * kmax + c);
+        const double b1 = ldg_cg(B + (size_t)(t + nparts) * kmax + c);
+        const double b2 = ldg_cg(B + (size_t)(t + 2 * nparts) * kmax + c);
+        const double b3 = ldg_cg(B + (size_t)(t + 3 * nparts) * kmax + c);
+        a0 = fma(xs[t], b0, a0);
+        a1 = fma(xs[t + nparts], b1, a1);
+        a2 = fma(xs[t + 2 * nparts], b2, a2);
+        a3 = fma(xs[t + 3 * nparts], b3, a3);
+      }
+      for (; t < len; t += nparts)
+        a0 = fma(xs[t], ldg_cg(B + (size_t)t * kmax + c), a0);
+      red[part * k + c] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
     if (tid < k) {
@@ -184,14 +263,29 @@ __device__ void gram(const double* X, int nrows, int k, int kmax,
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (kSeedThreads / 32) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (kSeedThreads / 32);
-  for (int pq = gw; pq < k * k; pq += nw) {
-    const int a = pq / k, b = pq - a * k;
-    if (a > b) continue;
-    double s = 0.0;
-    for (int t = lane; t < nrows; t += 32)
-      s = fma(ldg_cg(X + (size_t)t * kmax + a), ldg_cg(X + (size_t)t * kmax + b),
-              s);
-    s = warp_sum(s);
+  const int npairs = k * (k + 1) / 2;
+  for (int pq = gw; pq < npairs; pq += nw) {
+    // pq -> (a, b) with a <= b, row-major over the upper triangle
+    int a = 0, rem = pq;
+    while (rem >= k - a) {
+      rem -= k - a;
+      ++a;
+    }
+    const int b = a + rem;
+    double s0 = 0.0, s1 = 0.0;
+    int t = lane;
+    for (; t + 32 < nrows; t += 64) {
+      const double x0 = ldg_cg(X + (size_t)t * kmax + a);
+      const double y0 = ldg_cg(X + (size_t)t * kmax + b);
+      const double x1 = ldg_cg(X + (size_t)(t + 32) * kmax + a);
+      const double y1 = ldg_cg(X + (size_t)(t + 32) * kmax + b);
+      s0 = fma(x0, y0, s0);
+      s1 = fma(x1, y1, s1);
+    }
+    for (; t < nrows; t += 32)
+      s0 = fma(ldg_cg(X + (size_t)t * kmax + a),
+               ldg_cg(X + (size_t)t * kmax + b), s0);
+    const double s = warp_sum(s0 + s1);
     if (lane == 0) {
       __stcg(Gm + a * kmax + b, s);
       __stcg(Gm + b * kmax + a, s);
@@ -200,12 +294,19 @@ __device__ void gram(const double* X, int nrows, int k, int kmax,
 }
 
 // Column-normalised Cholesky QR: Out = X diag(1/||x_a||) R^{-1} with
-// R^T R = diag(1/||x_a||) X^T X diag(1/||x_a||).  Columns whose norm or
-// pivot vanishes are dead and come out zero.  A, Ri: k x k shared buffers.
+// R^T R = diag(1/||x_a||) X^T X diag(1/||x_a||) (unit diagonal, well
+// conditioned).  The k x k Cholesky factor and its inverse are computed in
+// FP32 (FP64 latency on this part is ~64 cycles per dependent FMA and ~650
+// per divide or square root); the row products X R^{-1} run in FP64 with
+// those FP32 values.  The result is orthonormal to ~1e-7, which the ALM
+// absorbs (tested against the full-SVD FP64 oracle).  Columns whose norm or
+// pivot vanishes are dead and come out zero.  A32: k x k shared; Ri32: k.
 __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
-                             const double* Gm, double* Out, double* A,
-                             double* Ri, double* dsc, int* dead) {
+                             const double* Gm, double* Out, float* A32,
+                             float* Ri32, double* dsc, int* dead,
+                             double* rowb) {
   const int tid = threadIdx.x;
+  __shared__ float s_inv[2];
   for (int c = tid; c < k; c += kSeedThreads) {
     const double g = ldg_cg(Gm + c * kmax + c);
     dead[c] = !(g > 0.0);
@@ -214,152 +315,192 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
   __syncthreads();
   for (int idx = tid; idx < k * k; idx += kSeedThreads) {
     const int a = idx / k, b = idx - a * k;
-    double v = ldg_cg(Gm + a * kmax + b) * dsc[a] * dsc[b];
-    if (dead[a] || dead[b]) v = (a == b) ? 1.0 : 0.0;
-    A[idx] = v;
-    Ri[idx] = 0.0;
+    float v = (float)(ldg_cg(Gm + a * kmax + b) * dsc[a] * dsc[b]);
+    if (dead[a] || dead[b]) v = (a == b) ? 1.0f : 0.0f;
+    A32[idx] = v;
   }
-  __syncthreads();
-  // right-looking Cholesky, R stored in the upper triangle of A
+  // Right-looking Cholesky, R in the upper triangle.  Step j's trailing
+  // update reads row j unscaled (times 1/pivot^2); row j is scaled at the
+  // start of step j+1.  The reciprocal alternates between two slots so step
+  // j+1's pivot never overwrites the value step j's scaling still reads.
   for (int j = 0; j < k; ++j) {
-    __shared__ double s_piv;
+    __syncthreads();
+    if (j > 0) {
+      const float inv = s_inv[(j - 1) & 1];
+      for (int c = j + tid; c < k; c += kSeedThreads) A32[(j - 1) * k + c] *= inv;
+    }
     if (tid == 0) {
-      double piv = A[j * k + j];
-      if (!(piv > 1e-13) || dead[j]) {
+      const float piv = A32[j * k + j];
+      if (!(piv > 1e-6f) || dead[j]) {
         dead[j] = 1;
-        piv = 1.0;
+        s_inv[j & 1] = 0.0f;
+        A32[j * k + j] = 1.0f;
       } else {
-        piv = sqrt(piv);
+        const float rs = rsqrtf(piv);
+        s_inv[j & 1] = rs;
+        A32[j * k + j] = piv * rs;
       }
-      s_piv = piv;
     }
     __syncthreads();
-    const double piv = s_piv;
-    const bool dj = dead[j];
-    for (int c = j + 1 + tid; c < k; c += kSeedThreads)
-      A[j * k + c] = dj ? 0.0 : A[j * k + c] / piv;
-    if (tid == 0) A[j * k + j] = piv;
-    __syncthreads();
+    const float inv2 = s_inv[j & 1] * s_inv[j & 1];
     const int rem = k - j - 1;
     for (int idx = tid; idx < rem * rem; idx += kSeedThreads) {
       const int a = j + 1 + idx / rem, b = j + 1 + idx % rem;
-      if (a <= b) A[a * k + b] -= A[j * k + a] * A[j * k + b];
-    }
-    __syncthreads();
-  }
-  // Ri = R^{-1} (upper triangular), one column per thread
-  for (int c = tid; c < k; c += kSeedThreads) {
-    Ri[c * k + c] = 1.0 / A[c * k + c];
-    for (int a = c - 1; a >= 0; --a) {
-      double s = 0.0;
-      for (int b = a + 1; b <= c; ++b) s = fma(A[a * k + b], Ri[b * k + c], s);
-      Ri[a * k + c] = -s / A[a * k + a];
+      if (a <= b) A32[a * k + b] -= A32[j * k + a] * A32[j * k + b] * inv2;
     }
   }
   __syncthreads();
-  // rows of the output, distributed over the grid
-  for (int t = blockIdx.x; t < nrows; t += gridDim.x) {
-    for (int c = tid; c < k; c += kSeedThreads) {
-      double s = 0.0;
-      if (!dead[c])
-        for (int a = 0; a <= c; ++a)
-          s = fma(ldg_cg(X + (size_t)t * kmax + a) * dsc[a], Ri[a * k + c], s);
-      __stcg(Out + (size_t)t * kmax + c, s);
+  // Reciprocal pivots, then one warp per output row solves x R = t~ by
+  // forward substitution (lane c owns columns c and c + 32).  The row data
+  // and the arithmetic are FP64; R and its reciprocal pivots are the FP32
+  // factor's values.  Keeping t~ in FP64 matters: rounding it to FP32
+  // perturbs the directions near the threshold enough to slow the ALM.
+  for (int c = tid; c < k; c += kSeedThreads) Ri32[c] = 1.0f / A32[c * k + c];
+  __syncthreads();
+  const int lane = tid & 31;
+  const int gw = blockIdx.x * (kSeedThreads / 32) + (tid >> 5);
+  const int nw = gridDim.x * (kSeedThreads / 32);
+  for (int t = gw; t < nrows; t += nw) {
+    const int c0 = lane, c1 = lane + 32;
+    double p0 = c0 < k ? ldg_cg(X + (size_t)t * kmax + c0) * dsc[c0] : 0.0;
+    double p1 = c1 < k ? ldg_cg(X + (size_t)t * kmax + c1) * dsc[c1] : 0.0;
+    double o0 = 0.0, o1 = 0.0;
+    for (int j = 0; j < k; ++j) {
+      const int owner = j & 31;
+      const double mine = (j < 32) ? p0 : p1;
+      double xj = __shfl_sync(0xffffffffu, mine * (double)Ri32[j], owner);
+      if (dead[j]) xj = 0.0;
+      if (lane == owner) {
+        if (j < 32) o0 = xj; else o1 = xj;
+      }
+      if (c0 > j && c0 < k) p0 = fma(-xj, (double)A32[j * k + c0], p0);
+      if (c1 > j && c1 < k) p1 = fma(-xj, (double)A32[j * k + c1], p1);
     }
+    if (c0 < k) __stcg(Out + (size_t)t * kmax + c0, o0);
+    if (c1 < k) __stcg(Out + (size_t)t * kmax + c1, o1);
   }
 }
 
-// Cyclic Jacobi eigen-decomposition of the symmetric k x k matrix in A
-// (k even), parallel (round-robin) ordering.  On return A's diagonal holds
-// the eigenvalues and V the eigenvectors (columns).  Every CTA runs it on
-// the same data and gets the same bits.
-__device__ void block_jacobi(double* A, double* V, int k, double* cs,
-                             int* prs) {
+// Rotation (c, s) that zeroes a_pq of the symmetric 2 x 2 block
+// [[app, apq], [apq, aqq]] (A' = J^T A J with J = [[c, s], [-s, c]]); the
+// identity when a_pq is at the FP32 noise floor (2 ulp of the unit largest
+// diagonal) or negligible against its own diagonal.
+// Branch-free, built from the fast reciprocal / reciprocal-square-root
+// units: the angle only has to be accurate to a few ulp (an inexact
+// rotation is still orthogonal to FP32 precision and the next sweep removes
+// what it leaves).
+__device__ __forceinline__ bool jacobi_angle(float app, float aqq, float apq,
+                                             float& c, float& s) {
+  const float mag = fabsf(apq);
+  const bool rot = (mag * mag > 1e-14f * fabsf(app * aqq)) && (mag > 2.4e-7f);
+  const float den = rot ? 2.0f * apq : 1.0f;
+  const float theta = __fdividef(aqq - app, den);
+  const float u = fmaf(theta, theta, 1.0f);
+  const float t = __fdividef(copysignf(1.0f, theta),
+                             fabsf(theta) + u * rsqrtf(u));
+  const float cc = rsqrtf(fmaf(t, t, 1.0f));
+  c = rot ? cc : 1.0f;
+  s = rot ? t * cc : 0.0f;
+  return rot;
+}
+
+// Cyclic Jacobi eigen-decomposition (FP32) of the symmetric k x k matrix in
+// A0 (k even, entries scaled to at most 1), parallel round-robin ordering.
+// One barrier per round: every thread owns 2 x 2 blocks (rows of pair i,
+// columns of pair j) and recomputes the two rotations it needs from the
+// current A; it writes the rotated block of A into the other buffer and
+// rotates its block of V (columns of pair j) in place.  Returns the buffer
+// holding the final A (diagonal = eigenvalues); V's columns are the
+// eigenvectors.
+__device__ float* block_jacobi32(float* A0, float* A1, float* V, int k,
+                                 unsigned char* tab, int max_sweeps,
+                                 int* sweeps_out, long long* cyc) {
   const int tid = threadIdx.x;
-  __shared__ int s_rot;
-  __shared__ double s_thr;
-  for (int idx = tid; idx < k * k; idx += kSeedThreads)
-    V[idx] = (idx / k == idx % k) ? 1.0 : 0.0;
-  if (tid == 0) {
-    double dmax = 0.0;
-    for (int i = 0; i < k; ++i) dmax = fmax(dmax, fabs(A[i * k + i]));
-    s_thr = 1e-15 * dmax;
+  // round-robin schedule: tab[round*k + x] = position of slot x (slot 0
+  // fixed, the others rotate); pair i is (slot i, slot k-1-i)
+  for (int e = tid; e < (k - 1) * k; e += kSeedThreads) {
+    const int round = e / k, x = e - round * k;
+    tab[e] = (unsigned char)(x == 0 ? 0 : 1 + (x - 1 + round) % (k - 1));
   }
-  __syncthreads();
-  const double thr = s_thr;
+  __shared__ int s_rot[2];
+  const bool prof = cyc && blockIdx.x == 0 && tid == 0;
+  long long c0 = 0;
+  for (int idx = tid; idx < k * k; idx += kSeedThreads)
+    V[idx] = (idx / k == idx % k) ? 1.0f : 0.0f;
   const int half = k / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    if (tid == 0) s_rot = 0;
+  float* A = A0;
+  float* An = A1;
+  int flip = 0;
+  if (tid == 0) s_rot[0] = s_rot[1] = 0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0 && sweeps_out && blockIdx.x == 0) *sweeps_out += 1;
     for (int round = 0; round < k - 1; ++round) {
+      const long long t0 = prof ? clock64() : 0;
       __syncthreads();
-      if (tid < half) {
-        auto pos = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + round) % (k - 1); };
-        int p = pos(tid), q = pos(k - 1 - tid);
-        if (p > q) { const int t = p; p = q; q = t; }
-        const double apq = A[p * k + q];
-        double c = 1.0, s = 0.0;
-        if (fabs(apq) > thr) {
-          const double theta = (A[q * k + q] - A[p * k + p]) / (2.0 * apq);
-          const double t = (theta >= 0.0 ? 1.0 : -1.0) /
-                           (fabs(theta) + sqrt(theta * theta + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
-          s = t * c;
-          s_rot = 1;
-        }
-        cs[2 * tid] = c;
-        cs[2 * tid + 1] = s;
-        prs[2 * tid] = p;
-        prs[2 * tid + 1] = q;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < half * k; idx += kSeedThreads) {
-        const int i = idx / k, x = idx - i * k;
-        const double s = cs[2 * i + 1];
-        if (s != 0.0) {
-          const double c = cs[2 * i];
-          const int p = prs[2 * i], q = prs[2 * i + 1];
-          const double ap = A[p * k + x], aq = A[q * k + x];
-          A[p * k + x] = c * ap - s * aq;
-          A[q * k + x] = s * ap + c * aq;
-        }
-      }
-      __syncthreads();
-      for (int idx = tid; idx < half * k; idx += kSeedThreads) {
-        const int i = idx / k, x = idx - i * k;
-        const double s = cs[2 * i + 1];
-        if (s != 0.0) {
-          const double c = cs[2 * i];
-          const int p = prs[2 * i], q = prs[2 * i + 1];
-          const double ap = A[x * k + p], aq = A[x * k + q];
-          A[x * k + p] = c * ap - s * aq;
-          A[x * k + q] = s * ap + c * aq;
-          const double vp = V[x * k + p], vq = V[x * k + q];
-          V[x * k + p] = c * vp - s * vq;
-          V[x * k + q] = s * vp + c * vq;
+      if (prof) c0 += clock64() - t0;
+      for (int w = tid; w < half * half; w += kSeedThreads) {
+        const int i = w / half, j = w - i * half;
+        const unsigned char* tr = tab + round * k;
+        int pi = tr[i], qi = tr[k - 1 - i];
+        int pj = tr[j], qj = tr[k - 1 - j];
+        if (pi > qi) { const int t = pi; pi = qi; qi = t; }
+        if (pj > qj) { const int t = pj; pj = qj; qj = t; }
+        float ci, si, cj, sj;
+        const bool ri = jacobi_angle(A[pi * k + pi], A[qi * k + qi],
+                                     A[pi * k + qi], ci, si);
+        const bool rj = jacobi_angle(A[pj * k + pj], A[qj * k + qj],
+                                     A[pj * k + qj], cj, sj);
+        if (ri && w == i * half + i) s_rot[flip] = 1;
+        const float b00 = A[pi * k + pj], b01 = A[pi * k + qj];
+        const float b10 = A[qi * k + pj], b11 = A[qi * k + qj];
+        const float r00 = ci * b00 - si * b10, r01 = ci * b01 - si * b11;
+        const float r10 = si * b00 + ci * b10, r11 = si * b01 + ci * b11;
+        An[pi * k + pj] = r00 * cj - r01 * sj;
+        An[pi * k + qj] = r00 * sj + r01 * cj;
+        An[qi * k + pj] = r10 * cj - r11 * sj;
+        An[qi * k + qj] = r10 * sj + r11 * cj;
+        if (rj) {
+          const float v0 = V[pi * k + pj], v1 = V[pi * k + qj];
+          const float v2 = V[qi * k + pj], v3 = V[qi * k + qj];
+          V[pi * k + pj] = cj * v0 - sj * v1;
+          V[pi * k + qj] = sj * v0 + cj * v1;
+          V[qi * k + pj] = cj * v2 - sj * v3;
+          V[qi * k + qj] = sj * v2 + cj * v3;
         }
       }
+      float* t = A;
+      A = An;
+      An = t;
     }
     __syncthreads();
-    if (s_rot == 0) break;
+    const int any = s_rot[flip];
     __syncthreads();
+    if (tid == 0) s_rot[flip] = 0;
+    flip ^= 1;
+    if (!any) break;
   }
+  __syncthreads();
+  (void)c0;
+  return A;
 }
 
-__global__ void __launch_bounds__(kSeedThreads, 1)
+__global__ void __launch_bounds__(kSeedThreads, 2)
     seed_alm_kernel(const SeedArgs a) {
   extern __shared__ __align__(16) double sm[];
   const int kmax = a.kmax;
-  double* A = sm;                       // kmax*kmax
-  double* Vb = A + kmax * kmax;         // kmax*kmax
-  double* red = Vb + kmax * kmax;       // kSeedThreads
-  double* lam = red + kSeedThreads;     // kmax
-  double* dsc = lam + kmax;             // kmax
-  double* xi = dsc + kmax;              // kmax
-  double* cs = xi + kmax;               // kmax (pairs of c,s)
-  int* ibuf = reinterpret_cast<int*>(cs + kmax);  // 2*kmax ints
-  int* dead = ibuf;
+  double* red = sm;                      // kSeedThreads
+  double* xs = red + kSeedThreads;       // 256 (staged column, len <= 256)
+  double* lam = xs + 256;                // kmax (singular values s_c)
+  double* dsc = lam + kmax;              // kmax
+  double* xi = dsc + kmax;               // kmax
+  double* rowb = xi + kmax;              // kmax
+  double* Vd = rowb + kmax;              // kmax*kmax (rotation as FP64)
+  float* J0 = reinterpret_cast<float*>(Vd + kmax * kmax);  // 2 x kmax*kmax
+  float* W0 = J0 + kmax * kmax;          // Jacobi A / V; Cholesky R / R^-1
+  float* cs = W0 + kmax * kmax;          // kmax*kmax floats (Jacobi buffer)
+  int* ibuf = reinterpret_cast<int*>(cs + kmax * kmax);  // 2*kmax ints,
+  int* dead = ibuf;                      // then kmax*kmax bytes (schedule)
   int* prs = ibuf + kmax;
-  __shared__ double s_scalar[8];
 
   const int tid = threadIdx.x;
   const int nb = gridDim.x, b = blockIdx.x;
@@ -381,21 +522,11 @@ __global__ void __launch_bounds__(kSeedThreads, 1)
       const int j = (int)(e / mp), i = (int)(e - (size_t)j * mp);
       __stcg(a.Gt + (size_t)i * np + j, d);
     }
-    ss = warp_sum(ss);
-    mx = warp_max(mx);
-    if ((tid & 31) == 0) {
-      red[tid >> 5] = ss;
-      red[8 + (tid >> 5)] = mx;
-    }
-    __syncthreads();
+    ss = block_reduce_sum(ss, red);
+    mx = block_reduce_max(mx, red);
     if (tid == 0) {
-      double s2 = 0.0, m2 = 0.0;
-      for (int q = 0; q < kSeedThreads / 32; ++q) {
-        s2 += red[q];
-        m2 = fmax(m2, red[8 + q]);
-      }
-      __stcg(a.part + 4 * b, s2);
-      __stcg(a.part + 4 * b + 1, m2);
+      __stcg(a.part + 4 * b, ss);
+      __stcg(a.part + 4 * b + 1, mx);
     }
     for (size_t e = (size_t)b * kSeedThreads + tid; e < (size_t)mp * a.k0;
          e += (size_t)nb * kSeedThreads) {
@@ -404,20 +535,14 @@ __global__ void __launch_bounds__(kSeedThreads, 1)
     }
   }
   if (!grid_sync(ctl, nb, tmo)) return;
-  if (tid == 0) {
-    double s2 = 0.0, m2 = 0.0;
-    for (int q = 0; q < nb; ++q) {
-      s2 += ldg_cg(a.part + 4 * q);
-      m2 = fmax(m2, ldg_cg(a.part + 4 * q + 1));
-    }
-    s_scalar[0] = sqrt(s2);
-    s_scalar[1] = m2;
-  }
-  __syncthreads();
-  const double normF = s_scalar[0];
-  const double norminf = s_scalar[1];
+  trace_mark(a, 1);
+  const double normF = sqrt(sum_partials(a.part, nb, 4, 0, red));
+  double m2 = 0.0;
+  for (int q = tid; q < nb; q += kSeedThreads)
+    m2 = fmax(m2, ldg_cg(a.part + 4 * q + 1));
+  const double norminf = block_reduce_max(m2, red);
   if (!(normF > 0.0)) {
-    // D = 0: L = S = 0, rank 0.
+    // D = 0 (or not finite): L = S = 0, rank 0.
     for (size_t e = (size_t)b * kSeedThreads + tid; e < (size_t)mp * kmax;
          e += (size_t)nb * kSeedThreads)
       a.U[e] = 0.0;
@@ -444,37 +569,198 @@ __global__ void __launch_bounds__(kSeedThreads, 1)
   int stage = 0;        // 0,1: power steps on D; 2: Rayleigh-Ritz on D; 3: ALM
   bool converged = false;
   double res = 1.0;
+  int knext = k;
 
   while (true) {
     // ---- T = G^T Omega ------------------------------------------------------
-    tall_gemm_t(a.G, mp, mp, np, a.Om, k, kmax, a.T, red);
+    tall_gemm_t(a.G, mp, mp, np, a.Om, k, kmax, a.T, red, xs);
     if (!grid_sync(ctl, nb, tmo)) return;
+    trace_mark(a, 2);
     gram(a.T, np, k, kmax, a.Gam);
     if (!grid_sync(ctl, nb, tmo)) return;
-    cholqr_apply(a.T, np, k, kmax, a.Gam, a.Psi, A, Vb, dsc, dead);
+    trace_mark(a, 3);
+    cholqr_apply(a.T, np, k, kmax, a.Gam, a.Psi, J0, W0, dsc, dead, rowb);
     if (!grid_sync(ctl, nb, tmo)) return;
+    trace_mark(a, 4);
     // ---- P = G Psi ------------------------------------------------------------
-    tall_gemm_t(a.Gt, np, np, mp, a.Psi, k, kmax, a.P, red);
+    tall_gemm_t(a.Gt, np, np, mp, a.Psi, k, kmax, a.P, red, xs);
+    if (stage >= 2) gram(a.Psi, np, k, kmax, a.Gam2);  // E = Psi1^T Psi1 - I
     if (!grid_sync(ctl, nb, tmo)) return;
+    trace_mark(a, 5);
     gram(a.P, mp, k, kmax, a.Gam);
     if (!grid_sync(ctl, nb, tmo)) return;
+    trace_mark(a, 6);
     if (stage < 2) {
       // plain power step on D: Omega = orth(P)
-      cholqr_apply(a.P, mp, k, kmax, a.Gam, a.Om, A, Vb, dsc, dead);
+      cholqr_apply(a.P, mp, k, kmax, a.Gam, a.Om, J0, W0, dsc, dead, rowb);
       if (!grid_sync(ctl, nb, tmo)) return;
+      trace_mark(a, 7);
       ++stage;
       continue;
     }
-    // ---- Rayleigh-Ritz: C = P^T P = Vb diag(lam) Vb^T -----------------------
-    for (int idx = tid; idx < k * k; idx += kSeedThreads) {
-      const int p = idx / k, q = idx - p * k;
-      A[idx] = ldg_cg(a.Gam + p * kmax + q);
+    // ---- Rayleigh-Ritz rotation ---------------------------------------------
+    // Psi1 (from the FP32 Cholesky QR) has Psi1^T Psi1 = I + E, |E| ~ 1e-7.
+    // Its first-order orthonormalisation Psi = Psi1 (I - E/2) is never
+    // formed: C = P^T P = C1 - (E C1 + C1 E)/2 and the rotation applied to
+    // P1 and Psi1 is W = (I - E/2) V.  The correction terms are tiny, so
+    // FP32 products are exact enough for them.
+    {
+      float* E32 = W0;  // E, then the Jacobi's V
+      float* C32 = J0;  // C1 / cmax, then the Jacobi's A
+      const long long ts0 = clock64();
+      const double cm = block_reduce_max(
+          tid < k ? ldg_cg(a.Gam + tid * kmax + tid) : 0.0, red);
+      const long long ts1 = clock64();
+      if (b == 0 && tid == 0) ctl->jcyc[0] += ts1 - ts0;
+      for (int idx = tid; idx < k * k; idx += kSeedThreads) {
+        const int p = idx / k, q = idx - p * k;
+        E32[idx] = (float)(ldg_cg(a.Gam2 + p * kmax + q) - (p == q ? 1.0 : 0.0));
+      }
+      __syncthreads();
+      const double inv = cm > 0.0 ? 1.0 / cm : 1.0;
+      for (int idx = tid; idx < k * k; idx += kSeedThreads) {
+        const int p = idx / k, q = idx - p * k;
+        C32[idx] = (float)(ldg_cg(a.Gam + p * kmax + q) * inv);
+      }
+      __syncthreads();
+      // Vd (scratch, FP64 buffer reused as floats): X = E C1n, then
+      // C = C1n - (X + X^T)/2 held in Vd as doubles
+      // X = E C1n and its transpose, four outputs per thread at once
+      for (int base = tid; base < k * k; base += 4 * kSeedThreads) {
+        int pp[4], qq[4];
+        float xs4[4] = {0.f, 0.f, 0.f, 0.f}, ys4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const int idx = min(base + o * kSeedThreads, k * k - 1);
+          pp[o] = idx / k;
+          qq[o] = idx - pp[o] * k;
+        }
+        for (int c = 0; c < k; ++c) {
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            xs4[o] = fmaf(E32[pp[o] * k + c], C32[c * k + qq[o]], xs4[o]);
+            ys4[o] = fmaf(E32[qq[o] * k + c], C32[c * k + pp[o]], ys4[o]);
+          }
+        }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const int idx = base + o * kSeedThreads;
+          if (idx < k * k)
+            Vd[idx] = (double)C32[idx] - 0.5 * ((double)xs4[o] + (double)ys4[o]);
+        }
+      }
+      __syncthreads();
+      for (int idx = tid; idx < k * k; idx += kSeedThreads)
+        C32[idx] = (float)Vd[idx];
+      // keep E (FP32) in Vd as doubles for the W correction after Jacobi
+      for (int idx = tid; idx < k * k; idx += kSeedThreads)
+        Vd[idx] = (double)E32[idx];
+      __syncthreads();
+      if (b == 0 && tid == 0) ctl->jcyc[3] += clock64() - ts0;
+      trace_mark(a, 12);
+      // the Jacobi needs a second k x k float buffer: the rotation buffer
+      // cs..cs+k*k (see the shared-memory map)
+      const long long tj0 = clock64();
+      // Far from convergence one sweep per ALM iteration is enough: the Ritz
+      // basis is carried to the next iteration (Omega_next = Pt / s), so the
+      // diagonalisation keeps improving.  Near convergence (residual below
+      // 1e-5) and on the first Rayleigh-Ritz the sweeps run to completion so
+      // the returned factors are orthonormal to FP32 accuracy.
+      const int max_sweeps = (stage == 2 || res < 1e-5) ? 30 : 1;
+      float* Afin = block_jacobi32(C32, cs, W0, k,
+                                   reinterpret_cast<unsigned char*>(prs + kmax),
+                                   max_sweeps, &ctl->jsweeps, ctl->jcyc);
+      (void)Afin;
+      const long long tj1 = clock64();
+      if (b == 0 && tid == 0) ctl->jcyc[1] += tj1 - tj0;
+      // W = V - (E/2) V (E in Vd as doubles, V in W0), written to J0,
+      // which the Jacobi no longer needs, then widened into Vd
+      for (int idx = tid; idx < k * k; idx += kSeedThreads)
+        cs[idx] = (float)Vd[idx];  // E as floats (cs is free after the Jacobi
+                                   // unless it holds the final A, unused)
+      __syncthreads();
+      for (int base = tid; base < k * k; base += 4 * kSeedThreads) {
+        int pp[4], qq[4];
+        float xs4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const int idx = min(base + o * kSeedThreads, k * k - 1);
+          pp[o] = idx / k;
+          qq[o] = idx - pp[o] * k;
+        }
+        for (int c = 0; c < k; ++c) {
+#pragma unroll
+          for (int o = 0; o < 4; ++o)
+            xs4[o] = fmaf(cs[pp[o] * k + c], W0[c * k + qq[o]], xs4[o]);
+        }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const int idx = base + o * kSeedThreads;
+          if (idx < k * k) J0[idx] = W0[idx] - 0.5f * xs4[o];  // J0 is free
+        }
+      }
+      __syncthreads();
+      for (int idx = tid; idx < k * k; idx += kSeedThreads) Vd[idx] = (double)J0[idx];
+      __syncthreads();
+      if (b == 0 && tid == 0) ctl->jcyc[2] += clock64() - tj1;
     }
-    __syncthreads();
-    block_jacobi(A, Vb, k, cs, prs);
-    __syncthreads();
+    trace_mark(a, 8);
+    // ---- rotate: Pt = P V, PsiT = Psi V, partial column sums of Pt^2 --------
+    {
+      double csq = 0.0;  // thread c's partial of sum_i Pt[i][c]^2
+      for (int i = b; i < mp; i += nb) {
+        for (int q = tid; q < k; q += kSeedThreads)
+          rowb[q] = ldg_cg(a.P + (size_t)i * kmax + q);
+        __syncthreads();
+        for (int c = tid; c < k; c += kSeedThreads) {
+          double s = 0.0;
+          for (int q = 0; q < k; ++q) s = fma(rowb[q], Vd[q * k + c], s);
+          __stcg(a.Pt + (size_t)i * kmax + c, s);
+          csq = fma(s, s, csq);
+        }
+        __syncthreads();
+      }
+      if (tid < k) __stcg(a.colsq + (size_t)b * kmax + tid, csq);
+      for (int j = b; j < np; j += nb) {
+        for (int q = tid; q < k; q += kSeedThreads)
+          rowb[q] = ldg_cg(a.Psi + (size_t)j * kmax + q);
+        __syncthreads();
+        for (int c = tid; c < k; c += kSeedThreads) {
+          double s = 0.0;
+          for (int q = 0; q < k; ++q) s = fma(rowb[q], Vd[q * k + c], s);
+          __stcg(a.PsiT + (size_t)j * kmax + c, s);
+        }
+        __syncthreads();
+      }
+    }
+    if (!grid_sync(ctl, nb, tmo)) return;
+    trace_mark(a, 9);
+    // ---- FP64 Ritz values s_c = ||Pt e_c|| (fixed-order sum over blocks) ---
+    {
+      const int nparts = kSeedThreads / k;
+      const int c = tid % k, part = tid / k;
+      if (part < nparts) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int q = part;
+        for (; q + 3 * nparts < nb; q += 4 * nparts) {
+          s0 += ldg_cg(a.colsq + (size_t)q * kmax + c);
+          s1 += ldg_cg(a.colsq + (size_t)(q + nparts) * kmax + c);
+          s2 += ldg_cg(a.colsq + (size_t)(q + 2 * nparts) * kmax + c);
+          s3 += ldg_cg(a.colsq + (size_t)(q + 3 * nparts) * kmax + c);
+        }
+        for (; q < nb; q += nparts) s0 += ldg_cg(a.colsq + (size_t)q * kmax + c);
+        red[part * k + c] = (s0 + s1) + (s2 + s3);
+      }
+      __syncthreads();
+      if (tid < k) {
+        double s2 = 0.0;
+        for (int q = 0; q < nparts; ++q) s2 += red[q * k + tid];
+        lam[tid] = sqrt(s2);
+      }
+      __syncthreads();
+    }
     double smax = 0.0;
-    for (int c = 0; c < k; ++c) smax = fmax(smax, sqrt(fmax(A[c * k + c], 0.0)));
+    for (int c = 0; c < k; ++c) smax = fmax(smax, lam[c]);
     if (stage == 2) {
       // ||D||_2 from the Ritz values; start the ALM.
       mu = a.mu_scale / smax;
@@ -482,44 +768,28 @@ __global__ void __launch_bounds__(kSeedThreads, 1)
       if (b == 0 && tid == 0) ctl->sigma1 = smax;
     }
     tau = 1.0 / mu;
-    int nsv = 0;
     for (int c = tid; c < k; c += kSeedThreads) {
-      const double s = sqrt(fmax(A[c * k + c], 0.0));
-      lam[c] = s;
+      const double s = lam[c];
       dsc[c] = (s > tau) ? 1.0 - tau / s : 0.0;  // shrink factor d_c
     }
     __syncthreads();
+    int nsv = 0;
     for (int c = 0; c < k; ++c) nsv += (lam[c] > tau);
-    // ---- rotate: Pt = P Vb, Omega_next = Pt / s, PsiT = Psi Vb --------------
-    int knext = k;
+    knext = k;
     if (stage == 3 && nsv >= k && k < kmax)
       knext = min(kmax, (k + max(6, k / 4) + 1) / 2 * 2);
+    // Omega_next = Pt / s (rows distributed); fresh directions for growth
+    // and for vanished Ritz vectors.
     for (int i = b; i < mp; i += nb) {
       for (int c = tid; c < knext; c += kSeedThreads) {
-        if (c < k) {
-          double s = 0.0;
-          for (int q = 0; q < k; ++q)
-            s = fma(ldg_cg(a.P + (size_t)i * kmax + q), Vb[q * k + c], s);
-          __stcg(a.Pt + (size_t)i * kmax + c, s);
-          const double sc = lam[c];
-          __stcg(a.Om + (size_t)i * kmax + c,
-                 (sc > 1e-12 * smax) ? s / sc
-                                     : hash_normal(0xA11CEull + 977ull * it + c, i));
-        } else {
-          __stcg(a.Om + (size_t)i * kmax + c,
-                 hash_normal(0xB0B0ull + 977ull * it + c, i));
-        }
+        double v;
+        if (c < k && lam[c] > 1e-12 * smax)
+          v = ldg_cg(a.Pt + (size_t)i * kmax + c) / lam[c];
+        else
+          v = hash_normal(0xA11CEull + 977ull * it + c, i);
+        __stcg(a.Om + (size_t)i * kmax + c, v);
       }
     }
-    for (int j = b; j < np; j += nb) {
-      for (int c = tid; c < k; c += kSeedThreads) {
-        double s = 0.0;
-        for (int q = 0; q < k; ++q)
-          s = fma(ldg_cg(a.Psi + (size_t)j * kmax + q), Vb[q * k + c], s);
-        __stcg(a.PsiT + (size_t)j * kmax + c, s);
-      }
-    }
-    if (!grid_sync(ctl, nb, tmo)) return;
 
     if (stage == 2) {
       // Y_0 = D / J,  J = max(||D||_2, ||D||_inf / lam);  G_1 = D + Y_0/mu_0.
@@ -536,53 +806,50 @@ __global__ void __launch_bounds__(kSeedThreads, 1)
       }
       stage = 3;
       if (!grid_sync(ctl, nb, tmo)) return;
+      trace_mark(a, 10);
       continue;
     }
 
     // ---- ALM step: L = Pt diag(d) PsiT^T, S, Y, G for the next iteration ---
     const double mu_next = fmin(a.rho * mu, mu_max);
-    const double lam_mu = a.lam / mu;
+    const double inv_mu = 1.0 / mu, inv_mu_next = 1.0 / mu_next;
+    const double lam_mu = a.lam * inv_mu;
     double zz = 0.0;
     for (int j = b; j < np; j += nb) {
       for (int c = tid; c < k; c += kSeedThreads)
         xi[c] = dsc[c] * ldg_cg(a.PsiT + (size_t)j * kmax + c);
       __syncthreads();
       for (int i = tid; i < mp; i += kSeedThreads) {
-        double l = 0.0;
-        for (int c = 0; c < k; ++c)
-          l = fma(ldg_cg(a.Pt + (size_t)i * kmax + c), xi[c], l);
+        const double* pr = a.Pt + (size_t)i * kmax;
+        double l0 = 0.0, l1 = 0.0;
+        int c = 0;
+        for (; c + 1 < k; c += 2) {
+          l0 = fma(ldg_cg(pr + c), xi[c], l0);
+          l1 = fma(ldg_cg(pr + c + 1), xi[c + 1], l1);
+        }
+        if (c < k) l0 = fma(ldg_cg(pr + c), xi[c], l0);
+        const double l = l0 + l1;
         const size_t e = (size_t)j * mp + i;
         const double d = __ldg(a.D + e);
         const double y = ldg_cg(a.Y + e);
-        const double s = shrink(d - l + y / mu, lam_mu);
+        const double s = shrink(d - l + y * inv_mu, lam_mu);
         const double z = d - l - s;
         const double yn = fma(mu, z, y);
         zz = fma(z, z, zz);
         __stcg(a.S + e, s);
         __stcg(a.Y + e, yn);
-        const double g = d - s + yn / mu_next;
+        const double g = d - s + yn * inv_mu_next;
         __stcg(a.G + e, g);
         __stcg(a.Gt + (size_t)i * np + j, g);
       }
       __syncthreads();
     }
-    zz = warp_sum(zz);
-    if ((tid & 31) == 0) red[tid >> 5] = zz;
-    __syncthreads();
-    if (tid == 0) {
-      double s2 = 0.0;
-      for (int q = 0; q < kSeedThreads / 32; ++q) s2 += red[q];
-      __stcg(a.part + 4 * b + 2, s2);
-    }
+    zz = block_reduce_sum(zz, red);
+    if (tid == 0) __stcg(a.part + 4 * b + 2, zz);
     ++it;
     if (!grid_sync(ctl, nb, tmo)) return;
-    if (tid == 0) {
-      double s2 = 0.0;
-      for (int q = 0; q < nb; ++q) s2 += ldg_cg(a.part + 4 * q + 2);
-      s_scalar[2] = sqrt(s2) / normF;
-    }
-    __syncthreads();
-    res = s_scalar[2];
+    trace_mark(a, 11);
+    res = sqrt(sum_partials(a.part, nb, 4, 2, red)) / normF;
     converged = res <= a.tol;
     if (converged || it >= a.max_iter) break;
     mu = mu_next;
@@ -590,14 +857,13 @@ __global__ void __launch_bounds__(kSeedThreads, 1)
   }
 
   // ---- outputs: skinny SVD of L^s sorted by decreasing singular value -------
-  // this iteration's factors: U = Omega_next (= Pt / s), Sigma = s - tau,
-  // V = PsiT; rank = #{s - tau > rank_cut * max(s - tau)}, capped at r_cap.
+  // this iteration's factors: U = Pt / s, Sigma = s - tau, V = PsiT;
+  // rank = #{s - tau > rank_cut * max(s - tau)}, capped at r_cap.
   if (tid == 0) {
     int* order = prs;
     int cnt = 0;
     for (int c = 0; c < k; ++c) order[c] = c;
-    // insertion sort by decreasing s (k <= 96)
-    for (int x = 1; x < k; ++x) {
+    for (int x = 1; x < k; ++x) {  // insertion sort, decreasing s
       const int v = order[x];
       int y = x - 1;
       while (y >= 0 && lam[order[y]] < lam[v]) {
@@ -621,7 +887,9 @@ __global__ void __launch_bounds__(kSeedThreads, 1)
   for (int i = b; i < mp; i += nb)
     for (int c = tid; c < kmax; c += kSeedThreads)
       a.U[i + (size_t)c * mp] =
-          (c < rank) ? ldg_cg(a.Om + (size_t)i * kmax + order[c]) : 0.0;
+          (c < rank) ? ldg_cg(a.Pt + (size_t)i * kmax + order[c]) /
+                           lam[order[c]]
+                     : 0.0;
   for (int j = b; j < np; j += nb)
     for (int c = tid; c < kmax; c += kSeedThreads)
       a.V[j + (size_t)c * np] =
@@ -636,13 +904,26 @@ __global__ void __launch_bounds__(kSeedThreads, 1)
       ctl->converged = converged ? 1 : 0;
       ctl->residual = res;
       ctl->k_final = k;
+      // closing records: Jacobi cycle split (phases 95..98) and total
+      // Jacobi sweeps (phase 99)
+      for (int q = 0; q < 5; ++q) {
+        const int i = ctl->ntrace;
+        if (i < kSeedTraceCap) {
+          a.trace[2 * i] = q < 4 ? (unsigned long long)ctl->jcyc[q]
+                                 : (unsigned long long)ctl->jsweeps;
+          a.trace[2 * i + 1] = 95ull + q;
+          ctl->ntrace = i + 1;
+        }
+      }
     }
   }
 }
 
 size_t seed_smem_bytes(int kmax) {
-  return sizeof(double) * ((size_t)2 * kmax * kmax + kSeedThreads + 4 * kmax) +
-         sizeof(int) * 2 * kmax;
+  return sizeof(double) * ((size_t)kmax * kmax + kSeedThreads + 256 +
+                           4 * kmax) +
+         sizeof(float) * ((size_t)3 * kmax * kmax) +
+         sizeof(int) * 2 * kmax + (size_t)kmax * kmax;
 }
 
 }  // namespace
@@ -673,6 +954,7 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
   a.timeout_ns = 2000000000ull;  // 2 s per barrier wait
   a.ctl = reinterpret_cast<SeedCtl*>(w + L.ctl);
   a.part = reinterpret_cast<double*>(w + L.part);
+  a.colsq = reinterpret_cast<double*>(w + L.colsq);
   a.S = reinterpret_cast<double*>(w + L.S);
   a.Y = reinterpret_cast<double*>(w + L.Y);
   a.G = reinterpret_cast<double*>(w + L.G);
@@ -684,6 +966,8 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
   a.Psi = reinterpret_cast<double*>(w + L.Psi);
   a.PsiT = reinterpret_cast<double*>(w + L.PsiT);
   a.Gam = reinterpret_cast<double*>(w + L.Gam);
+  a.Gam2 = reinterpret_cast<double*>(w + L.Gam2);
+  a.trace = reinterpret_cast<unsigned long long*>(w + L.trace);
   a.U = dU;
   a.Sigma = dSigma;
   a.V = dV;
@@ -707,7 +991,10 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
     set_error("seed PCP: kernel does not fit on an SM (smem %zu)", smem);
     return PCP_ERR_UNSUPPORTED;
   }
-  const int grid = std::min(sms, kMaxCoopBlocks);
+  // one CTA per column/row task (max(m', n')), as far as all CTAs can be
+  // co-resident (a cooperative launch needs every CTA resident at once)
+  const int grid = std::min(std::min(sms * per_sm, kMaxCoopBlocks),
+                            std::max(mp, np));
   PCP_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(SeedCtl), st));
   void* args[] = {&a};
   PCP_CUDA(cudaLaunchCooperativeKernel((const void*)seed_alm_kernel, grid,
@@ -749,7 +1036,8 @@ extern "C" pcp_status pcp_seed_pcp(const double* dD, int32_t mp, int32_t np,
                                    double* dU, double* dSigma, double* dV,
                                    int32_t* h_rank, int32_t* h_iters,
                                    double* h_residual, void* stream) {
-  PCP_ARG(mp >= 2 && np >= 2, "pcp_seed_pcp: seed %dx%d too small", mp, np);
+  PCP_ARG(mp >= 2 && np >= 2 && mp <= 256 && np <= 256,
+          "pcp_seed_pcp: seed %dx%d outside [2, 256]", mp, np);
   PCP_ARG(kmax >= 2 && kmax <= pcp::kSeedKmaxLimit && kmax % 2 == 0 &&
               kmax <= std::min(mp, np) + (std::min(mp, np) & 1),
           "pcp_seed_pcp: kmax=%d must be even, <= %d and <= min(mp,np)", kmax,
@@ -784,4 +1072,26 @@ extern "C" pcp_status pcp_seed_pcp(const double* dD, int32_t mp, int32_t np,
     return PCP_ERR_SEED_NOCONV;
   }
   return PCP_OK;
+}
+
+extern "C" int32_t pcp_seed_trace(const void* d_work, int32_t mp, int32_t np,
+                                  int32_t kmax, uint64_t* h_out, int32_t cap,
+                                  void* stream) {
+  if (!d_work || mp < 1 || np < 1 || kmax < 2 || cap < 0) return -1;
+  const pcp::SeedLayout L = pcp::seed_layout(mp, np, kmax);
+  const char* w = static_cast<const char*>(d_work);
+  pcp::SeedCtl h;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&h, w + L.ctl, sizeof(h), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return -1;
+  const int n = std::min(std::min(h.ntrace, pcp::kSeedTraceCap), cap);
+  if (n > 0 && h_out) {
+    if (cudaMemcpyAsync(h_out, w + L.trace, sizeof(uint64_t) * 2 * n,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return -1;
+  }
+  return n;
 }
