@@ -199,6 +199,33 @@ pcp_status pcp_seed_pcp(const double* dD, int32_t mp, int32_t np,
                         double* dSigma, double* dV, int32_t* h_rank,
                         int32_t* h_iters, double* h_residual, void* stream);
 
+/* Allocation-free seed PCP (the paper has no counterpart; this is a
+ * deployment convenience).  Same arguments, results and errors as
+ * pcp_seed_pcp, without d_work: the workspace is a fixed 3 MiB array in
+ * device memory owned by the library, for callers that cannot call
+ * cudaMalloc (host frameworks that give out all device memory from their own
+ * pool, latency-bound loops that cannot afford cudaMalloc's implicit device
+ * synchronisation, processes whose memory budget is committed up front).
+ *   - Limit: seeds whose pcp_seed_workspace_bytes(mp, np, kmax) is at most
+ *     3 MiB (e.g. 200 x 200 with kmax = 52; not 256 x 256 with kmax = 64);
+ *     larger sizes return PCP_ERR_ARG with the byte counts in the message.
+ *   - Every GPU that loads the library holds the array until process exit.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, once per device); make that first call before
+ *     any stream capture.
+ *   - All calls share the array: calls whose work overlaps on the GPU (other
+ *     streams, other threads) race and must be serialised by the caller.
+ *     Each call clears the control words it relies on, so the contents left
+ *     by the previous call do no harm. */
+pcp_status pcp_seed_pcp_static(const double* dD, int32_t mp, int32_t np,
+                               double lambda, double tol, double rho,
+                               double mu_scale, double mu_max_ratio,
+                               int32_t max_iter, int32_t k0, int32_t kmax,
+                               double rank_cut, int32_t r_cap, double* dU,
+                               double* dSigma, double* dV, int32_t* h_rank,
+                               int32_t* h_iters, double* h_residual,
+                               void* stream);
+
 /* Tracing of the seed stage: copy block 0's phase records of the last seed
  * solve that ran in d_work (pcp_seed_pcp's workspace) into h_out, up to
  * `cap` records of two uint64 each: (globaltimer ns, phase code).  Phase

@@ -21,7 +21,8 @@ __all__ = [
     "PCPError", "PCPInfo", "PCPParams", "PCP_FP32", "PCP_BF16_REFINED",
     "colmajor", "pcp_params_default", "pcp_l1filter_plan",
     "pcp_l1filter_solve", "pcp_plan_destroy", "pcp_gather_seed",
-    "pcp_seed_workspace_bytes", "pcp_seed_pcp", "pcp_l1_filter",
+    "pcp_seed_workspace_bytes", "pcp_seed_pcp", "pcp_seed_pcp_static",
+    "pcp_l1_filter",
     "pcp_assemble_factors", "pcp_spass", "pcp_plan_seed_trace", "Plan",
     "solve", "load", "SEED_PHASES",
 ]
@@ -166,6 +167,27 @@ def pcp_seed_pcp(D, lam, tol, rho, mu_scale, mu_max_ratio, max_iter, k0, kmax,
                              _stream(stream))
     if raise_on_error:
         check(st, "pcp_seed_pcp")
+    return st, rank.value, iters.value, resid.value
+
+
+def pcp_seed_pcp_static(D, lam, tol, rho, mu_scale, mu_max_ratio, max_iter,
+                        k0, kmax, rank_cut, r_cap, U, Sigma, V, stream=None,
+                        raise_on_error=True):
+    """pcp_seed_pcp without a workspace argument (library-owned scratch)."""
+    mp, np_ = D.shape
+    rank = C.c_int32()
+    iters = C.c_int32()
+    resid = C.c_double()
+    pD, ldd = _cm(D, "D")
+    if ldd != mp:
+        raise ValueError("D must be packed (ld == rows)")
+    st = load().pcp_seed_pcp_static(pD, mp, np_, lam, tol, rho, mu_scale,
+                                    mu_max_ratio, max_iter, k0, kmax,
+                                    rank_cut, r_cap, _ptr(U), _ptr(Sigma),
+                                    _ptr(V), C.byref(rank), C.byref(iters),
+                                    C.byref(resid), _stream(stream))
+    if raise_on_error:
+        check(st, "pcp_seed_pcp_static")
     return st, rank.value, iters.value, resid.value
 
 

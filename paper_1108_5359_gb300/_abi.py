@@ -91,6 +91,9 @@ PROTOTYPES = {
     "pcp_seed_pcp": (_i32, [_vp, _i32, _i32, _f64, _f64, _f64, _f64, _f64,
                             _i32, _i32, _i32, _f64, _i32, _vp, _vp, _vp, _vp,
                             _ip32, _ip32, _dp, _vp]),
+    "pcp_seed_pcp_static": (_i32, [_vp, _i32, _i32, _f64, _f64, _f64, _f64,
+                                   _f64, _i32, _i32, _i32, _f64, _i32, _vp,
+                                   _vp, _vp, _ip32, _ip32, _dp, _vp]),
     "pcp_seed_trace": (_i32, [_vp, _i32, _i32, _i32, C.POINTER(C.c_uint64),
                               _i32, _vp]),
     "pcp_plan_seed_trace": (_i32, [_vp, C.POINTER(C.c_uint64), _i32, _vp]),

@@ -36,6 +36,7 @@
 // bit-identical factors.  Cross-CTA data is read with L2-only loads
 // (ld.global.cg) so no CTA sees a stale L1 line.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -1094,4 +1095,77 @@ extern "C" int32_t pcp_seed_trace(const void* d_work, int32_t mp, int32_t np,
       return -1;
   }
   return n;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of pcp_seed_pcp.
+//
+// Some callers cannot call cudaMalloc: host frameworks that hand out every
+// byte of device memory from their own pool and do not let extensions
+// allocate, latency-bound loops where cudaMalloc's implicit device
+// synchronisation would stall other streams, and processes whose device
+// memory budget is committed up front.  For them the seed workspace lives
+// in a fixed file-scope device array instead of a caller buffer.  Its host
+// symbol is only a stand-in: the device address is looked up once per
+// device with cudaGetSymbolAddress (on that device's first call) and passed
+// to the kernel.  Every GPU that loads the library holds the array until the
+// process exits.
+namespace pcp {
+namespace {
+
+constexpr size_t kSeedStaticScratchBytes = (size_t)3 << 20;  // 3 MiB
+constexpr int kMaxScratchDevices = 64;
+
+static __device__ __align__(256) unsigned char
+    g_seed_static_scratch[kSeedStaticScratchBytes];
+
+std::mutex g_seed_scratch_mu;
+void* g_seed_scratch_addr[kMaxScratchDevices] = {};
+
+// Device address of the static scratch on the current device (set up on
+// the first call per device, under a lock).
+pcp_status seed_static_scratch(void** out) {
+  int dev = 0;
+  PCP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxScratchDevices) {
+    set_error("pcp_seed_pcp_static: device ordinal %d >= %d", dev,
+              kMaxScratchDevices);
+    return PCP_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_seed_scratch_mu);
+  if (!g_seed_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_seed_static_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                       "cudaGetSymbolAddress(seed scratch)", __FILE__,
+                       __LINE__);
+    g_seed_scratch_addr[dev] = p;
+  }
+  *out = g_seed_scratch_addr[dev];
+  return PCP_OK;
+}
+
+}  // namespace
+}  // namespace pcp
+
+extern "C" pcp_status pcp_seed_pcp_static(
+    const double* dD, int32_t mp, int32_t np, double lambda, double tol,
+    double rho, double mu_scale, double mu_max_ratio, int32_t max_iter,
+    int32_t k0, int32_t kmax, double rank_cut, int32_t r_cap, double* dU,
+    double* dSigma, double* dV, int32_t* h_rank, int32_t* h_iters,
+    double* h_residual, void* stream) {
+  PCP_ARG(mp >= 2 && np >= 2 && kmax >= 2,
+          "pcp_seed_pcp_static: seed %dx%d, kmax=%d too small", mp, np, kmax);
+  const size_t need = pcp::seed_workspace_bytes(mp, np, kmax);
+  PCP_ARG(need <= pcp::kSeedStaticScratchBytes,
+          "pcp_seed_pcp_static: a %dx%d seed with kmax=%d needs %zu bytes of "
+          "scratch, more than the fixed %zu",
+          mp, np, kmax, need, pcp::kSeedStaticScratchBytes);
+  void* w = nullptr;
+  const pcp_status s = pcp::seed_static_scratch(&w);
+  if (s != PCP_OK) return s;
+  return pcp_seed_pcp(dD, mp, np, lambda, tol, rho, mu_scale, mu_max_ratio,
+                      max_iter, k0, kmax, rank_cut, r_cap, w, dU, dSigma, dV,
+                      h_rank, h_iters, h_residual, stream);
 }
