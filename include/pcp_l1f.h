@@ -82,7 +82,8 @@ typedef struct pcp_params {
   double seed_mu_scale;     /* mu_0 = seed_mu_scale/||M^s||_2, default 1.25 */
   double seed_mu_max_ratio; /* mu_max = ratio * mu_0, default 1e7 */
   double rank_cut;          /* singular values of L^s below rank_cut * the
-                               largest are dropped, default 1e-10 */
+                               largest are dropped, default 1e-6 (the seed is
+                               resolved only to ~1e-7 of its norm) */
   double filter_tol;        /* epsilon of Algorithm 1, default 3e-7 */
   double filter_rho;        /* rho of Algorithm 1, default 1.5 */
   double beta0_scale;       /* beta_0 = beta0_scale/||x||_inf, default 1 */

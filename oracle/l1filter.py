@@ -103,7 +103,7 @@ def adm_l1(X, A, eps=ADM_EPS, rho=ADM_RHO, beta0_scale=ADM_BETA0_SCALE,
     return ADMResult(Z=Z, E=E, iters=iters, converged=converged)
 
 
-def numerical_rank(sigma, rel_cut=1e-10):
+def numerical_rank(sigma, rel_cut=1e-6):
     """Count singular values above rel_cut * sigma_max."""
     sigma = np.asarray(sigma)
     if sigma.size == 0 or sigma.max() <= 0:
@@ -159,12 +159,16 @@ class L1FilterResult:
 
 
 def l1_filter_pcp(M, rows, cols, r=None, seed_tol=1e-7, lam_seed=None,
-                  s_r=10.0, s_c=10.0, rank_cut=1e-10, adm_kw=None,
+                  s_r=10.0, s_c=10.0, rank_cut=1e-6, adm_kw=None,
                   seed_kw=None, form_L=True):
     """Algorithm 2 on M (m x n) with seed rows I_s = rows, columns J_s = cols.
 
     ``r`` caps the rank kept from the seed (the target rank); None keeps the
-    numerical rank of L^s.
+    numerical rank of L^s: singular values above rank_cut times the largest.
+    The seed PCP stops at a relative residual of 1e-7, so L^s is resolved
+    only to about 1e-7 of its norm; components below 1e-6 of the largest are
+    treated as zero (with a 1e-10 cut, two equally converged ALM iterates
+    of a borderline seed can disagree on the rank).
     """
     M = np.asarray(M, dtype=np.float64)
     m, n = M.shape

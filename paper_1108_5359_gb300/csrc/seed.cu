@@ -58,6 +58,7 @@ struct SeedCtl {
   int ntrace;
   int jsweeps;     // total Jacobi sweeps (block 0), for tracing
   long long jcyc[4];  // block 0 Jacobi cycles: angles, A, V, end-of-round
+  long long sub[8];   // block 0 sub-step cycle counters (tracing)
   double residual;
   double sigma1;
   double pad[4];
@@ -305,8 +306,10 @@ __device__ void gram(const double* X, int nrows, int k, int kmax,
 __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
                              const double* Gm, double* Out, float* A32,
                              float* Ri32, double* dsc, int* dead,
-                             double* rowb) {
+                             double* rowb, long long* sub = nullptr) {
   const int tid = threadIdx.x;
+  const bool prof = sub && blockIdx.x == 0 && tid == 0;
+  long long q0 = prof ? clock64() : 0;
   __shared__ float s_inv[2];
   for (int c = tid; c < k; c += kSeedThreads) {
     const double g = ldg_cg(Gm + c * kmax + c);
@@ -314,12 +317,17 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
     dsc[c] = (g > 0.0) ? 1.0 / sqrt(g) : 0.0;
   }
   __syncthreads();
-  for (int idx = tid; idx < k * k; idx += kSeedThreads) {
-    const int a = idx / k, b = idx - a * k;
-    float v = (float)(ldg_cg(Gm + a * kmax + b) * dsc[a] * dsc[b]);
-    if (dead[a] || dead[b]) v = (a == b) ? 1.0f : 0.0f;
-    A32[idx] = v;
+  // scaled Gram in FP32 (redundant per CTA: FP64 here would occupy the
+  // chip's narrow FP64 pipe in every CTA at once)
+  for (int a = tid >> 4; a < k; a += kSeedThreads / 16) {
+    const float da = (float)dsc[a];
+    for (int b = tid & 15; b < k; b += 16) {
+      float v = (float)ldg_cg(Gm + a * kmax + b) * da * (float)dsc[b];
+      if (dead[a] || dead[b]) v = (a == b) ? 1.0f : 0.0f;
+      A32[a * k + b] = v;
+    }
   }
+  long long q1 = prof ? clock64() : 0;
   // Right-looking Cholesky, R in the upper triangle.  Step j's trailing
   // update reads row j unscaled (times 1/pivot^2); row j is scaled at the
   // start of step j+1.  The reciprocal alternates between two slots so step
@@ -344,10 +352,10 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
     }
     __syncthreads();
     const float inv2 = s_inv[j & 1] * s_inv[j & 1];
-    const int rem = k - j - 1;
-    for (int idx = tid; idx < rem * rem; idx += kSeedThreads) {
-      const int a = j + 1 + idx / rem, b = j + 1 + idx % rem;
-      if (a <= b) A32[a * k + b] -= A32[j * k + a] * A32[j * k + b] * inv2;
+    for (int a = j + 1 + (tid >> 4); a < k; a += kSeedThreads / 16) {
+      const float rja = A32[j * k + a] * inv2;
+      for (int b = a + (tid & 15); b < k; b += 16)
+        A32[a * k + b] -= rja * A32[j * k + b];
     }
   }
   __syncthreads();
@@ -358,10 +366,11 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
   // perturbs the directions near the threshold enough to slow the ALM.
   for (int c = tid; c < k; c += kSeedThreads) Ri32[c] = 1.0f / A32[c * k + c];
   __syncthreads();
+  long long q2 = prof ? clock64() : 0;
+  // one warp per CTA: the FP64 pipe is narrow on this part, so the rows are
+  // spread over as many SMs as possible rather than over warps of few CTAs
   const int lane = tid & 31;
-  const int gw = blockIdx.x * (kSeedThreads / 32) + (tid >> 5);
-  const int nw = gridDim.x * (kSeedThreads / 32);
-  for (int t = gw; t < nrows; t += nw) {
+  for (int t = (tid < 32) ? blockIdx.x : nrows; t < nrows; t += gridDim.x) {
     const int c0 = lane, c1 = lane + 32;
     double p0 = c0 < k ? ldg_cg(X + (size_t)t * kmax + c0) * dsc[c0] : 0.0;
     double p1 = c1 < k ? ldg_cg(X + (size_t)t * kmax + c1) * dsc[c1] : 0.0;
@@ -379,6 +388,12 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
     }
     if (c0 < k) __stcg(Out + (size_t)t * kmax + c0, o0);
     if (c1 < k) __stcg(Out + (size_t)t * kmax + c1, o1);
+  }
+  if (prof) {
+    const long long q3 = clock64();
+    sub[0] += q1 - q0;
+    sub[1] += q2 - q1;
+    sub[2] += q3 - q2;
   }
 }
 
@@ -439,8 +454,12 @@ __device__ float* block_jacobi32(float* A0, float* A1, float* V, int k,
       const long long t0 = prof ? clock64() : 0;
       __syncthreads();
       if (prof) c0 += clock64() - t0;
-      for (int w = tid; w < half * half; w += kSeedThreads) {
-        const int i = w / half, j = w - i * half;
+      // 2-D thread map without integer division: 16 x 16 for half <= 16,
+      // 8 x 32 otherwise
+      const int jsh = half <= 16 ? 4 : 5;
+      for (int w = tid; w < (half << jsh); w += kSeedThreads) {
+        const int i = w >> jsh, j = w & ((1 << jsh) - 1);
+        if (j >= half) continue;
         const unsigned char* tr = tab + round * k;
         int pi = tr[i], qi = tr[k - 1 - i];
         int pj = tr[j], qj = tr[k - 1 - j];
@@ -451,7 +470,7 @@ __device__ float* block_jacobi32(float* A0, float* A1, float* V, int k,
                                      A[pi * k + qi], ci, si);
         const bool rj = jacobi_angle(A[pj * k + pj], A[qj * k + qj],
                                      A[pj * k + qj], cj, sj);
-        if (ri && w == i * half + i) s_rot[flip] = 1;
+        if (ri && i == j) s_rot[flip] = 1;
         const float b00 = A[pi * k + pj], b01 = A[pi * k + qj];
         const float b10 = A[qi * k + pj], b11 = A[qi * k + qj];
         const float r00 = ci * b00 - si * b10, r01 = ci * b01 - si * b11;
@@ -580,7 +599,8 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
     gram(a.T, np, k, kmax, a.Gam);
     if (!grid_sync(ctl, nb, tmo)) return;
     trace_mark(a, 3);
-    cholqr_apply(a.T, np, k, kmax, a.Gam, a.Psi, J0, W0, dsc, dead, rowb);
+    cholqr_apply(a.T, np, k, kmax, a.Gam, a.Psi, J0, W0, dsc, dead, rowb,
+                 ctl->sub);
     if (!grid_sync(ctl, nb, tmo)) return;
     trace_mark(a, 4);
     // ---- P = G Psi ------------------------------------------------------------
@@ -602,9 +622,11 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
     // ---- Rayleigh-Ritz rotation ---------------------------------------------
     // Psi1 (from the FP32 Cholesky QR) has Psi1^T Psi1 = I + E, |E| ~ 1e-7.
     // Its first-order orthonormalisation Psi = Psi1 (I - E/2) is never
-    // formed: C = P^T P = C1 - (E C1 + C1 E)/2 and the rotation applied to
-    // P1 and Psi1 is W = (I - E/2) V.  The correction terms are tiny, so
-    // FP32 products are exact enough for them.
+    // formed: the Jacobi runs on C1 = P1^T P1 (the correction to C is below
+    // the FP32 resolution of the Jacobi's input) and the rotation applied to
+    // P1 and Psi1 is W = (I - E/2) V, which makes the rotated bases
+    // orthonormal to O(E^2).  The W correction is tiny, so an FP32 product
+    // is exact enough for it.
     {
       float* E32 = W0;  // E, then the Jacobi's V
       float* C32 = J0;  // C1 / cmax, then the Jacobi's A
@@ -613,49 +635,25 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
           tid < k ? ldg_cg(a.Gam + tid * kmax + tid) : 0.0, red);
       const long long ts1 = clock64();
       if (b == 0 && tid == 0) ctl->jcyc[0] += ts1 - ts0;
-      for (int idx = tid; idx < k * k; idx += kSeedThreads) {
-        const int p = idx / k, q = idx - p * k;
-        E32[idx] = (float)(ldg_cg(a.Gam2 + p * kmax + q) - (p == q ? 1.0 : 0.0));
-      }
+      for (int p = tid >> 4; p < k; p += kSeedThreads / 16)
+        for (int q = tid & 15; q < k; q += 16)
+          E32[p * k + q] =
+              (float)ldg_cg(a.Gam2 + p * kmax + q) - (p == q ? 1.0f : 0.0f);
       __syncthreads();
-      const double inv = cm > 0.0 ? 1.0 / cm : 1.0;
-      for (int idx = tid; idx < k * k; idx += kSeedThreads) {
-        const int p = idx / k, q = idx - p * k;
-        C32[idx] = (float)(ldg_cg(a.Gam + p * kmax + q) * inv);
-      }
+      const long long ts2 = clock64();
+      if (b == 0 && tid == 0) ctl->sub[3] += ts2 - ts1;
+      const float inv = cm > 0.0 ? (float)(1.0 / cm) : 1.0f;
+      for (int p = tid >> 4; p < k; p += kSeedThreads / 16)
+        for (int q = tid & 15; q < k; q += 16)
+          C32[p * k + q] = (float)ldg_cg(a.Gam + p * kmax + q) * inv;
       __syncthreads();
-      // Vd (scratch, FP64 buffer reused as floats): X = E C1n, then
-      // C = C1n - (X + X^T)/2 held in Vd as doubles
-      // X = E C1n and its transpose, four outputs per thread at once
-      for (int base = tid; base < k * k; base += 4 * kSeedThreads) {
-        int pp[4], qq[4];
-        float xs4[4] = {0.f, 0.f, 0.f, 0.f}, ys4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const int idx = min(base + o * kSeedThreads, k * k - 1);
-          pp[o] = idx / k;
-          qq[o] = idx - pp[o] * k;
-        }
-        for (int c = 0; c < k; ++c) {
-#pragma unroll
-          for (int o = 0; o < 4; ++o) {
-            xs4[o] = fmaf(E32[pp[o] * k + c], C32[c * k + qq[o]], xs4[o]);
-            ys4[o] = fmaf(E32[qq[o] * k + c], C32[c * k + pp[o]], ys4[o]);
-          }
-        }
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const int idx = base + o * kSeedThreads;
-          if (idx < k * k)
-            Vd[idx] = (double)C32[idx] - 0.5 * ((double)xs4[o] + (double)ys4[o]);
-        }
-      }
-      __syncthreads();
+      const long long ts3 = clock64();
+      if (b == 0 && tid == 0) ctl->sub[4] += ts3 - ts2;
+      // keep E for the W correction after the Jacobi, as floats in the
+      // (still unused) storage of Vd
+      float* Esave = reinterpret_cast<float*>(Vd);
       for (int idx = tid; idx < k * k; idx += kSeedThreads)
-        C32[idx] = (float)Vd[idx];
-      // keep E (FP32) in Vd as doubles for the W correction after Jacobi
-      for (int idx = tid; idx < k * k; idx += kSeedThreads)
-        Vd[idx] = (double)E32[idx];
+        Esave[idx] = E32[idx];
       __syncthreads();
       if (b == 0 && tid == 0) ctl->jcyc[3] += clock64() - ts0;
       trace_mark(a, 12);
@@ -674,12 +672,9 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
       (void)Afin;
       const long long tj1 = clock64();
       if (b == 0 && tid == 0) ctl->jcyc[1] += tj1 - tj0;
-      // W = V - (E/2) V (E in Vd as doubles, V in W0), written to J0,
+      // W = V - (E/2) V (E kept as floats in Vd, V in W0), written to J0,
       // which the Jacobi no longer needs, then widened into Vd
-      for (int idx = tid; idx < k * k; idx += kSeedThreads)
-        cs[idx] = (float)Vd[idx];  // E as floats (cs is free after the Jacobi
-                                   // unless it holds the final A, unused)
-      __syncthreads();
+      const float* Ef = reinterpret_cast<const float*>(Vd);
       for (int base = tid; base < k * k; base += 4 * kSeedThreads) {
         int pp[4], qq[4];
         float xs4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -692,7 +687,7 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
         for (int c = 0; c < k; ++c) {
 #pragma unroll
           for (int o = 0; o < 4; ++o)
-            xs4[o] = fmaf(cs[pp[o] * k + c], W0[c * k + qq[o]], xs4[o]);
+            xs4[o] = fmaf(Ef[pp[o] * k + c], W0[c * k + qq[o]], xs4[o]);
         }
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
@@ -913,6 +908,14 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
           a.trace[2 * i] = q < 4 ? (unsigned long long)ctl->jcyc[q]
                                  : (unsigned long long)ctl->jsweeps;
           a.trace[2 * i + 1] = 95ull + q;
+          ctl->ntrace = i + 1;
+        }
+      }
+      for (int q = 0; q < 8; ++q) {  // sub-step counters, phases 80..87
+        const int i = ctl->ntrace;
+        if (i < kSeedTraceCap) {
+          a.trace[2 * i] = (unsigned long long)ctl->sub[q];
+          a.trace[2 * i + 1] = 80ull + q;
           ctl->ntrace = i + 1;
         }
       }

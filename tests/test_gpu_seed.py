@@ -32,7 +32,7 @@ def _seed(D, r, kmax=None, tol=1e-7):
     Sg = torch.zeros(kmax, dtype=torch.float64, device="cuda")
     lam = 1.0 / np.sqrt(max(mp, np_))
     st, rank, iters, res = pk.pcp_seed_pcp(dD, lam, tol, 1.5, 1.25, 1e7, 500,
-                                           k0, kmax, 1e-10, r, work, U, Sg, V)
+                                           k0, kmax, 1e-6, r, work, U, Sg, V)
     torch.cuda.synchronize()
     return to_host(U), to_host(Sg), to_host(V), rank, iters, res
 

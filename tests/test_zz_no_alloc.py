@@ -53,7 +53,7 @@ def _args(D, r):
     k0, kmax = _k(mp, np_, r)
     lam = 1.0 / np.sqrt(max(mp, np_))
     return dict(lam=lam, tol=1e-7, rho=1.5, mu_scale=1.25, mu_max_ratio=1e7,
-                max_iter=500, k0=k0, kmax=kmax, rank_cut=1e-10, r_cap=r)
+                max_iter=500, k0=k0, kmax=kmax, rank_cut=1e-6, r_cap=r)
 
 
 def test_static_matches_workspace_two_calls_in_a_row():
