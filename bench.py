@@ -48,7 +48,7 @@ FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
@@ -56,6 +56,19 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true",
                     help="500x500 rank-5 workload (profiling / smoke)")
+    ap.add_argument("--workload", choices=["single", "batch", "serve"],
+                    default="single",
+                    help="single: the 5000x5000 rank-20 solve (default); "
+                         "batch: uneven instances through pcp_l1filter_batch "
+                         "vs one pcp_l1filter_solve per instance; serve: "
+                         "Poisson arrivals of video-like solves through "
+                         "pcp_serve_* vs a one-at-a-time queue")
+    ap.add_argument("--count", type=int, default=256,
+                    help="instances (batch) / requests (serve)")
+    ap.add_argument("--rate", type=float, default=50.0,
+                    help="serve: arrival rate, requests/s")
+    ap.add_argument("--r-max", type=int, default=25,
+                    help="batch: largest rank drawn (seed 10r <= 256)")
     return ap.parse_args()
 
 
@@ -97,7 +110,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}",
                  f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"),
+                 "-lms", "50"], stdout=open(self.path, "w"),
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -416,10 +429,292 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# -------------------------------------------------------------------------
+# batched and served forms (extra lines, not the default bench line)
+# -------------------------------------------------------------------------
+
+def _pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
+
+
+def run_batch(args):
+    """Uneven instances: one pcp_l1filter_batch call per step against one
+    pcp_l1filter_solve per instance (plans made outside the timed span)."""
+    import torch
+    import paper_1108_5359_gb300 as pk
+    from paper_1108_5359_gb300 import build as pkbuild, synth
+    pkbuild.build()
+    pk.load()
+    t0 = time.perf_counter()
+    Ps = synth.uneven_instances(count=args.count, seed=args.seed,
+                                r_max=args.r_max, keep_truth=False,
+                                dtype=np.float32)
+    t_gen = time.perf_counter() - t0
+    dev = torch.device("cuda", 0)
+    bufs, probs, plans = [], [], []
+    for P in Ps:
+        dM = pk.colmajor(P.m, P.n, device=dev)
+        dM.copy_(torch.from_numpy(P.M))
+        Lu = pk.colmajor(P.m, P.r, device=dev)
+        Lv = pk.colmajor(P.n, P.r, device=dev)
+        S = pk.colmajor(P.m, P.n, device=dev)
+        bufs.append((dM, Lu, Lv, S))
+        prm = pk.pcp_params_default(P.m, P.n, P.r)
+        probs.append(pk.problem(prm, dM, Lu, Lv, S, P.rows, P.cols))
+        plans.append(pk.Plan(pk.pcp_params_default(P.m, P.n, P.r), P.rows,
+                             P.cols))
+    entries = sum(P.m * P.n for P in Ps)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def batched():
+        st, infos = pk.pcp_l1filter_batch(probs, info=True, stream=stream,
+                                          raise_on_error=False)
+        return st, infos
+
+    def plain():
+        done_ms = []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        evs = []
+        for pl, (dM, Lu, Lv, S) in zip(plans, bufs):
+            pk.pcp_l1filter_solve(pl, dM, Lu, Lv, S, info=False,
+                                  stream=stream)
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            evs.append(e)
+        evs[-1].synchronize()
+        for e in evs:
+            done_ms.append(e0.elapsed_time(e))
+        return done_ms
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        st, infos = batched()
+        flush.zero_()
+        plain()
+    torch.cuda.synchronize()
+    statuses = [inf.status for inf in infos]
+    sampler = ClockSampler(0)
+    sampler.start()
+    b_ms, p_ms, p_lat = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st, infos = batched()
+        ev1.record(stream)
+        ev1.synchronize()
+        b_ms.append(ev0.elapsed_time(ev1))
+        flush.zero_()
+        done = plain()
+        p_ms.append(done[-1])
+        p_lat.extend(done)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    # parity: exact recovery on a sample of instances (regenerated with truth)
+    check = sorted(set([0, len(Ps) // 2, len(Ps) - 1]))
+    truth = synth.uneven_instances(count=args.count, seed=args.seed,
+                                   r_max=args.r_max, indices=check)
+    par = []
+    for i, T in zip(check, truth):
+        dM, Lu, Lv, S = bufs[i]
+        L = Lu.double().cpu().numpy() @ Lv.double().cpu().numpy().T
+        par.append({"instance": i, "m": T.m, "n": T.n, "r": T.r,
+                    "status": int(statuses[i]),
+                    "relerr_L_vs_L0": relerr(L, T.L0),
+                    "relerr_S_vs_S0": relerr(S.double().cpu().numpy(), T.S0)})
+    tb = statistics.mean(b_ms)
+    tp = statistics.mean(p_ms)
+    out = {
+        "metric": METRIC, "workload": "batch", "value": entries / (tb * 1e-3),
+        "unit": "entries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": tb,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"uneven{args.count}_r3-{args.r_max}",
+                   "desc": f"{args.count} instances, m~U[300,4000], "
+                           f"n~U[200,3000], r~U[3,{args.r_max}], density "
+                           "U[0.02,0.15], values U[-50,50], seed 10r x 10r, "
+                           "FP32 M",
+                   "entries_per_step": entries, "generate_s": t_gen,
+                   "l2": "flushed before each timed call"},
+        "plain_per_instance": {"value": entries / (tp * 1e-3),
+                               "ms_per_step": tp,
+                               "latency_ms": {"p50": _pct(p_lat, 0.5),
+                                              "p99": _pct(p_lat, 0.99)}},
+        "latency_ms": {"p50": _pct(b_ms, 0.5), "p99": _pct(b_ms, 0.99)},
+        "speedup_vs_plain": tp / tb,
+        "stages_ms": {"seed": infos[0].t_seed_ms,
+                      "filter": infos[0].t_filter_ms,
+                      "spass": infos[0].t_spass_ms},
+        "statuses": {str(k): statuses.count(k) for k in set(statuses)},
+        "parity_sample": par, "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    for pl in plans:
+        pl.close()
+
+
+def run_serve(args):
+    """Poisson arrivals of video-like solves (m = 320*240 frames, n ~
+    U[200,1000], rank 1-5): the server (continuous batching) against one
+    solve at a time in arrival order; latency = arrival to result on the
+    host."""
+    import threading
+    import torch
+    import paper_1108_5359_gb300 as pk
+    from paper_1108_5359_gb300 import build as pkbuild, synth
+    pkbuild.build()
+    pk.load()
+    rng = np.random.default_rng(args.seed)
+    kinds = 6
+    t0 = time.perf_counter()
+    Ps = [synth.video_like(int(rng.integers(200, 1001)), seed=args.seed + k)
+          for k in range(kinds)]
+    t_gen = time.perf_counter() - t0
+    dev = torch.device("cuda", 0)
+    dMs = []
+    for P in Ps:
+        dM = pk.colmajor(P.m, P.n, device=dev)
+        dM.copy_(torch.from_numpy(P.M.astype(np.float32)))
+        dMs.append(dM)
+    n_req = args.count
+    kind = [int(k) for k in rng.integers(0, kinds, size=n_req)]
+    gaps = rng.exponential(1.0 / args.rate, size=n_req)
+    arrive = np.cumsum(gaps) - gaps[0]
+    slots = 16
+    mx = max(P.n for P in Ps)
+    m = Ps[0].m
+    out_sets = []
+    for _ in range(slots):
+        out_sets.append((torch.empty(m * 5, device=dev),
+                         torch.empty(mx * 5, device=dev),
+                         pk.colmajor(m, mx, device=dev)))
+
+    def views(slot, P):
+        # Lu (m x r, ld m) and Lv (n x r, ld n) as the ABI lays them out
+        fu, fv, S = out_sets[slot]
+        return (fu[:P.m * P.r].view(P.r, P.m).t(),
+                fv[:P.n * P.r].view(P.r, P.n).t(), S[:, :P.n])
+
+    def mkprob(i, slot):
+        P = Ps[kind[i]]
+        Lu, Lv, S = views(slot, P)
+        return pk.problem(pk.pcp_params_default(P.m, P.n, P.r), dMs[kind[i]],
+                          Lu, Lv, S, P.rows, P.cols)
+
+    def run_served(rate_scale):
+        srv = pk.Server(hbm_budget_bytes=8 << 30, max_slots=slots, streams=4)
+        lat = [None] * n_req
+        sts = [None] * n_req
+        free = list(range(slots))
+        cv = threading.Condition()
+        tickets = {}
+
+        def waiter():
+            for i in range(n_req):
+                while True:
+                    with cv:
+                        if i in tickets:
+                            t, slot, ta = tickets[i]
+                            break
+                        cv.wait(0.01)
+                st, inf = srv.wait(t)
+                lat[i] = 1e3 * (time.perf_counter() - ta)
+                sts[i] = st
+                with cv:
+                    free.append(slot)
+                    cv.notify_all()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        tstart = time.perf_counter()
+        for i in range(n_req):
+            target = tstart + arrive[i] / rate_scale
+            while time.perf_counter() < target:
+                time.sleep(min(0.0005, max(0.0, target - time.perf_counter())))
+            ta = max(target, tstart)
+            with cv:
+                while not free:
+                    cv.wait(0.01)
+                slot = free.pop()
+            q = mkprob(i, slot)
+            t = srv.submit(q)
+            with cv:
+                tickets[i] = (t, slot, ta)
+                cv.notify_all()
+        th.join()
+        wall = time.perf_counter() - tstart
+        srv.close()
+        return lat, sts, wall
+
+    plans = [pk.Plan(pk.pcp_params_default(P.m, P.n, P.r), P.rows, P.cols)
+             for P in Ps]
+
+    def run_plain(rate_scale):
+        lat = []
+        sts = []
+        stream = torch.cuda.current_stream()
+        tstart = time.perf_counter()
+        for i in range(n_req):
+            target = tstart + arrive[i] / rate_scale
+            while time.perf_counter() < target:
+                time.sleep(min(0.0005, max(0.0, target - time.perf_counter())))
+            P = Ps[kind[i]]
+            Lu, Lv, S = views(0, P)
+            st, inf, _, _ = pk.pcp_l1filter_solve(
+                plans[kind[i]], dMs[kind[i]], Lu, Lv, S, info=True,
+                stream=stream, raise_on_error=False)
+            lat.append(1e3 * (time.perf_counter() - (tstart + arrive[i]
+                                                        / rate_scale)))
+            sts.append(st)
+        wall = time.perf_counter() - tstart
+        return lat, sts, wall
+
+    # warm-up both paths
+    run_plain(1e6)
+    run_served(1e6)
+    entries = sum(Ps[k].m * Ps[k].n for k in kind)
+    res = {}
+    for label, scale in (("poisson", 1.0), ("burst", 1e6)):
+        ls, ss, ws_ = run_served(scale)
+        lp, sp, wp = run_plain(scale)
+        res[label] = {
+            "served": {"entries_per_s": entries / ws_, "wall_s": ws_,
+                       "p50_ms": _pct(ls, 0.5), "p99_ms": _pct(ls, 0.99),
+                       "ok": ss.count(0)},
+            "plain": {"entries_per_s": entries / wp, "wall_s": wp,
+                      "p50_ms": _pct(lp, 0.5), "p99_ms": _pct(lp, 0.99),
+                      "ok": sp.count(0)},
+        }
+    for pl in plans:
+        pl.close()
+    out = {
+        "metric": METRIC, "workload": "serve",
+        "value": res["burst"]["served"]["entries_per_s"], "unit": "entries/s",
+        "n_gpus": 1, "requests": n_req, "rate_req_s": args.rate,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "video_like_76800xU[200,1000]_r1-5",
+                   "kinds": [{"n": P.n, "r": P.r} for P in Ps],
+                   "generate_s": t_gen,
+                   "latency": "host clock, arrival to result"},
+        "latency_ms": {"p50": res["poisson"]["served"]["p50_ms"],
+                       "p99": res["poisson"]["served"]["p99_ms"]},
+        "results": res,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

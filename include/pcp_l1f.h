@@ -114,8 +114,23 @@ typedef struct pcp_info {
   float t_seed_ms;          /* gather + seed PCP + factor assembly */
   float t_filter_ms;        /* column and row filtering */
   float t_spass_ms;         /* S = M - L */
-  float t_total_ms;
+  float t_total_ms;         /* whole solve (batched and served forms: the
+                               batch / request end to end) */
+  int32_t status;           /* pcp_status of this solve */
+  int32_t reserved;
 } pcp_info;
+
+/* One instance of a batched or served solve: its parameters and buffers
+ * (same meaning and layout as the arguments of pcp_l1filter_solve). */
+typedef struct pcp_problem {
+  pcp_params params;
+  const float* dM;
+  int64_t ldm;
+  float* dLu;
+  float* dLv;
+  float* dS; /* may be NULL */
+  int64_t lds;
+} pcp_problem;
 
 typedef struct pcp_plan pcp_plan;
 
@@ -163,6 +178,79 @@ pcp_status pcp_l1filter_solve(pcp_plan* plan, const float* dM, int64_t ldm,
                               void* stream);
 
 void pcp_plan_destroy(pcp_plan* plan);
+
+/* Batched form of Algorithm 2 (Section 3.2: the column and row problems of
+ * every instance are independent): `count` independent instances of any
+ * sizes, each stage one launch over all of them (batched gather; one CTA per
+ * seed PCP, so the seeds run side by side; batched factor assembly; one
+ * Algorithm 1 launch per kernel shape over every instance's column and row
+ * problems), then the S pass per instance.  Every parameter is per
+ * instance, and an instance's result does not depend on the other
+ * instances of the batch.  The seed PCP here runs on one CTA per instance,
+ * so its rounding differs from pcp_l1filter_solve's (whole-GPU seed) by
+ * reduction order only.  Workspace is stream-ordered (cudaMallocAsync /
+ * cudaFreeAsync on `stream`); the caller's buffers must stay valid until
+ * the stream reaches the end of the batch.  With infos (count entries) the
+ * call synchronises and fills one pcp_info per instance, including its
+ * status; the return value is then the first non-OK status.  Without infos
+ * the call is asynchronous.  Limits: count <= 65535, r <= 32, seeds up to
+ * 256 x 256; violations give PCP_ERR_ARG before any device work. */
+pcp_status pcp_l1filter_batch(int32_t count, const pcp_problem* probs,
+                              pcp_info* infos, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of independent solves (no counterpart in
+ * the paper, which solves one matrix at a time; built on the batched form).
+ *
+ * A server owns a scheduler thread and `streams` CUDA streams on the device
+ * current at creation.  pcp_serve_submit queues a request and returns at
+ * once with a ticket.  The scheduler admits queued requests in arrival
+ * order while their summed device workspace stays within hbm_budget_bytes
+ * and at most max_slots requests are in flight, launches each admitted
+ * group as one batched solve on a free stream, and keeps admitting while
+ * earlier groups run, so requests that arrive during a solve join the next
+ * group instead of waiting for the device to drain.  A request whose
+ * workspace alone exceeds the budget completes with PCP_ERR_NOMEM.  The
+ * result of a request does not depend on which other requests share its
+ * group.  The caller's buffers (pcp_problem pointers) must stay valid and
+ * untouched until the request completes; the optional seed index arrays
+ * are copied at submission.
+ * ---------------------------------------------------------------------- */
+typedef struct pcp_server pcp_server;
+
+/* Create a server.  hbm_budget_bytes > 0; max_slots >= 1;
+ * 1 <= streams <= 16.  PCP_ERR_ARG on bad arguments, PCP_ERR_CUDA if a
+ * stream cannot be created. */
+pcp_status pcp_serve_create(size_t hbm_budget_bytes, int32_t max_slots,
+                            int32_t streams, pcp_server** out);
+
+/* Queue one request (validated now: PCP_ERR_ARG before queueing on bad
+ * sizes or pointers).  *ticket receives its id.  PCP_ERR_CANCELLED once
+ * pcp_serve_destroy has begun. */
+pcp_status pcp_serve_submit(pcp_server* server, const pcp_problem* prob,
+                            uint64_t* ticket);
+
+/* Non-blocking: PCP_ERR_BUSY while the request is queued or running;
+ * otherwise the request's own status, *info filled (if non-NULL; its
+ * t_total_ms is submission to completion), and the ticket is released.
+ * PCP_ERR_ARG for an unknown or already released ticket. */
+pcp_status pcp_serve_poll(pcp_server* server, uint64_t ticket,
+                          pcp_info* info);
+
+/* Blocking form of pcp_serve_poll. */
+pcp_status pcp_serve_wait(pcp_server* server, uint64_t ticket,
+                          pcp_info* info);
+
+/* Stop admitting: requests not yet launched complete with
+ * PCP_ERR_CANCELLED, running groups are finished and the scheduler thread
+ * is joined.  Every ticket stays pollable afterwards; later submissions
+ * return PCP_ERR_CANCELLED.  Idempotent. */
+pcp_status pcp_serve_stop(pcp_server* server);
+
+/* pcp_serve_stop, then release the server (its streams and any results
+ * never polled).  No other call on this server may be in progress or made
+ * afterwards.  NULL is accepted. */
+pcp_status pcp_serve_destroy(pcp_server* server);
 
 /* ------------------------------------------------------------------------
  * Stage entry points (the rows of the hot path, callable one by one).

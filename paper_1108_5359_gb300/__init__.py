@@ -14,8 +14,9 @@ from __future__ import annotations
 import ctypes as C
 
 from . import _abi
-from ._abi import (PCPError, PCPInfo, PCPParams, PCP_BF16_REFINED, PCP_FP32,
-                   PCP_OK, check, load)
+from ._abi import (PCPError, PCPInfo, PCPParams, PCPProblem,
+                   PCP_BF16_REFINED, PCP_ERR_BUSY, PCP_FP32, PCP_OK, check,
+                   load)
 
 __all__ = [
     "PCPError", "PCPInfo", "PCPParams", "PCP_FP32", "PCP_BF16_REFINED",
@@ -24,7 +25,9 @@ __all__ = [
     "pcp_seed_workspace_bytes", "pcp_seed_pcp", "pcp_seed_pcp_static",
     "pcp_l1_filter",
     "pcp_assemble_factors", "pcp_spass", "pcp_plan_seed_trace", "Plan",
-    "solve", "load", "SEED_PHASES",
+    "solve", "load", "SEED_PHASES", "PCPProblem", "problem",
+    "pcp_l1filter_batch", "Server", "pcp_serve_create", "pcp_serve_submit",
+    "pcp_serve_poll", "pcp_serve_wait", "pcp_serve_stop", "pcp_serve_destroy",
 ]
 
 
@@ -139,6 +142,121 @@ def pcp_l1filter_solve(plan: Plan, M, Lu, Lv, S=None, info=True,
     return st, inf, rows, cols
 
 
+class _Problem:
+    """A pcp_problem plus the host arrays its seed index pointers refer to."""
+
+    def __init__(self, params, M, Lu, Lv, S=None, seed_rows=None,
+                 seed_cols=None):
+        import numpy as np
+        self._keep = [M, Lu, Lv, S]
+        p = PCPParams.from_buffer_copy(params)
+        if seed_rows is not None:
+            a = np.ascontiguousarray(seed_rows, dtype=np.int64)
+            self._keep.append(a)
+            p.seed_rows = a.ctypes.data_as(C.POINTER(C.c_int64))
+        if seed_cols is not None:
+            a = np.ascontiguousarray(seed_cols, dtype=np.int64)
+            self._keep.append(a)
+            p.seed_cols = a.ctypes.data_as(C.POINTER(C.c_int64))
+        pM, ldm = _cm(M, "M")
+        pLu, _ = _cm(Lu, "Lu")
+        pLv, _ = _cm(Lv, "Lv")
+        pS, lds = _cm(S, "S")
+        self.c = PCPProblem(p, pM, ldm, pLu, pLv, pS,
+                            lds if S is not None else p.m)
+
+
+def problem(params, M, Lu, Lv, S=None, seed_rows=None, seed_cols=None):
+    """One instance for pcp_l1filter_batch / pcp_serve_submit (tensors as
+    for pcp_l1filter_solve; Lu must be m x r and Lv n x r with ld m / n)."""
+    return _Problem(params, M, Lu, Lv, S, seed_rows, seed_cols)
+
+
+def pcp_l1filter_batch(problems, info=True, stream=None,
+                       raise_on_error=True):
+    """Batched Algorithm 2; returns (status, [PCPInfo per instance] or None)."""
+    n = len(problems)
+    arr = (PCPProblem * max(n, 1))(*[q.c for q in problems])
+    infos = (PCPInfo * max(n, 1))() if info else None
+    st = load().pcp_l1filter_batch(n, arr, infos, _stream(stream))
+    if raise_on_error and st != PCP_OK:
+        check(st, "pcp_l1filter_batch")
+    return st, (list(infos)[:n] if infos is not None else None)
+
+
+class Server:
+    """Owns a pcp_server; keeps each request's tensors alive until polled."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=256, streams=4):
+        self.handle = C.c_void_p()
+        check(load().pcp_serve_create(int(hbm_budget_bytes), int(max_slots),
+                                      int(streams), C.byref(self.handle)),
+              "pcp_serve_create")
+        self._live = {}
+
+    def submit(self, prob):
+        t = C.c_uint64()
+        check(load().pcp_serve_submit(self.handle, C.byref(prob.c),
+                                      C.byref(t)), "pcp_serve_submit")
+        self._live[t.value] = prob
+        return t.value
+
+    def poll(self, ticket):
+        """(status, PCPInfo) or (PCP_ERR_BUSY, None) while pending."""
+        inf = PCPInfo()
+        st = load().pcp_serve_poll(self.handle, ticket, C.byref(inf))
+        if st == PCP_ERR_BUSY:
+            return st, None
+        self._live.pop(ticket, None)
+        return st, inf
+
+    def wait(self, ticket):
+        inf = PCPInfo()
+        st = load().pcp_serve_wait(self.handle, ticket, C.byref(inf))
+        self._live.pop(ticket, None)
+        return st, inf
+
+    def stop(self):
+        if self.handle:
+            check(load().pcp_serve_stop(self.handle), "pcp_serve_stop")
+
+    def close(self):
+        if self.handle:
+            load().pcp_serve_destroy(self.handle)
+            self.handle = C.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pcp_serve_create(hbm_budget_bytes, max_slots=256, streams=4):
+    return Server(hbm_budget_bytes, max_slots, streams)
+
+
+def pcp_serve_submit(server, prob):
+    return server.submit(prob)
+
+
+def pcp_serve_poll(server, ticket):
+    return server.poll(ticket)
+
+
+def pcp_serve_wait(server, ticket):
+    return server.wait(ticket)
+
+
+def pcp_serve_stop(server):
+    server.stop()
+
+
+def pcp_serve_destroy(server):
+    server.close()
+
+
 def pcp_gather_seed(M, d_rows, d_cols, Ms, stream=None):
     pM, ldm = _cm(M, "M")
     check(load().pcp_gather_seed(pM, ldm, _ptr(d_rows), d_rows.numel(),
@@ -206,7 +324,8 @@ def pcp_plan_seed_trace(plan, cap=4096, stream=None):
 SEED_PHASES = {1: "prologue", 2: "T=G^T Omega", 3: "gram(T)", 4: "cholqr(T)",
                5: "P=G Psi", 6: "gram(P)", 7: "power orth", 8: "jacobi",
                9: "rotate", 10: "alm start", 11: "alm update",
-               12: "jacobi setup"}
+               12: "jacobi setup", 13: "refine gram(Pt)",
+               14: "refine apply"}
 
 
 def pcp_l1_filter(M, d_pidx, sp, d_qidx, sq, A, r, Z, ldz, eps, rho,

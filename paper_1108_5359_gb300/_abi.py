@@ -65,10 +65,20 @@ class PCPInfo(C.Structure):
         ("seed_residual", C.c_double), ("lambda_", C.c_double),
         ("t_seed_ms", C.c_float), ("t_filter_ms", C.c_float),
         ("t_spass_ms", C.c_float), ("t_total_ms", C.c_float),
+        ("status", C.c_int32), ("reserved", C.c_int32),
     ]
 
     def as_dict(self):
         return {f[0].rstrip("_"): getattr(self, f[0]) for f in self._fields_}
+
+
+class PCPProblem(C.Structure):
+    _fields_ = [
+        ("params", PCPParams),
+        ("dM", C.c_void_p), ("ldm", C.c_int64),
+        ("dLu", C.c_void_p), ("dLv", C.c_void_p),
+        ("dS", C.c_void_p), ("lds", C.c_int64),
+    ]
 
 
 _vp = C.c_void_p
@@ -86,6 +96,15 @@ PROTOTYPES = {
     "pcp_l1filter_solve": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _ip64,
                                   _ip64, C.POINTER(PCPInfo), _vp]),
     "pcp_plan_destroy": (None, [_vp]),
+    "pcp_l1filter_batch": (_i32, [_i32, C.POINTER(PCPProblem),
+                                  C.POINTER(PCPInfo), _vp]),
+    "pcp_serve_create": (_i32, [C.c_size_t, _i32, _i32, C.POINTER(_vp)]),
+    "pcp_serve_submit": (_i32, [_vp, C.POINTER(PCPProblem),
+                                C.POINTER(C.c_uint64)]),
+    "pcp_serve_poll": (_i32, [_vp, C.c_uint64, C.POINTER(PCPInfo)]),
+    "pcp_serve_wait": (_i32, [_vp, C.c_uint64, C.POINTER(PCPInfo)]),
+    "pcp_serve_stop": (_i32, [_vp]),
+    "pcp_serve_destroy": (_i32, [_vp]),
     "pcp_gather_seed": (_i32, [_vp, _i64, _vp, _i32, _vp, _i32, _vp, _vp]),
     "pcp_seed_workspace_bytes": (C.c_size_t, [_i32, _i32, _i32]),
     "pcp_seed_pcp": (_i32, [_vp, _i32, _i32, _f64, _f64, _f64, _f64, _f64,

@@ -452,6 +452,13 @@ extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
   info->t_filter_ms = t12;
   info->t_spass_ms = t23;
   info->t_total_ms = t03;
+  pcp_status result = PCP_OK;
+  if (err) result = PCP_ERR_TIMEOUT;
+  else if (bad) result = PCP_ERR_NONFINITE;
+  else if (!conv) result = PCP_ERR_SEED_NOCONV;
+  else if (!info->rank_ok) result = PCP_ERR_RANK_TEST;
+  else if (unconv) result = PCP_ERR_FILTER_NOCONV;
+  info->status = (int32_t)result;
   if (err) {
     pcp::set_error("seed PCP: device barrier wait timed out");
     return PCP_ERR_TIMEOUT;

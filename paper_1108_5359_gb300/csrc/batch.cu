@@ -1,0 +1,457 @@
+// Many independent PCP solves at once (the batched form of Algorithm 2).
+//
+// Every stage runs as one launch over all instances: a batched gather, one
+// CTA per seed PCP (the seeds of different instances run side by side), a
+// batched factor assembly, and a single Algorithm 1 launch whose tile list
+// covers the column and row problems of every instance (Section 3.2: all
+// these problems are independent).  The S pass runs per instance.  The
+// launch half (batch_launch) is asynchronous and is shared with the serving
+// loop; batch_finish reads the per-instance diagnostics.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "batch.cuh"
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace pcp {
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+uint64_t splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+std::vector<int64_t> sample(int64_t n, int64_t k, uint64_t seed) {
+  std::vector<int64_t> all(n);
+  std::iota(all.begin(), all.end(), 0);
+  uint64_t s = seed;
+  for (int64_t i = 0; i < k; ++i) {
+    const int64_t j = i + (int64_t)(splitmix(s) % (uint64_t)(n - i));
+    std::swap(all[i], all[j]);
+  }
+  std::vector<int64_t> out(all.begin(), all.begin() + k);
+  std::sort(out.begin(), out.end());
+  return out;
+}
+
+struct SummaryTask {
+  const SeedCtl* ctl;
+  const int32_t* iters;
+  int64_t nprob;
+  const int32_t* bad;
+};
+
+// Per-instance diagnostics reduced on the device, so that batch_finish
+// reads the whole batch with one copy.
+__global__ void batch_summary_kernel(const SummaryTask* __restrict__ tasks,
+                                     BatchSummary* __restrict__ out) {
+  const SummaryTask t = tasks[blockIdx.x];
+  int imax = 0;
+  long long unconv = 0;
+  for (int64_t j = threadIdx.x; j < t.nprob; j += blockDim.x) {
+    const int v = t.iters[j];
+    imax = max(imax, v < 0 ? -v : v);
+    unconv += (v < 0);
+  }
+  __shared__ int smax[8];
+  __shared__ long long scnt[8];
+  for (int o = 16; o > 0; o >>= 1) {
+    imax = max(imax, __shfl_xor_sync(0xffffffffu, imax, o));
+    unconv += __shfl_xor_sync(0xffffffffu, unconv, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    smax[w] = imax;
+    scnt[w] = unconv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    BatchSummary r;
+    r.iters_max = 0;
+    r.unconverged = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      r.iters_max = max(r.iters_max, smax[q]);
+      r.unconverged += scnt[q];
+    }
+    r.rank = t.ctl->rank;
+    r.iters = t.ctl->iters;
+    r.converged = t.ctl->converged;
+    r.rank_raw = t.ctl->rank_raw;
+    r.residual = t.ctl->residual;
+    r.bad = *t.bad;
+    out[blockIdx.x] = r;
+  }
+}
+
+}  // namespace
+
+pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi) {
+  const pcp_params& q = pr.params;
+  PCP_ARG(q.m >= 2 && q.n >= 2 && q.m < (1LL << 31) && q.n < (1LL << 31),
+          "batch: m=%lld n=%lld out of range", (long long)q.m, (long long)q.n);
+  PCP_ARG(q.r >= 1 && q.r <= 32, "batch: r=%d outside [1, 32]", q.r);
+  PCP_ARG(q.precision == PCP_FP32, "batch: precision %d not available",
+          q.precision);
+  PCP_ARG(pr.dM && pr.dLu && pr.dLv && pr.ldm >= q.m &&
+              (!pr.dS || pr.lds >= q.m),
+          "batch: null pointer or leading dimension too small");
+  const int mp = (int)std::llround(q.s_r * q.r);
+  const int np = (int)std::llround(q.s_c * q.r);
+  PCP_ARG(mp >= 2 && np >= 2 && mp < q.m && np < q.n && mp <= 256 && np <= 256,
+          "batch: seed %dx%d invalid for %lldx%lld", mp, np, (long long)q.m,
+          (long long)q.n);
+  PCP_ARG(q.filter_tol > 0 && q.filter_rho > 1 && q.seed_tol > 0 &&
+              q.seed_rho > 1 && q.seed_max_iter >= 1 &&
+              q.filter_max_iter >= 1 && q.beta0_scale > 0 &&
+              q.beta_bar_ratio >= 1 && q.seed_mu_scale > 0 &&
+              q.seed_mu_max_ratio >= 1,
+          "batch: bad tolerances or penalty constants");
+  bi->mp = mp;
+  bi->np = np;
+  int k0 = q.seed_subspace > 0 ? q.seed_subspace : q.r + std::max(6, q.r / 4);
+  k0 = (k0 + 1) / 2 * 2;
+  const int kcap = std::min(std::min(mp, np) / 2 * 2, 64);
+  bi->k0 = std::min(k0, kcap);
+  bi->kmax = std::min(kcap, std::max(bi->k0 + 16, 2 * bi->k0) / 2 * 2);
+  bi->lam_seed = q.lambda_seed > 0
+                     ? q.lambda_seed
+                     : 1.0 / std::sqrt((double)std::max(mp, np));
+  bi->lam_full = q.lambda > 0 ? q.lambda
+                              : 1.0 / std::sqrt((double)std::max(q.m, q.n));
+  auto check = [&](const int64_t* v, int64_t k, int64_t n) {
+    std::vector<char> seen(n, 0);
+    for (int64_t i = 0; i < k; ++i) {
+      if (v[i] < 0 || v[i] >= n || seen[v[i]]) return false;
+      seen[v[i]] = 1;
+    }
+    return true;
+  };
+  PCP_ARG(!q.seed_rows || check(q.seed_rows, mp, q.m),
+          "batch: seed_rows out of range or repeated");
+  PCP_ARG(!q.seed_cols || check(q.seed_cols, np, q.n),
+          "batch: seed_cols out of range or repeated");
+  return PCP_OK;
+}
+
+size_t batch_footprint(const pcp_problem& pr, const BatchInstance& bi) {
+  const pcp_params& q = pr.params;
+  const int64_t nrb = q.m - bi.mp, ncb = q.n - bi.np;
+  size_t b = 0;
+  b += align256(sizeof(int32_t) * (q.m + q.n));                  // indices
+  b += align256(sizeof(double) * bi.mp * bi.np);                 // M^s
+  b += align256(seed_workspace_bytes_cta(bi.mp, bi.np, bi.kmax));
+  b += align256(sizeof(double) * (bi.mp + bi.np + 1) * bi.kmax); // U, S, V
+  b += align256(sizeof(float) * ((bi.mp + bi.np) * q.r + q.r));  // FP32 copies
+  b += align256(sizeof(int32_t) * (nrb + ncb + 1));              // iters, bad
+  return b + 8192;  // share of the batch-wide argument blocks
+}
+
+pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
+                        BatchHandle* h, bool timed) {
+  PCP_ARG(count >= 1 && count <= 65535,
+          "batch: count %d outside [1, 65535]", count);
+  h->count = count;
+  h->inst.assign(count, BatchInstance());
+  h->probs.assign(probs, probs + count);
+  h->d_base = nullptr;
+  for (int i = 0; i < count; ++i) {
+    pcp_status s = batch_validate(probs[i], &h->inst[i]);
+    if (s != PCP_OK) {
+      set_error("batch instance %d: %s", i, pcp_last_error());
+      return s;
+    }
+  }
+  // ---- device layout ------------------------------------------------------
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  std::vector<size_t> o_idx(count), o_Ms(count), o_work(count), o_U(count),
+      o_Sig(count), o_V(count), o_U32(count), o_V32(count), o_isg(count),
+      o_it(count);
+  int64_t idx_total = 0;
+  for (int i = 0; i < count; ++i) {
+    const pcp_params& q = probs[i].params;
+    const BatchInstance& b = h->inst[i];
+    o_idx[i] = take(sizeof(int32_t) * (q.m + q.n));
+    idx_total += q.m + q.n;
+    o_Ms[i] = take(sizeof(double) * b.mp * b.np);
+    o_work[i] = take(seed_workspace_bytes_cta(b.mp, b.np, b.kmax));
+    o_U[i] = take(sizeof(double) * b.mp * b.kmax);
+    o_Sig[i] = take(sizeof(double) * b.kmax);
+    o_V[i] = take(sizeof(double) * b.np * b.kmax);
+    o_U32[i] = take(sizeof(float) * b.mp * q.r);
+    o_V32[i] = take(sizeof(float) * b.np * q.r);
+    o_isg[i] = take(sizeof(float) * q.r);
+    o_it[i] = take(sizeof(int32_t) * ((q.m - b.mp) + (q.n - b.np)));
+  }
+  const size_t o_bad = take(sizeof(int32_t) * count);
+  const size_t o_sargs = take(seed_batched_args_bytes(count));
+  const size_t o_gat = take(sizeof(GatherTask) * count);
+  const size_t o_asm = take(sizeof(AssembleTask) * count);
+  const size_t o_stask = take(sizeof(SummaryTask) * count);
+  const size_t o_sum = take(sizeof(BatchSummary) * count);
+  // filter sets: two per instance
+  std::vector<FilterSet> sets(2 * count);
+  for (int i = 0; i < count; ++i) {
+    const pcp_params& q = probs[i].params;
+    const BatchInstance& b = h->inst[i];
+    sets[2 * i].N = (int)(q.n - b.np);
+    sets[2 * i + 1].N = (int)(q.m - b.mp);
+  }
+  const size_t fbytes = filter_batch_bytes(sets.data(), 2 * count);
+  const size_t o_filt = take(fbytes);
+  h->bytes = off;
+  PCP_CUDA(cudaMallocAsync(&h->d_base, off, st));
+  char* base = static_cast<char*>(h->d_base);
+
+  // ---- host staging: indices, then the argument blocks ----------------------
+  std::vector<int32_t> hidx((size_t)idx_total);
+  int64_t pos = 0;
+  for (int i = 0; i < count; ++i) {
+    const pcp_params& q = probs[i].params;
+    BatchInstance& b = h->inst[i];
+    std::vector<int64_t> rows =
+        q.seed_rows ? std::vector<int64_t>(q.seed_rows, q.seed_rows + b.mp)
+                    : sample(q.m, b.mp, q.rng_seed);
+    std::vector<int64_t> cols =
+        q.seed_cols ? std::vector<int64_t>(q.seed_cols, q.seed_cols + b.np)
+                    : sample(q.n, b.np, q.rng_seed ^ 0xC01C01C0ull);
+    b.rows = rows;
+    b.cols = cols;
+    std::vector<char> in_r(q.m, 0), in_c(q.n, 0);
+    int32_t* hp = hidx.data() + pos;
+    int64_t o = 0;
+    for (int64_t v : rows) { hp[o++] = (int32_t)v; in_r[v] = 1; }
+    for (int64_t v : cols) { hp[o++] = (int32_t)v; in_c[v] = 1; }
+    for (int64_t v = 0; v < q.m; ++v) if (!in_r[v]) hp[o++] = (int32_t)v;
+    for (int64_t v = 0; v < q.n; ++v) if (!in_c[v]) hp[o++] = (int32_t)v;
+    pos += q.m + q.n;
+  }
+  // indices are contiguous per instance; each instance's block is 256-byte
+  // aligned, so copy instance by instance
+  pos = 0;
+  for (int i = 0; i < count; ++i) {
+    const pcp_params& q = probs[i].params;
+    PCP_CUDA(cudaMemcpyAsync(base + o_idx[i], hidx.data() + pos,
+                             sizeof(int32_t) * (q.m + q.n),
+                             cudaMemcpyHostToDevice, st));
+    pos += q.m + q.n;
+  }
+  PCP_CUDA(cudaMemsetAsync(base + o_bad, 0, sizeof(int32_t) * count, st));
+
+  std::vector<GatherTask> gat(count);
+  std::vector<SeedTask> seeds(count);
+  std::vector<AssembleTask> asmb(count);
+  for (int i = 0; i < count; ++i) {
+    const pcp_params& q = probs[i].params;
+    const pcp_problem& pr = probs[i];
+    BatchInstance& b = h->inst[i];
+    int32_t* d_idx = reinterpret_cast<int32_t*>(base + o_idx[i]);
+    b.d_rows = d_idx;
+    b.d_cols = d_idx + b.mp;
+    b.d_rbar = d_idx + b.mp + b.np;
+    b.d_cbar = d_idx + b.mp + b.np + (q.m - b.mp);
+    b.d_work = base + o_work[i];
+    b.d_iters = reinterpret_cast<int32_t*>(base + o_it[i]);
+    b.d_bad = reinterpret_cast<int32_t*>(base + o_bad) + i;
+    double* Ms = reinterpret_cast<double*>(base + o_Ms[i]);
+    gat[i] = GatherTask{pr.dM, pr.ldm, b.d_rows, b.d_cols, b.mp, b.np, Ms,
+                        b.d_bad};
+    SeedTask& t = seeds[i];
+    t.D = Ms;
+    t.mp = b.mp;
+    t.np = b.np;
+    t.k0 = b.k0;
+    t.kmax = b.kmax;
+    t.max_iter = q.seed_max_iter;
+    t.r_cap = q.r;
+    t.lam = b.lam_seed;
+    t.tol = q.seed_tol;
+    t.rho = q.seed_rho;
+    t.mu_scale = q.seed_mu_scale;
+    t.mu_max_ratio = q.seed_mu_max_ratio;
+    t.rank_cut = q.rank_cut;
+    t.work = b.d_work;
+    t.U = reinterpret_cast<double*>(base + o_U[i]);
+    t.Sigma = reinterpret_cast<double*>(base + o_Sig[i]);
+    t.V = reinterpret_cast<double*>(base + o_V[i]);
+    b.d_rank = seed_rank_ptr_cta(b.d_work, b.mp, b.np, b.kmax);
+    float* U32 = reinterpret_cast<float*>(base + o_U32[i]);
+    float* V32 = reinterpret_cast<float*>(base + o_V32[i]);
+    float* isg = reinterpret_cast<float*>(base + o_isg[i]);
+    asmb[i] = AssembleTask{t.U, t.Sigma, t.V, b.mp, b.np, b.kmax, q.r,
+                           b.d_rank, b.d_rows, b.d_cols, pr.dLu, pr.dLv,
+                           q.m, q.n, U32, V32, isg};
+    const int64_t ncb = q.n - b.np, nrb = q.m - b.mp;
+    sets[2 * i] = FilterSet{pr.dM, b.d_rows, b.mp, 1, b.d_cbar, (int)ncb,
+                            pr.ldm, U32, b.mp, q.r, b.d_rank, nullptr, pr.dLv,
+                            q.n, b.d_iters, q.filter_tol, q.filter_rho,
+                            q.beta0_scale, q.beta_bar_ratio,
+                            q.filter_max_iter};
+    sets[2 * i + 1] = FilterSet{pr.dM, b.d_cols, b.np, pr.ldm, b.d_rbar,
+                                (int)nrb, 1, V32, b.np, q.r, b.d_rank, isg,
+                                pr.dLu, q.m, b.d_iters + ncb, q.filter_tol,
+                                q.filter_rho, q.beta0_scale,
+                                q.beta_bar_ratio, q.filter_max_iter};
+  }
+  // host blocks for the argument copies must outlive the async copies; the
+  // handle keeps them
+  h->h_gat.resize(sizeof(GatherTask) * count);
+  h->h_asm.resize(sizeof(AssembleTask) * count);
+  h->h_sargs.resize(seed_batched_args_bytes(count));
+  h->h_filt.resize(fbytes);
+  if (timed) {
+    for (cudaEvent_t& e : h->ev) PCP_CUDA(cudaEventCreate(&e));
+    PCP_CUDA(cudaEventRecord(h->ev[0], st));
+  }
+  pcp_status s;
+  if ((s = gather_batched_async(gat.data(), count, h->h_gat.data(),
+                                base + o_gat, st)) != PCP_OK)
+    return s;
+  if ((s = seed_pcp_batched_async(seeds.data(), count, h->h_sargs.data(),
+                                  base + o_sargs, st)) != PCP_OK)
+    return s;
+  if ((s = assemble_batched_async(asmb.data(), count, h->h_asm.data(),
+                                  base + o_asm, st)) != PCP_OK)
+    return s;
+  if (timed) PCP_CUDA(cudaEventRecord(h->ev[1], st));
+  if ((s = l1_filter_batched_async(sets.data(), 2 * count, h->h_filt.data(),
+                                   base + o_filt, st)) != PCP_OK)
+    return s;
+  if (timed) PCP_CUDA(cudaEventRecord(h->ev[2], st));
+  h->h_stask.resize(sizeof(SummaryTask) * count);
+  SummaryTask* stask = reinterpret_cast<SummaryTask*>(h->h_stask.data());
+  for (int i = 0; i < count; ++i) {
+    const pcp_params& q = probs[i].params;
+    const BatchInstance& b = h->inst[i];
+    stask[i] = SummaryTask{seed_ctl_ptr_cta(b.d_work, b.mp, b.np, b.kmax),
+                           b.d_iters, (q.m - b.mp) + (q.n - b.np), b.d_bad};
+  }
+  h->d_summary = reinterpret_cast<BatchSummary*>(base + o_sum);
+  PCP_CUDA(cudaMemcpyAsync(base + o_stask, stask, sizeof(SummaryTask) * count,
+                           cudaMemcpyHostToDevice, st));
+  batch_summary_kernel<<<count, 256, 0, st>>>(
+      reinterpret_cast<const SummaryTask*>(base + o_stask), h->d_summary);
+  PCP_CUDA(cudaGetLastError());
+  for (int i = 0; i < count; ++i) {
+    const pcp_problem& pr = probs[i];
+    if (!pr.dS) continue;
+    s = pcp_spass(pr.dM, pr.ldm, pr.dLu, pr.params.m, pr.dLv, pr.params.n,
+                  pr.params.r, pr.dS, pr.lds, pr.params.m, pr.params.n, st);
+    if (s != PCP_OK) return s;
+  }
+  if (timed) PCP_CUDA(cudaEventRecord(h->ev[3], st));
+  return PCP_OK;
+}
+
+pcp_status batch_finish(BatchHandle* h, pcp_info* infos, cudaStream_t st,
+                        float batch_ms) {
+  pcp_status first = PCP_OK;
+  if (infos) {
+    std::vector<BatchSummary> sum(h->count);
+    PCP_CUDA(cudaMemcpyAsync(sum.data(), h->d_summary,
+                             sizeof(BatchSummary) * h->count,
+                             cudaMemcpyDeviceToHost, st));
+    PCP_CUDA(cudaStreamSynchronize(st));
+    float stage_ms[3] = {0.0f, 0.0f, 0.0f};
+    if (h->ev[0])
+      for (int q = 0; q < 3; ++q)
+        cudaEventElapsedTime(&stage_ms[q], h->ev[q], h->ev[q + 1]);
+    h->status.clear();
+    for (int i = 0; i < h->count; ++i) {
+      const pcp_params& q = h->probs[i].params;
+      const BatchInstance& b = h->inst[i];
+      const BatchSummary& u = sum[i];
+      pcp_info& inf = infos[i];
+      std::memset(&inf, 0, sizeof(inf));
+      inf.rank = u.rank;
+      inf.seed_iters = u.iters;
+      inf.seed_residual = u.residual;
+      inf.seed_m = b.mp;
+      inf.seed_n = b.np;
+      inf.problems = (q.m - b.mp) + (q.n - b.np);
+      inf.lambda = b.lam_full;
+      inf.filter_iters_max = u.iters_max;
+      inf.problems_unconverged = u.unconverged;
+      inf.rank_ok = (u.rank_raw >= 1 &&
+                     (double)b.mp / u.rank_raw >= q.s_r - 1e-9 &&
+                     (double)b.np / u.rank_raw >= q.s_c - 1e-9)
+                        ? 1
+                        : 0;
+      inf.t_total_ms = batch_ms;
+      inf.t_seed_ms = stage_ms[0];   // stage times of the whole batch
+      inf.t_filter_ms = stage_ms[1];
+      inf.t_spass_ms = stage_ms[2];
+      pcp_status si = PCP_OK;
+      if (u.bad) si = PCP_ERR_NONFINITE;
+      else if (!u.converged) si = PCP_ERR_SEED_NOCONV;
+      else if (!inf.rank_ok) si = PCP_ERR_RANK_TEST;
+      else if (u.unconverged) si = PCP_ERR_FILTER_NOCONV;
+      inf.status = (int32_t)si;
+      if (si != PCP_OK && first == PCP_OK) {
+        first = si;
+        set_error("batch instance %d: status %d (rank %d, raw %d, iters %d)",
+                  i, (int)si, u.rank, u.rank_raw, u.iters);
+      }
+      h->status.push_back(si);
+    }
+  }
+  for (cudaEvent_t& e : h->ev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
+  if (h->d_base) {
+    PCP_CUDA(cudaFreeAsync(h->d_base, st));
+    h->d_base = nullptr;
+  }
+  return first;
+}
+
+}  // namespace pcp
+
+extern "C" pcp_status pcp_l1filter_batch(int32_t count,
+                                         const pcp_problem* probs,
+                                         pcp_info* infos, void* stream) {
+  PCP_ARG(count >= 0, "pcp_l1filter_batch: count < 0");
+  if (count == 0) return PCP_OK;
+  PCP_ARG(probs, "pcp_l1filter_batch: null problems");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (infos) {
+    PCP_CUDA(cudaEventCreate(&e0));
+    PCP_CUDA(cudaEventCreate(&e1));
+    PCP_CUDA(cudaEventRecord(e0, st));
+  }
+  pcp::BatchHandle h;
+  pcp_status s = pcp::batch_launch(count, probs, st, &h, infos != nullptr);
+  if (s != PCP_OK) {
+    if (h.d_base) cudaFreeAsync(h.d_base, st);
+    for (cudaEvent_t e : h.ev)
+      if (e) cudaEventDestroy(e);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return s;
+  }
+  float ms = 0.0f;
+  if (infos) {
+    PCP_CUDA(cudaEventRecord(e1, st));
+    PCP_CUDA(cudaEventSynchronize(e1));
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  return pcp::batch_finish(&h, infos, st, ms);
+}

@@ -1,0 +1,56 @@
+// Internal: the asynchronous halves of the batched solve, shared by
+// pcp_l1filter_batch and the serving loop.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace pcp {
+
+struct BatchInstance {
+  int mp = 0, np = 0, k0 = 0, kmax = 0;
+  double lam_seed = 0, lam_full = 0;
+  std::vector<int64_t> rows, cols;
+  int32_t *d_rows = nullptr, *d_cols = nullptr, *d_rbar = nullptr,
+          *d_cbar = nullptr;
+  void* d_work = nullptr;
+  int32_t *d_iters = nullptr, *d_bad = nullptr;
+  int* d_rank = nullptr;
+};
+
+// Per-instance diagnostics, reduced on the device at the end of a batch.
+struct BatchSummary {
+  int rank, iters, converged, rank_raw, bad, iters_max;
+  long long unconverged;
+  double residual;
+};
+
+struct BatchHandle {
+  int count = 0;
+  std::vector<BatchInstance> inst;
+  std::vector<pcp_problem> probs;
+  void* d_base = nullptr;  // one stream-ordered allocation
+  size_t bytes = 0;
+  std::vector<char> h_gat, h_asm, h_sargs, h_filt, h_stask;
+  BatchSummary* d_summary = nullptr;
+  // stage boundaries (start, seed done, filters done, S pass done) when
+  // the launch is timed
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<pcp_status> status;
+};
+
+pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi);
+// Device workspace one instance needs (its share of a batch).
+size_t batch_footprint(const pcp_problem& pr, const BatchInstance& bi);
+// Enqueue the whole batch on st (asynchronous; allocates with
+// cudaMallocAsync on st).
+pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
+                        BatchHandle* h, bool timed = false);
+// With infos: synchronise st, fill one pcp_info (and h->status) per
+// instance.  Always releases the workspace (stream-ordered).
+pcp_status batch_finish(BatchHandle* h, pcp_info* infos, cudaStream_t st,
+                        float batch_ms);
+
+}  // namespace pcp

@@ -25,8 +25,11 @@
 //     converged writes its z and is frozen (its lanes keep computing but
 //     never write again) so every problem stops exactly at its own test.
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "common.cuh"
+#include "internal.cuh"
 
 namespace pcp {
 
@@ -69,9 +72,10 @@ __device__ __forceinline__ void load_arow(const float* __restrict__ As, int t,
   }
 }
 
+// Algorithm 1 on the 32 problems of tile `tile` of set `a`.
 template <int SPT, int RMAX>
-__global__ void __launch_bounds__(kThreads, 1)
-    adm_f32_kernel(const FilterArgs a) {
+__device__ __forceinline__ void adm_f32_tile(const FilterArgs& a,
+                                             const int tile) {
   extern __shared__ __align__(16) float smem[];
   float* As = smem;                                 // [kWarps*SPT][RMAX]
   float* red = As + kWarps * SPT * RMAX;            // [kWarps][RMAX][32]
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  const int j = blockIdx.x * 32 + lane;
+  const int j = tile * 32 + lane;
   const bool valid = j < a.N;
   const int p = a.p;
   int reff = a.r;
@@ -213,6 +217,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int SPT, int RMAX>
+__global__ void __launch_bounds__(kThreads, 1)
+    adm_f32_kernel(const FilterArgs a) {
+  adm_f32_tile<SPT, RMAX>(a, blockIdx.x);
+}
+
+// Batched form: CTA b runs tile tiles[2b+1] of set tiles[2b].
+template <int SPT, int RMAX>
+__global__ void __launch_bounds__(kThreads, 1)
+    adm_f32_batched_kernel(const FilterArgs* __restrict__ sets,
+                           const int32_t* __restrict__ tiles) {
+  const FilterArgs a = sets[tiles[2 * blockIdx.x]];
+  adm_f32_tile<SPT, RMAX>(a, tiles[2 * blockIdx.x + 1]);
+}
+
+template <int SPT, int RMAX>
 size_t adm_smem_bytes() {
   return sizeof(float) * ((size_t)kWarps * SPT * RMAX +
                           (size_t)kWarps * RMAX * 32 + (size_t)RMAX * 32 +
@@ -244,7 +263,124 @@ cudaError_t dispatch_r(const FilterArgs& a, cudaStream_t st) {
   return cudaErrorInvalidValue;
 }
 
+// Batched launches: the shape class of a set is (SPT index, RMAX index).
+int shape_class(int p, int r) {
+  const int si = p <= 64 ? 0 : (p <= 128 ? 1 : 2);
+  return si * 4 + (r - 1) / 8;
+}
+
+template <int SPT, int RMAX>
+cudaError_t launch_adm_batched(const FilterArgs* d_sets, const int32_t* d_tiles,
+                               int ntiles, cudaStream_t st) {
+  const size_t smem = adm_smem_bytes<SPT, RMAX>();
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(
+        adm_f32_batched_kernel<SPT, RMAX>,
+        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  adm_f32_batched_kernel<SPT, RMAX><<<ntiles, kThreads, smem, st>>>(d_sets,
+                                                                    d_tiles);
+  return cudaGetLastError();
+}
+
+template <int SPT>
+cudaError_t dispatch_batched_r(int ri, const FilterArgs* d_sets,
+                               const int32_t* d_tiles, int ntiles,
+                               cudaStream_t st) {
+  switch (ri) {
+    case 0: return launch_adm_batched<SPT, 8>(d_sets, d_tiles, ntiles, st);
+    case 1: return launch_adm_batched<SPT, 16>(d_sets, d_tiles, ntiles, st);
+    case 2: return launch_adm_batched<SPT, 24>(d_sets, d_tiles, ntiles, st);
+    case 3: return launch_adm_batched<SPT, 32>(d_sets, d_tiles, ntiles, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+constexpr int kShapeClasses = 12;
+
+size_t args_block_bytes(int nsets) {
+  return (sizeof(FilterArgs) * (size_t)nsets + 255) / 256 * 256;
+}
+
 }  // namespace
+
+size_t filter_batch_bytes(const FilterSet* sets, int nsets) {
+  size_t tiles = 0;
+  for (int i = 0; i < nsets; ++i) tiles += (size_t)(sets[i].N + 31) / 32;
+  return args_block_bytes(nsets) + 8 * tiles + 16 * kShapeClasses;
+}
+
+pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
+                                   void* h_buf, void* d_buf,
+                                   cudaStream_t st) {
+  if (nsets <= 0) return PCP_OK;
+  char* hb = static_cast<char*>(h_buf);
+  FilterArgs* ha = reinterpret_cast<FilterArgs*>(hb);
+  std::vector<std::vector<int32_t>> by_class(kShapeClasses);
+  for (int i = 0; i < nsets; ++i) {
+    const FilterSet& f = sets[i];
+    PCP_ARG(f.p >= 1 && f.p <= 256 && f.r >= 1 && f.r <= 32 && f.N >= 0,
+            "batched filter: set %d has p=%d r=%d N=%d", i, f.p, f.r, f.N);
+    FilterArgs a;
+    a.M = f.M;
+    a.pidx = f.pidx;
+    a.p = f.p;
+    a.sp = f.sp;
+    a.qidx = f.qidx;
+    a.N = f.N;
+    a.sq = f.sq;
+    a.A = f.A;
+    a.lda = f.lda;
+    a.r = f.r;
+    a.d_rank = f.d_rank;
+    a.scale = f.scale;
+    a.Z = f.Z;
+    a.ldz = f.ldz;
+    a.eps = (float)f.eps;
+    a.rho = (float)f.rho;
+    a.beta0_scale = (float)f.beta0_scale;
+    a.beta_bar_ratio = (float)f.beta_bar_ratio;
+    a.max_iter = f.max_iter;
+    a.iters_out = f.iters_out;
+    std::memcpy(ha + i, &a, sizeof(a));
+    std::vector<int32_t>& t = by_class[shape_class(f.p, f.r)];
+    for (int b = 0; b < (f.N + 31) / 32; ++b) {
+      t.push_back(i);
+      t.push_back(b);
+    }
+  }
+  size_t off = args_block_bytes(nsets);
+  size_t used = off;
+  std::vector<size_t> class_off(kShapeClasses, 0);
+  for (int c = 0; c < kShapeClasses; ++c) {
+    if (by_class[c].empty()) continue;
+    class_off[c] = used;
+    std::memcpy(hb + used, by_class[c].data(), 4 * by_class[c].size());
+    used += (4 * by_class[c].size() + 15) / 16 * 16;
+  }
+  PCP_CUDA(cudaMemcpyAsync(d_buf, h_buf, used, cudaMemcpyHostToDevice, st));
+  char* db = static_cast<char*>(d_buf);
+  const FilterArgs* d_sets = reinterpret_cast<const FilterArgs*>(db);
+  for (int c = 0; c < kShapeClasses; ++c) {
+    if (by_class[c].empty()) continue;
+    const int ntiles = (int)(by_class[c].size() / 2);
+    const int32_t* d_tiles = reinterpret_cast<const int32_t*>(db + class_off[c]);
+    const int si = c / 4, ri = c % 4;
+    cudaError_t e;
+    if (si == 0)
+      e = dispatch_batched_r<8>(ri, d_sets, d_tiles, ntiles, st);
+    else if (si == 1)
+      e = dispatch_batched_r<16>(ri, d_sets, d_tiles, ntiles, st);
+    else
+      e = dispatch_batched_r<32>(ri, d_sets, d_tiles, ntiles, st);
+    if (e != cudaSuccess)
+      return cuda_fail(e, "adm_f32_batched_kernel launch", __FILE__, __LINE__);
+  }
+  return PCP_OK;
+}
 
 }  // namespace pcp
 

@@ -1,0 +1,106 @@
+// Internal (not exported) entry points shared between translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace pcp {
+
+// Control block of one seed PCP solve (device memory, start of its
+// workspace): barrier state, status and diagnostics.
+struct SeedCtl {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int error;
+  int iters;
+  int rank;
+  int converged;
+  int k_final;
+  int rank_raw;
+  int ntrace;
+  int jsweeps;     // total Jacobi sweeps (block 0), for tracing
+  long long jcyc[4];  // block 0 Jacobi cycles: angles, A, V, end-of-round
+  long long sub[8];   // block 0 sub-step cycle counters (tracing)
+  double residual;
+  double sigma1;
+  double pad[4];
+};
+
+// One seed PCP instance for the batched (one CTA per seed) solver.
+struct SeedTask {
+  const double* D;  // mp x np, FP64, ld mp
+  int mp, np, k0, kmax, max_iter, r_cap;
+  double lam, tol, rho, mu_scale, mu_max_ratio, rank_cut;
+  void* work;  // seed_workspace_bytes_cta(mp, np, kmax) bytes
+  double *U, *Sigma, *V;  // outputs, ld mp / np, kmax columns
+};
+
+size_t seed_workspace_bytes_cta(int mp, int np, int kmax);
+size_t seed_args_bytes();  // bytes of one packed per-instance argument block
+// Bytes of the host / device argument area of a batched seed launch.
+size_t seed_batched_args_bytes(int count);
+// Pack the tasks into h_args (seed_batched_args_bytes(count) bytes), copy
+// them to d_args and launch: a team of CTAs per seed, sized by its work
+// (cooperative launch) when every seed gets at least one co-resident CTA,
+// else one CTA per seed.
+pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
+                                  void* h_args, void* d_args,
+                                  cudaStream_t st);
+// Device addresses of the control block / the seed rank (int) inside a
+// CTA-solver workspace.
+SeedCtl* seed_ctl_ptr_cta(void* d_work, int mp, int np, int kmax);
+int* seed_rank_ptr_cta(void* d_work, int mp, int np, int kmax);
+
+// One set of Algorithm 1 problems for the batched filter (the arguments of
+// pcp_l1_filter, constants included, so that every set keeps its own).
+struct FilterSet {
+  const float* M;
+  const int32_t* pidx;
+  int p;
+  int64_t sp;
+  const int32_t* qidx;
+  int N;
+  int64_t sq;
+  const float* A;
+  int lda;
+  int r;
+  const int32_t* d_rank;
+  const float* scale;
+  float* Z;
+  int64_t ldz;
+  int32_t* iters_out;
+  double eps, rho, beta0_scale, beta_bar_ratio;
+  int max_iter;
+};
+// Bytes of the device argument block for these sets (h_buf and d_buf).
+size_t filter_batch_bytes(const FilterSet* sets, int nsets);
+// All sets, 32 problems per CTA, one launch per kernel shape present (the
+// shape is fixed by p and r; sets of equal shape share a launch).
+pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
+                                   void* h_buf, void* d_buf,
+                                   cudaStream_t st);
+
+// Batched gather / assembly: one launch for all instances.
+struct GatherTask {
+  const float* M;
+  int64_t ldm;
+  const int32_t* rows;
+  const int32_t* cols;
+  int mp, np;
+  double* Ms;
+  int32_t* bad;
+};
+pcp_status gather_batched_async(const GatherTask* tasks, int count,
+                                void* h_buf, void* d_buf, cudaStream_t st);
+struct AssembleTask {
+  const double *U, *Sigma, *V;
+  int mp, np, ku, r;
+  const int32_t* d_rank;
+  const int32_t *rows, *cols;
+  float *Lu, *Lv;
+  int64_t ldu, ldv;
+  float *U32, *V32, *inv_sigma32;
+};
+pcp_status assemble_batched_async(const AssembleTask* tasks, int count,
+                                  void* h_buf, void* d_buf, cudaStream_t st);
+
+}  // namespace pcp

@@ -36,40 +36,27 @@
 // bit-identical factors.  Cross-CTA data is read with L2-only loads
 // (ld.global.cg) so no CTA sees a stale L1 line.
 #include <algorithm>
+#include <cstring>
 #include <mutex>
+#include <queue>
+#include <vector>
 
 #include "common.cuh"
+#include "internal.cuh"
 
 namespace pcp {
 
 constexpr int kSeedThreads = 256;
 constexpr int kSeedKmaxLimit = 64;
 constexpr int kSeedTraceCap = 4096;  // (timestamp, phase) records
-
-struct SeedCtl {
-  unsigned int bar_count;
-  unsigned int bar_gen;
-  int error;
-  int iters;
-  int rank;
-  int converged;
-  int k_final;
-  int rank_raw;
-  int ntrace;
-  int jsweeps;     // total Jacobi sweeps (block 0), for tracing
-  long long jcyc[4];  // block 0 Jacobi cycles: angles, A, V, end-of-round
-  long long sub[8];   // block 0 sub-step cycle counters (tracing)
-  double residual;
-  double sigma1;
-  double pad[4];
-};
+constexpr int kSeedTeamMax = 64;     // largest team of the batched solver
 
 struct SeedLayout {
   size_t ctl, part, colsq, S, Y, G, Gt, Om, P, Pt, T, Psi, PsiT, Gam, Gam2,
       trace, total;
 };
 
-SeedLayout seed_layout(int mp, int np, int kmax) {
+SeedLayout seed_layout(int mp, int np, int kmax, int nbmax) {
   SeedLayout L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -79,8 +66,8 @@ SeedLayout seed_layout(int mp, int np, int kmax) {
   };
   const size_t mn = (size_t)mp * np * sizeof(double);
   L.ctl = take(sizeof(SeedCtl));
-  L.part = take((size_t)kMaxCoopBlocks * 4 * sizeof(double));
-  L.colsq = take((size_t)kMaxCoopBlocks * kmax * sizeof(double));
+  L.part = take((size_t)nbmax * 4 * sizeof(double));
+  L.colsq = take((size_t)nbmax * kmax * sizeof(double));
   L.S = take(mn);
   L.Y = take(mn);
   L.G = take(mn);
@@ -98,17 +85,30 @@ SeedLayout seed_layout(int mp, int np, int kmax) {
   return L;
 }
 
+// Workspace of the cooperative (one seed over the whole GPU) solver.
 size_t seed_workspace_bytes(int mp, int np, int kmax) {
-  return seed_layout(mp, np, kmax).total;
+  return seed_layout(mp, np, kmax, kMaxCoopBlocks).total;
+}
+
+// Workspace of one instance of the batched solver (a team of at most
+// kSeedTeamMax CTAs per seed).
+size_t seed_workspace_bytes_cta(int mp, int np, int kmax) {
+  return seed_layout(mp, np, kmax, kSeedTeamMax).total;
 }
 
 namespace {
 
-struct SeedArgs {
+// 16-byte aligned: the batched launch packs these back to back with a
+// stride of sizeof(SeedArgs), which device code indexes the same way
+struct alignas(16) SeedArgs {
   const double* D;
   int mp, np, kmax, k0;
   double lam, tol, rho, mu_scale, mu_max_ratio, rank_cut;
   int max_iter, r_cap;
+  // partial-sum slots of the three reductions (norms of D, Ritz values,
+  // residual): fixed per solve, so the summation order (and the result)
+  // does not depend on how many CTAs the team has
+  int nv;
   unsigned long long timeout_ns;
   SeedCtl* ctl;
   double* part;
@@ -160,7 +160,7 @@ __device__ bool grid_sync(SeedCtl* ctl, unsigned int nblocks,
 
 // Block 0 records (globaltimer, phase) after the phase ends.
 __device__ __forceinline__ void trace_mark(const SeedArgs& a, int phase) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) {
     const int i = a.ctl->ntrace;
     if (i < kSeedTraceCap) {
       a.trace[2 * i] = globaltimer_ns();
@@ -223,11 +223,11 @@ __device__ double sum_partials(const double* src, int nb, int stride, int off,
 // loads of B overlap.
 __device__ void tall_gemm_t(const double* X, int ldx, int len, int ntask,
                             const double* B, int k, int kmax, double* out,
-                            double* red, double* xs) {
+                            double* red, double* xs, int bid, int nblk) {
   const int tid = threadIdx.x;
   const int nparts = kSeedThreads / k;
   const int c = tid % k, part = tid / k;
-  for (int task = blockIdx.x; task < ntask; task += gridDim.x) {
+  for (int task = bid; task < ntask; task += nblk) {
     const double* x = X + (size_t)task * ldx;
     for (int t = tid; t < len; t += kSeedThreads) xs[t] = ldg_cg(x + t);
     __syncthreads();
@@ -261,10 +261,10 @@ __device__ void tall_gemm_t(const double* X, int ldx, int len, int ntask,
 // Gm = X^T X (k x k) for X (nrows x k, row-major stride kmax); one warp per
 // entry a <= b, both triangles written.
 __device__ void gram(const double* X, int nrows, int k, int kmax,
-                     double* Gm) {
+                     double* Gm, int bid, int nblk) {
   const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (kSeedThreads / 32) + (threadIdx.x >> 5);
-  const int nw = gridDim.x * (kSeedThreads / 32);
+  const int gw = bid * (kSeedThreads / 32) + (threadIdx.x >> 5);
+  const int nw = nblk * (kSeedThreads / 32);
   const int npairs = k * (k + 1) / 2;
   for (int pq = gw; pq < npairs; pq += nw) {
     // pq -> (a, b) with a <= b, row-major over the upper triangle
@@ -306,9 +306,10 @@ __device__ void gram(const double* X, int nrows, int k, int kmax,
 __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
                              const double* Gm, double* Out, float* A32,
                              float* Ri32, double* dsc, int* dead,
-                             double* rowb, long long* sub = nullptr) {
+                             double* rowb, int bid, int nblk, int row_warps,
+                             long long* sub) {
   const int tid = threadIdx.x;
-  const bool prof = sub && blockIdx.x == 0 && tid == 0;
+  const bool prof = sub && bid == 0 && tid == 0;
   long long q0 = prof ? clock64() : 0;
   __shared__ float s_inv[2];
   for (int c = tid; c < k; c += kSeedThreads) {
@@ -367,10 +368,11 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
   for (int c = tid; c < k; c += kSeedThreads) Ri32[c] = 1.0f / A32[c * k + c];
   __syncthreads();
   long long q2 = prof ? clock64() : 0;
-  // one warp per CTA: the FP64 pipe is narrow on this part, so the rows are
-  // spread over as many SMs as possible rather than over warps of few CTAs
-  const int lane = tid & 31;
-  for (int t = (tid < 32) ? blockIdx.x : nrows; t < nrows; t += gridDim.x) {
+  // row_warps warps per CTA (1 for a grid-wide team: the FP64 pipe is
+  // narrow on this part, so rows are spread over as many SMs as possible)
+  const int lane = tid & 31, wid = tid >> 5;
+  for (int t = (wid < row_warps) ? bid * row_warps + wid : nrows; t < nrows;
+       t += nblk * row_warps) {
     const int c0 = lane, c1 = lane + 32;
     double p0 = c0 < k ? ldg_cg(X + (size_t)t * kmax + c0) * dsc[c0] : 0.0;
     double p1 = c1 < k ? ldg_cg(X + (size_t)t * kmax + c1) * dsc[c1] : 0.0;
@@ -504,8 +506,12 @@ __device__ float* block_jacobi32(float* A0, float* A1, float* V, int k,
   return A;
 }
 
-__global__ void __launch_bounds__(kSeedThreads, 2)
-    seed_alm_kernel(const SeedArgs a) {
+// The ALM body, run by a team of CTAs: the whole cooperative grid (kGrid,
+// phases separated by the software grid barrier) or a single CTA (one seed
+// per CTA, phases separated by __syncthreads).  b / nb: this CTA's position
+// in the team.
+template <bool kGrid>
+__device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
   extern __shared__ __align__(16) double sm[];
   const int kmax = a.kmax;
   double* red = sm;                      // kSeedThreads
@@ -523,30 +529,41 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
   int* prs = ibuf + kmax;
 
   const int tid = threadIdx.x;
-  const int nb = gridDim.x, b = blockIdx.x;
   const int mp = a.mp, np = a.np;
   const size_t mn = (size_t)mp * np;
   SeedCtl* ctl = a.ctl;
   const unsigned long long tmo = a.timeout_ns;
+  // warps per CTA for the row-wise forward substitutions: one per CTA on a
+  // wide team (rows spread over many SMs' FP64 pipes), more on small teams
+  const int row_warps = kGrid ? max(1, min(kSeedThreads / 32, 128 / nb))
+                              : kSeedThreads / 32;
+  auto team_sync = [&]() -> bool {
+    if (kGrid) return grid_sync(ctl, nb, tmo);
+    __syncthreads();
+    return true;
+  };
 
   // ---- prologue: norms of D, G = D, random Omega ---------------------------
+  const int nv = a.nv;
   {
-    double ss = 0.0, mx = 0.0;
-    for (size_t e = (size_t)b * kSeedThreads + tid; e < mn;
-         e += (size_t)nb * kSeedThreads) {
-      const double d = __ldg(a.D + e);
-      ss = fma(d, d, ss);
-      mx = fmax(mx, fabs(d));
-      __stcg(a.S + e, 0.0);
-      __stcg(a.G + e, d);
-      const int j = (int)(e / mp), i = (int)(e - (size_t)j * mp);
-      __stcg(a.Gt + (size_t)i * np + j, d);
-    }
-    ss = block_reduce_sum(ss, red);
-    mx = block_reduce_max(mx, red);
-    if (tid == 0) {
-      __stcg(a.part + 4 * b, ss);
-      __stcg(a.part + 4 * b + 1, mx);
+    for (int v = b; v < nv; v += nb) {
+      double ss = 0.0, mx = 0.0;
+      for (size_t e = (size_t)v * kSeedThreads + tid; e < mn;
+           e += (size_t)nv * kSeedThreads) {
+        const double d = __ldg(a.D + e);
+        ss = fma(d, d, ss);
+        mx = fmax(mx, fabs(d));
+        __stcg(a.S + e, 0.0);
+        __stcg(a.G + e, d);
+        const int j = (int)(e / mp), i = (int)(e - (size_t)j * mp);
+        __stcg(a.Gt + (size_t)i * np + j, d);
+      }
+      ss = block_reduce_sum(ss, red);
+      mx = block_reduce_max(mx, red);
+      if (tid == 0) {
+        __stcg(a.part + 4 * v, ss);
+        __stcg(a.part + 4 * v + 1, mx);
+      }
     }
     for (size_t e = (size_t)b * kSeedThreads + tid; e < (size_t)mp * a.k0;
          e += (size_t)nb * kSeedThreads) {
@@ -554,11 +571,11 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
       __stcg(a.Om + (size_t)i * kmax + c, hash_normal(0x5EEDull + c, i));
     }
   }
-  if (!grid_sync(ctl, nb, tmo)) return;
+  if (!team_sync()) return;
   trace_mark(a, 1);
-  const double normF = sqrt(sum_partials(a.part, nb, 4, 0, red));
+  const double normF = sqrt(sum_partials(a.part, nv, 4, 0, red));
   double m2 = 0.0;
-  for (int q = tid; q < nb; q += kSeedThreads)
+  for (int q = tid; q < nv; q += kSeedThreads)
     m2 = fmax(m2, ldg_cg(a.part + 4 * q + 1));
   const double norminf = block_reduce_max(m2, red);
   if (!(normF > 0.0)) {
@@ -590,31 +607,36 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
   bool converged = false;
   double res = 1.0;
   int knext = k;
+  // the Ritz bases of this iteration: Pt / PsiT, or P / Psi after the FP64
+  // refinement below
+  const double* Ptc = a.Pt;
+  const double* PsiTc = a.PsiT;
 
   while (true) {
     // ---- T = G^T Omega ------------------------------------------------------
-    tall_gemm_t(a.G, mp, mp, np, a.Om, k, kmax, a.T, red, xs);
-    if (!grid_sync(ctl, nb, tmo)) return;
+    tall_gemm_t(a.G, mp, mp, np, a.Om, k, kmax, a.T, red, xs, b, nb);
+    if (!team_sync()) return;
     trace_mark(a, 2);
-    gram(a.T, np, k, kmax, a.Gam);
-    if (!grid_sync(ctl, nb, tmo)) return;
+    gram(a.T, np, k, kmax, a.Gam, b, nb);
+    if (!team_sync()) return;
     trace_mark(a, 3);
     cholqr_apply(a.T, np, k, kmax, a.Gam, a.Psi, J0, W0, dsc, dead, rowb,
-                 ctl->sub);
-    if (!grid_sync(ctl, nb, tmo)) return;
+                 b, nb, row_warps, kGrid ? ctl->sub : nullptr);
+    if (!team_sync()) return;
     trace_mark(a, 4);
     // ---- P = G Psi ------------------------------------------------------------
-    tall_gemm_t(a.Gt, np, np, mp, a.Psi, k, kmax, a.P, red, xs);
-    if (stage >= 2) gram(a.Psi, np, k, kmax, a.Gam2);  // E = Psi1^T Psi1 - I
-    if (!grid_sync(ctl, nb, tmo)) return;
+    tall_gemm_t(a.Gt, np, np, mp, a.Psi, k, kmax, a.P, red, xs, b, nb);
+    if (stage >= 2) gram(a.Psi, np, k, kmax, a.Gam2, b, nb);  // E = Psi1^T Psi1 - I
+    if (!team_sync()) return;
     trace_mark(a, 5);
-    gram(a.P, mp, k, kmax, a.Gam);
-    if (!grid_sync(ctl, nb, tmo)) return;
+    gram(a.P, mp, k, kmax, a.Gam, b, nb);
+    if (!team_sync()) return;
     trace_mark(a, 6);
     if (stage < 2) {
       // plain power step on D: Omega = orth(P)
-      cholqr_apply(a.P, mp, k, kmax, a.Gam, a.Om, J0, W0, dsc, dead, rowb);
-      if (!grid_sync(ctl, nb, tmo)) return;
+      cholqr_apply(a.P, mp, k, kmax, a.Gam, a.Om, J0, W0, dsc, dead, rowb, b, nb,
+                   row_warps, nullptr);
+      if (!team_sync()) return;
       trace_mark(a, 7);
       ++stage;
       continue;
@@ -668,7 +690,8 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
       const int max_sweeps = (stage == 2 || res < 1e-5) ? 30 : 1;
       float* Afin = block_jacobi32(C32, cs, W0, k,
                                    reinterpret_cast<unsigned char*>(prs + kmax),
-                                   max_sweeps, &ctl->jsweeps, ctl->jcyc);
+                                   max_sweeps, kGrid ? &ctl->jsweeps : nullptr,
+                                   kGrid ? ctl->jcyc : nullptr);
       (void)Afin;
       const long long tj1 = clock64();
       if (b == 0 && tid == 0) ctl->jcyc[1] += tj1 - tj0;
@@ -702,34 +725,53 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
     }
     trace_mark(a, 8);
     // ---- rotate: Pt = P V, PsiT = Psi V, partial column sums of Pt^2 --------
+    // Thread (c, part) owns column c of this CTA's rows i = b + (part + s *
+    // nparts) * nb; partial sums of Pt^2 are reduced over parts in a fixed
+    // order, so the result does not depend on timing.
     {
-      double csq = 0.0;  // thread c's partial of sum_i Pt[i][c]^2
-      for (int i = b; i < mp; i += nb) {
-        for (int q = tid; q < k; q += kSeedThreads)
-          rowb[q] = ldg_cg(a.P + (size_t)i * kmax + q);
+      const int nparts = kSeedThreads / k;
+      const int c = tid % k, part = tid / k;
+      for (int v = b; v < nv; v += nb) {
+        double csq = 0.0;
+        if (part < nparts) {
+          for (int i = v + part * nv; i < mp; i += nv * nparts) {
+            const double* pr = a.P + (size_t)i * kmax;
+            double s0 = 0.0, s1 = 0.0;
+            int q = 0;
+            for (; q + 1 < k; q += 2) {
+              s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
+              s1 = fma(ldg_cg(pr + q + 1), Vd[(q + 1) * k + c], s1);
+            }
+            if (q < k) s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
+            const double sv = s0 + s1;
+            __stcg(a.Pt + (size_t)i * kmax + c, sv);
+            csq = fma(sv, sv, csq);
+          }
+          red[part * k + c] = csq;
+        }
         __syncthreads();
-        for (int c = tid; c < k; c += kSeedThreads) {
-          double s = 0.0;
-          for (int q = 0; q < k; ++q) s = fma(rowb[q], Vd[q * k + c], s);
-          __stcg(a.Pt + (size_t)i * kmax + c, s);
-          csq = fma(s, s, csq);
+        if (tid < k) {
+          double s2 = 0.0;
+          for (int q = 0; q < nparts; ++q) s2 += red[q * k + tid];
+          __stcg(a.colsq + (size_t)v * kmax + tid, s2);
         }
         __syncthreads();
       }
-      if (tid < k) __stcg(a.colsq + (size_t)b * kmax + tid, csq);
-      for (int j = b; j < np; j += nb) {
-        for (int q = tid; q < k; q += kSeedThreads)
-          rowb[q] = ldg_cg(a.Psi + (size_t)j * kmax + q);
-        __syncthreads();
-        for (int c = tid; c < k; c += kSeedThreads) {
-          double s = 0.0;
-          for (int q = 0; q < k; ++q) s = fma(rowb[q], Vd[q * k + c], s);
-          __stcg(a.PsiT + (size_t)j * kmax + c, s);
+      if (part < nparts) {
+        for (int j = b + part * nb; j < np; j += nb * nparts) {
+          const double* pr = a.Psi + (size_t)j * kmax;
+          double s0 = 0.0, s1 = 0.0;
+          int q = 0;
+          for (; q + 1 < k; q += 2) {
+            s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
+            s1 = fma(ldg_cg(pr + q + 1), Vd[(q + 1) * k + c], s1);
+          }
+          if (q < k) s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
+          __stcg(a.PsiT + (size_t)j * kmax + c, s0 + s1);
         }
-        __syncthreads();
       }
     }
-    if (!grid_sync(ctl, nb, tmo)) return;
+    if (!team_sync()) return;
     trace_mark(a, 9);
     // ---- FP64 Ritz values s_c = ||Pt e_c|| (fixed-order sum over blocks) ---
     {
@@ -738,13 +780,13 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
       if (part < nparts) {
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         int q = part;
-        for (; q + 3 * nparts < nb; q += 4 * nparts) {
+        for (; q + 3 * nparts < nv; q += 4 * nparts) {
           s0 += ldg_cg(a.colsq + (size_t)q * kmax + c);
           s1 += ldg_cg(a.colsq + (size_t)(q + nparts) * kmax + c);
           s2 += ldg_cg(a.colsq + (size_t)(q + 2 * nparts) * kmax + c);
           s3 += ldg_cg(a.colsq + (size_t)(q + 3 * nparts) * kmax + c);
         }
-        for (; q < nb; q += nparts) s0 += ldg_cg(a.colsq + (size_t)q * kmax + c);
+        for (; q < nv; q += nparts) s0 += ldg_cg(a.colsq + (size_t)q * kmax + c);
         red[part * k + c] = (s0 + s1) + (s2 + s3);
       }
       __syncthreads();
@@ -754,6 +796,65 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
         lam[tid] = sqrt(s2);
       }
       __syncthreads();
+    }
+    Ptc = a.Pt;
+    PsiTc = a.PsiT;
+    if (stage == 3 && res < 1e-5) {
+      // ---- FP64 refinement of the Ritz basis (near convergence) -----------
+      // The FP32 Jacobi leaves B = Pt^T Pt with off-diagonal entries of
+      // ~1e-7 of its diagonal, an error floor at the ALM's own tolerance.
+      // First-order perturbation theory removes it: the eigenvectors of
+      // B = D + F are I + Theta to O(F^2), Theta_pq = F_pq / (d_q - d_p),
+      // so Pt (I + Theta) and PsiT (I + Theta) have orthogonal columns to
+      // ~1e-14.  Theta is tiny, so FP32 arithmetic is exact enough for it;
+      // pairs too close for the first-order formula are left alone (their
+      // shrink factors are nearly equal, so mixing them changes little).
+      gram(a.Pt, mp, k, kmax, a.Gam2, b, nb);
+      if (!team_sync()) return;
+      trace_mark(a, 13);
+      for (int idx = tid; idx < k * k; idx += kSeedThreads) {
+        const int p = idx / k, q = idx - p * k;
+        double x = (p == q) ? 1.0 : 0.0;
+        if (p != q) {
+          const double gap = ldg_cg(a.Gam2 + q * kmax + q) -
+                             ldg_cg(a.Gam2 + p * kmax + p);
+          const float f = (float)ldg_cg(a.Gam2 + p * kmax + q);
+          const float g = (float)gap;
+          if (fabsf(f) < 0.01f * fabsf(g)) x = (double)__fdividef(f, g);
+        }
+        Vd[idx] = x;  // (I + Theta)[p][q]
+      }
+      __syncthreads();
+      const int nparts = kSeedThreads / k;
+      const int c = tid % k, part = tid / k;
+      if (part < nparts) {
+        for (int i = b + part * nb; i < mp; i += nb * nparts) {
+          const double* pr = a.Pt + (size_t)i * kmax;
+          double s0 = 0.0, s1 = 0.0;
+          int q = 0;
+          for (; q + 1 < k; q += 2) {
+            s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
+            s1 = fma(ldg_cg(pr + q + 1), Vd[(q + 1) * k + c], s1);
+          }
+          if (q < k) s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
+          __stcg(a.P + (size_t)i * kmax + c, s0 + s1);
+        }
+        for (int j = b + part * nb; j < np; j += nb * nparts) {
+          const double* pr = a.PsiT + (size_t)j * kmax;
+          double s0 = 0.0, s1 = 0.0;
+          int q = 0;
+          for (; q + 1 < k; q += 2) {
+            s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
+            s1 = fma(ldg_cg(pr + q + 1), Vd[(q + 1) * k + c], s1);
+          }
+          if (q < k) s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
+          __stcg(a.Psi + (size_t)j * kmax + c, s0 + s1);
+        }
+      }
+      if (!team_sync()) return;
+      trace_mark(a, 14);
+      Ptc = a.P;  // P and Psi are free until the next iteration's products
+      PsiTc = a.Psi;
     }
     double smax = 0.0;
     for (int c = 0; c < k; ++c) smax = fmax(smax, lam[c]);
@@ -776,14 +877,17 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
       knext = min(kmax, (k + max(6, k / 4) + 1) / 2 * 2);
     // Omega_next = Pt / s (rows distributed); fresh directions for growth
     // and for vanished Ritz vectors.
-    for (int i = b; i < mp; i += nb) {
-      for (int c = tid; c < knext; c += kSeedThreads) {
-        double v;
-        if (c < k && lam[c] > 1e-12 * smax)
-          v = ldg_cg(a.Pt + (size_t)i * kmax + c) / lam[c];
-        else
-          v = hash_normal(0xA11CEull + 977ull * it + c, i);
-        __stcg(a.Om + (size_t)i * kmax + c, v);
+    {
+      const int nparts = kSeedThreads / knext;
+      const int c = tid % knext, part = tid / knext;
+      if (part < nparts) {
+        const bool keep = c < k && lam[c] > 1e-12 * smax;
+        const double inv = keep ? 1.0 / lam[c] : 0.0;
+        for (int i = b + part * nb; i < mp; i += nb * nparts) {
+          const double v = keep ? ldg_cg(Ptc + (size_t)i * kmax + c) * inv
+                                : hash_normal(0xA11CEull + 977ull * it + c, i);
+          __stcg(a.Om + (size_t)i * kmax + c, v);
+        }
       }
     }
 
@@ -801,7 +905,7 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
         __stcg(a.Gt + (size_t)i * np + j, g);
       }
       stage = 3;
-      if (!grid_sync(ctl, nb, tmo)) return;
+      if (!team_sync()) return;
       trace_mark(a, 10);
       continue;
     }
@@ -810,42 +914,44 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
     const double mu_next = fmin(a.rho * mu, mu_max);
     const double inv_mu = 1.0 / mu, inv_mu_next = 1.0 / mu_next;
     const double lam_mu = a.lam * inv_mu;
-    double zz = 0.0;
-    for (int j = b; j < np; j += nb) {
-      for (int c = tid; c < k; c += kSeedThreads)
-        xi[c] = dsc[c] * ldg_cg(a.PsiT + (size_t)j * kmax + c);
-      __syncthreads();
-      for (int i = tid; i < mp; i += kSeedThreads) {
-        const double* pr = a.Pt + (size_t)i * kmax;
-        double l0 = 0.0, l1 = 0.0;
-        int c = 0;
-        for (; c + 1 < k; c += 2) {
-          l0 = fma(ldg_cg(pr + c), xi[c], l0);
-          l1 = fma(ldg_cg(pr + c + 1), xi[c + 1], l1);
+    for (int v = b; v < nv; v += nb) {
+      double zz = 0.0;
+      for (int j = v; j < np; j += nv) {
+        for (int c = tid; c < k; c += kSeedThreads)
+          xi[c] = dsc[c] * ldg_cg(PsiTc + (size_t)j * kmax + c);
+        __syncthreads();
+        for (int i = tid; i < mp; i += kSeedThreads) {
+          const double* pr = Ptc + (size_t)i * kmax;
+          double l0 = 0.0, l1 = 0.0;
+          int c = 0;
+          for (; c + 1 < k; c += 2) {
+            l0 = fma(ldg_cg(pr + c), xi[c], l0);
+            l1 = fma(ldg_cg(pr + c + 1), xi[c + 1], l1);
+          }
+          if (c < k) l0 = fma(ldg_cg(pr + c), xi[c], l0);
+          const double l = l0 + l1;
+          const size_t e = (size_t)j * mp + i;
+          const double d = __ldg(a.D + e);
+          const double y = ldg_cg(a.Y + e);
+          const double s = shrink(d - l + y * inv_mu, lam_mu);
+          const double z = d - l - s;
+          const double yn = fma(mu, z, y);
+          zz = fma(z, z, zz);
+          __stcg(a.S + e, s);
+          __stcg(a.Y + e, yn);
+          const double g = d - s + yn * inv_mu_next;
+          __stcg(a.G + e, g);
+          __stcg(a.Gt + (size_t)i * np + j, g);
         }
-        if (c < k) l0 = fma(ldg_cg(pr + c), xi[c], l0);
-        const double l = l0 + l1;
-        const size_t e = (size_t)j * mp + i;
-        const double d = __ldg(a.D + e);
-        const double y = ldg_cg(a.Y + e);
-        const double s = shrink(d - l + y * inv_mu, lam_mu);
-        const double z = d - l - s;
-        const double yn = fma(mu, z, y);
-        zz = fma(z, z, zz);
-        __stcg(a.S + e, s);
-        __stcg(a.Y + e, yn);
-        const double g = d - s + yn * inv_mu_next;
-        __stcg(a.G + e, g);
-        __stcg(a.Gt + (size_t)i * np + j, g);
+        __syncthreads();
       }
-      __syncthreads();
+      zz = block_reduce_sum(zz, red);
+      if (tid == 0) __stcg(a.part + 4 * v + 2, zz);
     }
-    zz = block_reduce_sum(zz, red);
-    if (tid == 0) __stcg(a.part + 4 * b + 2, zz);
     ++it;
-    if (!grid_sync(ctl, nb, tmo)) return;
+    if (!team_sync()) return;
     trace_mark(a, 11);
-    res = sqrt(sum_partials(a.part, nb, 4, 2, red)) / normF;
+    res = sqrt(sum_partials(a.part, nv, 4, 2, red)) / normF;
     converged = res <= a.tol;
     if (converged || it >= a.max_iter) break;
     mu = mu_next;
@@ -883,13 +989,13 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
   for (int i = b; i < mp; i += nb)
     for (int c = tid; c < kmax; c += kSeedThreads)
       a.U[i + (size_t)c * mp] =
-          (c < rank) ? ldg_cg(a.Pt + (size_t)i * kmax + order[c]) /
+          (c < rank) ? ldg_cg(Ptc + (size_t)i * kmax + order[c]) /
                            lam[order[c]]
                      : 0.0;
   for (int j = b; j < np; j += nb)
     for (int c = tid; c < kmax; c += kSeedThreads)
       a.V[j + (size_t)c * np] =
-          (c < rank) ? ldg_cg(a.PsiT + (size_t)j * kmax + order[c]) : 0.0;
+          (c < rank) ? ldg_cg(PsiTc + (size_t)j * kmax + order[c]) : 0.0;
   if (b == 0) {
     for (int c = tid; c < kmax; c += kSeedThreads)
       a.Sigma[c] = (c < rank) ? lam[order[c]] - tau : 0.0;
@@ -900,6 +1006,8 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
       ctl->converged = converged ? 1 : 0;
       ctl->residual = res;
       ctl->k_final = k;
+    }
+    if (tid == 0 && a.trace) {
       // closing records: Jacobi cycle split (phases 95..98) and total
       // Jacobi sweeps (phase 99)
       for (int q = 0; q < 5; ++q) {
@@ -923,6 +1031,37 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
   }
 }
 
+__global__ void __launch_bounds__(kSeedThreads, 2)
+    seed_alm_kernel(const SeedArgs a) {
+  seed_alm_body<true>(a, blockIdx.x, gridDim.x);
+}
+
+// Batched form: CTA x belongs to the team of seed team[x].x, at position
+// team[x].y of team[x].z CTAs.  A team of one CTA separates its phases with
+// __syncthreads; a larger team uses the grid barrier on its own seed's
+// control block (the launch is cooperative, so every team is co-resident).
+__global__ void __launch_bounds__(kSeedThreads, 2)
+    seed_alm_team_kernel(const SeedArgs* __restrict__ args,
+                         const int4* __restrict__ team) {
+  const int4 t = team[blockIdx.x];
+  const SeedArgs a = args[t.x];
+  if (t.z == 1)
+    seed_alm_body<false>(a, 0, 1);
+  else
+    seed_alm_body<true>(a, t.y, t.z);
+}
+
+// Control blocks start at zero (barrier counters included) before any team
+// member runs.
+__global__ void seed_ctl_zero_kernel(const SeedArgs* __restrict__ args,
+                                     int count) {
+  for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    int* c = reinterpret_cast<int*>(args[i].ctl);
+    for (int w = threadIdx.x; w < (int)(sizeof(SeedCtl) / 4); w += blockDim.x)
+      c[w] = 0;
+  }
+}
+
 size_t seed_smem_bytes(int kmax) {
   return sizeof(double) * ((size_t)kmax * kmax + kSeedThreads + 256 +
                            4 * kmax) +
@@ -933,15 +1072,13 @@ size_t seed_smem_bytes(int kmax) {
 }  // namespace
 
 // Enqueue the seed solve; results stay on the device (ctl, U, Sigma, V).
-pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
-                          double tol, double rho, double mu_scale,
-                          double mu_max_ratio, int max_iter, int k0, int kmax,
-                          double rank_cut, int r_cap, void* d_work,
-                          double* dU, double* dSigma, double* dV,
-                          cudaStream_t st, int** d_rank_out) {
-  const SeedLayout L = seed_layout(mp, np, kmax);
-  char* w = static_cast<char*>(d_work);
-  SeedArgs a;
+namespace {
+void fill_seed_args(SeedArgs& a, const SeedLayout& L, char* w,
+                    const double* dD, int mp, int np, double lam, double tol,
+                    double rho, double mu_scale, double mu_max_ratio,
+                    int max_iter, int k0, int kmax, double rank_cut,
+                    int r_cap, double* dU, double* dSigma, double* dV,
+                    bool trace) {
   a.D = dD;
   a.mp = mp;
   a.np = np;
@@ -956,6 +1093,7 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
   a.max_iter = max_iter;
   a.r_cap = r_cap;
   a.timeout_ns = 2000000000ull;  // 2 s per barrier wait
+  a.nv = kSeedTeamMax;
   a.ctl = reinterpret_cast<SeedCtl*>(w + L.ctl);
   a.part = reinterpret_cast<double*>(w + L.part);
   a.colsq = reinterpret_cast<double*>(w + L.colsq);
@@ -971,10 +1109,131 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
   a.PsiT = reinterpret_cast<double*>(w + L.PsiT);
   a.Gam = reinterpret_cast<double*>(w + L.Gam);
   a.Gam2 = reinterpret_cast<double*>(w + L.Gam2);
-  a.trace = reinterpret_cast<unsigned long long*>(w + L.trace);
+  a.trace =
+      trace ? reinterpret_cast<unsigned long long*>(w + L.trace) : nullptr;
   a.U = dU;
   a.Sigma = dSigma;
   a.V = dV;
+}
+}  // namespace
+
+static_assert(sizeof(SeedArgs) % 16 == 0, "SeedArgs stride");
+size_t seed_args_bytes() { return sizeof(SeedArgs); }
+
+size_t seed_batched_args_bytes(int count) {
+  return seed_args_bytes() * (size_t)count +
+         sizeof(int4) * ((size_t)count + kMaxCoopBlocks);
+}
+
+SeedCtl* seed_ctl_ptr_cta(void* d_work, int mp, int np, int kmax) {
+  const SeedLayout L = seed_layout(mp, np, kmax, kSeedTeamMax);
+  return reinterpret_cast<SeedCtl*>(static_cast<char*>(d_work) + L.ctl);
+}
+
+int* seed_rank_ptr_cta(void* d_work, int mp, int np, int kmax) {
+  const SeedLayout L = seed_layout(mp, np, kmax, kSeedTeamMax);
+  return &reinterpret_cast<SeedCtl*>(static_cast<char*>(d_work) + L.ctl)->rank;
+}
+
+pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
+                                  void* h_args, void* d_args,
+                                  cudaStream_t st) {
+  if (count <= 0) return PCP_OK;
+  char* hb = static_cast<char*>(h_args);
+  int kmax_all = 2;
+  for (int i = 0; i < count; ++i) {
+    const SeedTask& t = tasks[i];
+    const SeedLayout L = seed_layout(t.mp, t.np, t.kmax, kSeedTeamMax);
+    char* w = static_cast<char*>(t.work);
+    SeedArgs a;
+    fill_seed_args(a, L, w, t.D, t.mp, t.np, t.lam, t.tol, t.rho, t.mu_scale,
+                   t.mu_max_ratio, t.max_iter, t.k0, t.kmax, t.rank_cut,
+                   t.r_cap, t.U, t.Sigma, t.V, false);
+    std::memcpy(hb + (size_t)i * seed_args_bytes(), &a, sizeof(a));
+    kmax_all = std::max(kmax_all, t.kmax);
+  }
+  const size_t smem = seed_smem_bytes(kmax_all);
+  PCP_CUDA(cudaFuncSetAttribute(seed_alm_team_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  PCP_CUDA(cudaGetDevice(&dev));
+  PCP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  PCP_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  PCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, seed_alm_team_kernel, kSeedThreads, smem));
+  const int slots = std::min(per_sm * sms, kMaxCoopBlocks);
+  // Team sizes: FP64 work of one ALM iteration ~ m' n' k (plus a fixed
+  // latency share); spare CTAs go one by one to the seed with the most work
+  // per CTA, up to kSeedTeamMax and a quarter of its shorter side.
+  std::vector<int> nb(count, 1);
+  const bool teams = coop && slots >= count && count > 0;
+  if (teams) {
+    std::vector<double> w(count);
+    std::vector<int> cap(count);
+    using Item = std::pair<double, int>;
+    std::priority_queue<Item> pq;
+    for (int i = 0; i < count; ++i) {
+      w[i] = (double)tasks[i].mp * tasks[i].np * tasks[i].k0 + 2.0e4;
+      cap[i] = std::max(1, std::min(kSeedTeamMax,
+                                    std::min(tasks[i].mp, tasks[i].np) / 4));
+      pq.push({w[i], i});
+    }
+    int spare = slots - count;
+    while (spare > 0 && !pq.empty()) {
+      const int i = pq.top().second;
+      pq.pop();
+      if (nb[i] >= cap[i]) continue;
+      ++nb[i];
+      --spare;
+      pq.push({w[i] / nb[i], i});
+    }
+  }
+  // block table after the argument blocks; without teams (more seeds than
+  // co-resident CTAs) one CTA per seed, largest first
+  int4* tab = reinterpret_cast<int4*>(hb + seed_args_bytes() * (size_t)count);
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  if (!teams)
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return (double)tasks[x].mp * tasks[x].np * tasks[x].k0 >
+             (double)tasks[y].mp * tasks[y].np * tasks[y].k0;
+    });
+  int nblocks = 0;
+  for (int i : order)
+    for (int b = 0; b < nb[i]; ++b) tab[nblocks++] = make_int4(i, b, nb[i], 0);
+  PCP_CUDA(cudaMemcpyAsync(d_args, h_args,
+                           seed_args_bytes() * (size_t)count +
+                               sizeof(int4) * (size_t)nblocks,
+                           cudaMemcpyHostToDevice, st));
+  const SeedArgs* d_a = static_cast<const SeedArgs*>(d_args);
+  const int4* d_tab = reinterpret_cast<const int4*>(
+      static_cast<char*>(d_args) + seed_args_bytes() * (size_t)count);
+  seed_ctl_zero_kernel<<<std::min(count, 1024), 64, 0, st>>>(d_a, count);
+  PCP_CUDA(cudaGetLastError());
+  if (teams) {
+    void* kargs[] = {(void*)&d_a, (void*)&d_tab};
+    PCP_CUDA(cudaLaunchCooperativeKernel((void*)seed_alm_team_kernel,
+                                         dim3(nblocks), dim3(kSeedThreads),
+                                         kargs, smem, st));
+  } else {
+    seed_alm_team_kernel<<<nblocks, kSeedThreads, smem, st>>>(d_a, d_tab);
+    PCP_CUDA(cudaGetLastError());
+  }
+  return PCP_OK;
+}
+
+pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
+                          double tol, double rho, double mu_scale,
+                          double mu_max_ratio, int max_iter, int k0, int kmax,
+                          double rank_cut, int r_cap, void* d_work,
+                          double* dU, double* dSigma, double* dV,
+                          cudaStream_t st, int** d_rank_out) {
+  const SeedLayout L = seed_layout(mp, np, kmax, kMaxCoopBlocks);
+  char* w = static_cast<char*>(d_work);
+  SeedArgs a;
+  fill_seed_args(a, L, w, dD, mp, np, lam, tol, rho, mu_scale, mu_max_ratio,
+                 max_iter, k0, kmax, rank_cut, r_cap, dU, dSigma, dV, true);
   if (d_rank_out) *d_rank_out = &a.ctl->rank;
 
   const size_t smem = seed_smem_bytes(kmax);
@@ -999,6 +1258,7 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
   // co-resident (a cooperative launch needs every CTA resident at once)
   const int grid = std::min(std::min(sms * per_sm, kMaxCoopBlocks),
                             std::max(mp, np));
+  a.nv = grid;
   PCP_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(SeedCtl), st));
   void* args[] = {&a};
   PCP_CUDA(cudaLaunchCooperativeKernel((const void*)seed_alm_kernel, grid,
@@ -1010,7 +1270,7 @@ pcp_status seed_read_ctl(void* d_work, int mp, int np, int kmax,
                          cudaStream_t st, int* rank, int* iters,
                          double* residual, int* converged, int* error,
                          int* rank_raw) {
-  const SeedLayout L = seed_layout(mp, np, kmax);
+  const SeedLayout L = seed_layout(mp, np, kmax, kMaxCoopBlocks);
   SeedCtl h;
   PCP_CUDA(cudaMemcpyAsync(&h, static_cast<char*>(d_work) + L.ctl,
                            sizeof(SeedCtl), cudaMemcpyDeviceToHost, st));
@@ -1082,7 +1342,7 @@ extern "C" int32_t pcp_seed_trace(const void* d_work, int32_t mp, int32_t np,
                                   int32_t kmax, uint64_t* h_out, int32_t cap,
                                   void* stream) {
   if (!d_work || mp < 1 || np < 1 || kmax < 2 || cap < 0) return -1;
-  const pcp::SeedLayout L = pcp::seed_layout(mp, np, kmax);
+  const pcp::SeedLayout L = pcp::seed_layout(mp, np, kmax, pcp::kMaxCoopBlocks);
   const char* w = static_cast<const char*>(d_work);
   pcp::SeedCtl h;
   cudaStream_t st = (cudaStream_t)stream;

@@ -60,8 +60,18 @@ class Problem:
         return np.asfortranarray(self.M.astype(np.float32))
 
 
+def _flat(seed):
+    if isinstance(seed, (tuple, list)):
+        out = []
+        for s in seed:
+            out.extend(_flat(s))
+        return out
+    return [int(seed)]
+
+
 def _rng(seed) -> np.random.Generator:
-    return np.random.Generator(np.random.PCG64(seed))
+    """PCG64 generator; ``seed`` is an int or a (nested) tuple of ints."""
+    return np.random.Generator(np.random.PCG64(_flat(seed)))
 
 
 def _sparse_support(rng, m, n, density, exact=None):
@@ -95,15 +105,16 @@ def lowrank_plus_sparse(m, n, r, density, lo, hi, seed=0, factor_std=1.0,
     rng = _rng(seed)
     X = rng.standard_normal((m, r)) * factor_std
     Y = rng.standard_normal((n, r)) * factor_std
-    L0 = np.asfortranarray((X @ Y.T).astype(dtype))
+    L0 = np.asfortranarray(X @ Y.T)
     mask = _sparse_support(rng, m, n, density)
     vals = rng.uniform(lo, hi, size=int(mask.sum()))
-    S0 = np.zeros((m, n), dtype=dtype, order="F")
+    S0 = np.zeros((m, n), order="F")
     S0[mask] = vals  # boolean assignment fills in the mask's (C-)order
-    M = np.asfortranarray(L0 + S0)
+    # sum in FP64, then round once to the storage type
+    M = np.asfortranarray((L0 + S0).astype(dtype, copy=False))
     if not keep_truth:
         return M, None, None
-    return M, L0, S0
+    return M, L0.astype(dtype, copy=False), S0.astype(dtype, copy=False)
 
 
 def seed_indices(m, n, mp, np_, seed=0):
@@ -151,14 +162,18 @@ def make_config(name, seed=0, keep_truth=True, dtype=np.float64, **override):
 
 def uneven_instances(count=256, seed=0, m_range=(300, 4000),
                      n_range=(200, 3000), r_max=30, density_range=(0.02, 0.15),
-                     lo=-50.0, hi=50.0, s=10):
+                     lo=-50.0, hi=50.0, s=10, keep_truth=True,
+                     dtype=np.float64, indices=None):
     """Many instances of different sizes (batched workload).
 
     m ~ U[m_range], n ~ U[n_range], r ~ U[3, min(r_max, floor(min(m, n)/20))]
     (so that the 10r x 10r seed stays within half of each dimension, the size
     limit of the target-rank test in Section 3.5), density ~ U[density_range].
+    ``indices`` builds only those instances (the sizes of all are drawn in
+    order, so instance i is the same whichever subset is built).
     """
     rng = _rng((seed, 0xBA7C))
+    want = None if indices is None else set(int(i) for i in indices)
     out = []
     for i in range(count):
         m = int(rng.integers(m_range[0], m_range[1] + 1))
@@ -166,8 +181,11 @@ def uneven_instances(count=256, seed=0, m_range=(300, 4000),
         rmax = max(3, min(r_max, min(m, n) // 20))
         r = int(rng.integers(3, rmax + 1))
         dens = float(rng.uniform(*density_range))
+        if want is not None and i not in want:
+            continue
         M, L0, S0 = lowrank_plus_sparse(m, n, r, dens, lo, hi,
-                                        seed=(seed, i, 1))
+                                        seed=(seed, i, 1),
+                                        keep_truth=keep_truth, dtype=dtype)
         rows, cols = seed_indices(m, n, s * r, s * r, seed=(seed, i, 2))
         out.append(Problem(M=M, L0=L0, S0=S0, r=r, rows=rows, cols=cols,
                            name=f"uneven{i}"))
@@ -180,8 +198,9 @@ def _blur1d(a, sigma, axis):
     t = np.arange(-rad, rad + 1, dtype=np.float64)
     k = np.exp(-0.5 * (t / sigma) ** 2)
     k /= k.sum()
-    return np.apply_along_axis(lambda v: np.convolve(v, k, mode="same"),
-                               axis, a)
+    n = a.shape[axis]
+    return np.apply_along_axis(
+        lambda v: np.convolve(v, k, mode="full")[rad:rad + n], axis, a)
 
 
 def video_like(n_frames, height=240, width=320, r=None, seed=0,
@@ -210,13 +229,18 @@ def video_like(n_frames, height=240, width=320, r=None, seed=0,
         B[:, k] = 1.0 + 0.1 * curve / max(np.abs(curve).max(), 1e-12)
     L0 = np.asfortranarray(A @ B.T)
     S0 = np.zeros((m, n_frames), order="F")
+    # rectangle sides in [8, side/3) px (narrower bounds on tiny frames)
+    hlo = max(2, min(8, height // 6))
+    hhi = max(hlo + 1, height // 3)
+    wlo = max(2, min(8, width // 6))
+    whi = max(wlo + 1, width // 3)
     for j in range(n_frames):
         frame = np.zeros((height, width))
         mask = np.zeros((height, width), dtype=bool)
         target = rng.uniform(*cover_range)
         while mask.mean() < target:
-            h = int(rng.integers(8, height // 3))
-            w = int(rng.integers(8, width // 3))
+            h = int(rng.integers(hlo, hhi))
+            w = int(rng.integers(wlo, whi))
             y0 = int(rng.integers(0, height - h))
             x0 = int(rng.integers(0, width - w))
             frame[y0:y0 + h, x0:x0 + w] = rng.uniform(fg_lo, fg_hi)

@@ -84,3 +84,18 @@ def test_stage_entry_points_validate_sizes(lib):
     assert st == _abi.PCP_ERR_ARG
     st = lib.pcp_spass(None, 1, None, 1, None, 1, 100, None, 1, 1, 1, None)
     assert st == _abi.PCP_ERR_ARG
+
+
+def test_batch_and_serve_validate_without_gpu(lib):
+    from paper_1108_5359_gb300 import _abi
+    assert lib.pcp_l1filter_batch(0, None, None, None) == _abi.PCP_OK
+    assert lib.pcp_l1filter_batch(-1, None, None, None) == _abi.PCP_ERR_ARG
+    assert lib.pcp_l1filter_batch(2, None, None, None) == _abi.PCP_ERR_ARG
+    h = C.c_void_p()
+    assert lib.pcp_serve_create(0, 4, 1, C.byref(h)) == _abi.PCP_ERR_ARG
+    assert lib.pcp_serve_create(1 << 30, 0, 1, C.byref(h)) == _abi.PCP_ERR_ARG
+    assert lib.pcp_serve_create(1 << 30, 4, 17, C.byref(h)) == _abi.PCP_ERR_ARG
+    assert not h.value
+    assert lib.pcp_serve_destroy(None) == _abi.PCP_OK
+    assert lib.pcp_serve_poll(None, 1, None) == _abi.PCP_ERR_ARG
+    assert lib.pcp_serve_stop(None) == _abi.PCP_ERR_ARG

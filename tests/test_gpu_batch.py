@@ -1,0 +1,159 @@
+"""GPU parity of the batched form (pcp_l1filter_batch).
+
+Many independent instances of different sizes in one call (Section 3.2: the
+column and row problems of every instance are independent).  Each instance
+must (a) match the FP64 oracle, and the single-instance solve, within
+relative Frobenius error 1e-5 on L and S, with the same rank; (b) give
+bit-identical outputs alone (a batch of one) and inside the mix; (c) keep
+its own status when another instance of the batch fails.
+"""
+import numpy as np
+import pytest
+
+from oracle import l1filter
+from paper_1108_5359_gb300 import synth
+from tests.gpuhelp import build_and_load, relerr, to_dev_cm, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _instances():
+    return synth.uneven_instances(count=6, seed=11, m_range=(300, 1400),
+                                  n_range=(250, 1200), r_max=12)
+
+
+def _buffers(P, ld=None, want_S=True):
+    import paper_1108_5359_gb300 as pk
+    dM = to_dev_cm(P.M.astype(np.float32), ld=ld)
+    Lu = pk.colmajor(P.m, P.r, fill=0.0)
+    Lv = pk.colmajor(P.n, P.r, fill=0.0)
+    S = pk.colmajor(P.m, P.n, fill=0.0) if want_S else None
+    return dM, Lu, Lv, S
+
+
+def _run_batch(Ps, lds=None, want_S=None):
+    import torch
+    import paper_1108_5359_gb300 as pk
+    build_and_load()
+    lds = lds or [None] * len(Ps)
+    want_S = want_S or [True] * len(Ps)
+    bufs, probs = [], []
+    for P, ld, ws in zip(Ps, lds, want_S):
+        dM, Lu, Lv, S = _buffers(P, ld, ws)
+        bufs.append((dM, Lu, Lv, S))
+        probs.append(pk.problem(pk.pcp_params_default(P.m, P.n, P.r), dM, Lu,
+                                Lv, S, P.rows, P.cols))
+    st, infos = pk.pcp_l1filter_batch(probs, raise_on_error=False)
+    torch.cuda.synchronize()
+    out = []
+    for (dM, Lu, Lv, S), inf in zip(bufs, infos):
+        out.append(dict(info=inf.as_dict(), Lu=Lu.cpu().numpy(),
+                        Lv=Lv.cpu().numpy(),
+                        S=None if S is None else S.cpu().numpy()))
+    return st, out
+
+
+def _run_single(P):
+    import torch
+    import paper_1108_5359_gb300 as pk
+    dM, Lu, Lv, S = _buffers(P)
+    plan = pk.Plan(pk.pcp_params_default(P.m, P.n, P.r), P.rows, P.cols)
+    st, info, _, _ = pk.pcp_l1filter_solve(plan, dM, Lu, Lv, S,
+                                           raise_on_error=False)
+    torch.cuda.synchronize()
+    plan.close()
+    return st, to_host(Lu) @ to_host(Lv).T, to_host(S)
+
+
+def _L(o):
+    return o["Lu"].astype(np.float64) @ o["Lv"].astype(np.float64).T
+
+
+def test_batch_matches_oracle_and_single_solve():
+    Ps = _instances()
+    st, out = _run_batch(Ps)
+    for i, (P, o) in enumerate(zip(Ps, out)):
+        st1, L1, S1 = _run_single(P)
+        assert o["info"]["status"] == st1, (i, o["info"])
+        if st1 != 0:
+            continue
+        assert o["info"]["rank"] == P.r
+        assert o["info"]["problems"] == (P.m - 10 * P.r) + (P.n - 10 * P.r)
+        assert o["info"]["problems_unconverged"] == 0
+        assert relerr(_L(o), L1) < TOL, i
+        assert relerr(o["S"].astype(np.float64), S1) < TOL, i
+    # the oracle on the two smallest instances (it is slow)
+    small = sorted(range(len(Ps)), key=lambda i: Ps[i].m * Ps[i].n)[:2]
+    for i in small:
+        P, o = Ps[i], out[i]
+        M = P.M.astype(np.float32).astype(np.float64)
+        ref = l1filter.l1_filter_pcp(M, P.rows, P.cols, r=P.r)
+        if ref.rank != P.r or o["info"]["status"] != 0:
+            continue
+        assert relerr(_L(o), ref.L) < TOL, i
+        assert relerr(o["S"].astype(np.float64), ref.S) < TOL, i
+
+
+def test_alone_equals_in_mix_bitwise():
+    Ps = _instances()
+    _, mix = _run_batch(Ps)
+    for i in (0, 3, 5):
+        _, alone = _run_batch([Ps[i]])
+        a, b = alone[0], mix[i]
+        assert a["info"]["status"] == b["info"]["status"]
+        assert a["info"]["seed_iters"] == b["info"]["seed_iters"]
+        assert a["info"]["filter_iters_max"] == b["info"]["filter_iters_max"]
+        np.testing.assert_array_equal(a["Lu"], b["Lu"])
+        np.testing.assert_array_equal(a["Lv"], b["Lv"])
+        np.testing.assert_array_equal(a["S"], b["S"])
+
+
+def test_failing_instance_does_not_affect_others():
+    Ps = _instances()[:3]
+    bad = Ps[1]
+    Mbad = bad.M.copy()
+    Mbad[bad.rows[0], bad.cols[0]] = np.nan   # inside the seed block
+    Pbad = synth.Problem(M=Mbad, L0=bad.L0, S0=bad.S0, r=bad.r,
+                         rows=bad.rows, cols=bad.cols, name="nan")
+    st, out = _run_batch([Ps[0], Pbad, Ps[2]])
+    assert out[1]["info"]["status"] == -4      # PCP_ERR_NONFINITE
+    # the call returns the first non-OK status in instance order
+    assert st == next(o["info"]["status"] for o in out
+                      if o["info"]["status"] != 0)
+    _, clean = _run_batch([Ps[0], Ps[2]])
+    for o, c in zip((out[0], out[2]), clean):
+        assert o["info"]["status"] == c["info"]["status"]
+        np.testing.assert_array_equal(o["Lu"], c["Lu"])
+        np.testing.assert_array_equal(o["S"], c["S"])
+
+
+def test_ragged_leading_dims_and_factors_only():
+    P1 = synth.make_config("c1_500_r5", seed=5, m=437, n=389, r=4)
+    P2 = synth.make_config("c1_500_r5", seed=5, m=300, n=650, r=3)
+    st, out = _run_batch([P1, P2], lds=[441, None], want_S=[True, False])
+    assert st == 0
+    refs = []
+    for P, o in zip((P1, P2), out):
+        M = P.M.astype(np.float32).astype(np.float64)
+        ref = l1filter.l1_filter_pcp(M, P.rows, P.cols, r=P.r)
+        assert o["info"]["rank"] == ref.rank == P.r
+        assert relerr(_L(o), ref.L) < TOL
+        refs.append(ref)
+    assert relerr(out[0]["S"].astype(np.float64), refs[0].S) < TOL
+    assert out[1]["S"] is None
+
+
+def test_empty_batch_and_bad_instance_rejected():
+    import paper_1108_5359_gb300 as pk
+    from paper_1108_5359_gb300 import _abi
+    lib = build_and_load()
+    assert lib.pcp_l1filter_batch(0, None, None, None) == 0
+    P = synth.make_config("c1_500_r5", seed=3)
+    dM, Lu, Lv, S = _buffers(P)
+    p = pk.pcp_params_default(P.m, P.n, 40)      # r > 32
+    q = pk.problem(p, dM, Lu, Lv, S)
+    arr = (_abi.PCPProblem * 1)(q.c)
+    assert lib.pcp_l1filter_batch(1, arr, None, None) == _abi.PCP_ERR_ARG
+    assert b"instance 0" in lib.pcp_last_error()
