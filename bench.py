@@ -38,11 +38,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("PCP entries recovered/s (m*n/s) at rel err<=1e-5 vs plain FP32; "
           "p50/p99 latency")
+LARGE = "c3_20000_r50"
+LARGE_DESC = ("m=n=20000, r=50, L0=XY^T with X,Y iid N(0,1/r); S0 10% uniform "
+              "support, values U[-10,10]; seed 500x500; FP32 M (1.6 GB)")
 WORKLOAD = "c2_5000_r20"
 WORKLOAD_DESC = ("m=n=5000, r=20, L0=XY^T with X,Y iid N(0,1); S0 10% uniform "
                  "support, values U[-100,100]; seed 200x200 (10r x 10r); "
                  "lambda=1/sqrt(5000); FP32 M")
 FLUSH_BYTES = 256 << 20
+PRECISIONS = {"fp32": 0, "tf32": 2, "fp32simt": 5}
 
 
 def parse():
@@ -56,17 +60,26 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true",
                     help="500x500 rank-5 workload (profiling / smoke)")
-    ap.add_argument("--workload", choices=["single", "batch", "serve"],
+    ap.add_argument("--workload", choices=["single", "large", "batch",
+                                           "serve"],
                     default="single",
                     help="single: the 5000x5000 rank-20 solve (default); "
+                         "large: the 20000x20000 rank-50 solve; "
                          "batch: uneven instances through pcp_l1filter_batch "
                          "vs one pcp_l1filter_solve per instance; serve: "
                          "Poisson arrivals of video-like solves through "
                          "pcp_serve_* vs a one-at-a-time queue")
+    ap.add_argument("--size", type=int, default=0,
+                    help="large: m = n = SIZE instead of 20000 (profiling)")
     ap.add_argument("--count", type=int, default=256,
                     help="instances (batch) / requests (serve)")
     ap.add_argument("--rate", type=float, default=50.0,
                     help="serve: arrival rate, requests/s")
+    ap.add_argument("--precision", choices=["fp32", "tf32", "fp32simt"],
+                    default="fp32",
+                    help="Algorithm 1 arithmetic: fp32 (split-TF32 tensor "
+                         "cores, FP32-accurate), tf32 (one-pass TF32 then "
+                         "split-TF32 refinement), fp32simt (FP32 FMA)")
     ap.add_argument("--r-max", type=int, default=25,
                     help="batch: largest rank drawn (seed 10r <= 256)")
     return ap.parse_args()
@@ -150,14 +163,46 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
-def make_problem(seed, small=False):
+def make_problem(seed, small=False, large=False, size=0):
     from paper_1108_5359_gb300 import synth
     if small:
         P = synth.make_config("c1_500_r5", seed=3 + seed)
+    elif large:
+        kw = {"m": size, "n": size} if size else {}
+        P = synth.make_config(LARGE, seed=seed, keep_truth=False,
+                              dtype=np.float32, **kw)
     else:
         P = synth.make_config(WORKLOAD, seed=seed)
-    M32 = np.asfortranarray(P.M.astype(np.float32))
+    M32 = np.asfortranarray(P.M.astype(np.float32, copy=False))
     return P, M32
+
+
+def workload_name(args):
+    if args.small:
+        return "c1_500_r5", "m=n=500, r=5, 5% support U[-50,50], seed 50x50"
+    if args.workload == "large":
+        if args.size:
+            return (f"{LARGE}_at_{args.size}",
+                    LARGE_DESC.replace("m=n=20000", f"m=n={args.size}"))
+        return LARGE, LARGE_DESC
+    return WORKLOAD, WORKLOAD_DESC
+
+
+def sampled_parity(P, seed, Lu, Lv, S, k=256):
+    """Exact recovery on a sampled k x k block when L0 is not kept."""
+    from paper_1108_5359_gb300 import synth
+    cfg = synth.CONFIGS[LARGE]
+    X, Y = synth.lowrank_factors(P.m, P.n, P.r, seed=seed,
+                                 factor_std=cfg["factor_std"])
+    rng = np.random.default_rng(17)
+    ri = np.sort(rng.choice(P.m, k, replace=False))
+    ci = np.sort(rng.choice(P.n, k, replace=False))
+    L0 = X[ri] @ Y[ci].T
+    Lg = Lu.double().cpu().numpy()[ri] @ Lv.double().cpu().numpy()[ci].T
+    Mb = P.M[np.ix_(ri, ci)].astype(np.float64)
+    Sg = S.double().cpu().numpy()[np.ix_(ri, ci)]
+    return {"sample": f"{k}x{k} block", "relerr_L_vs_L0": relerr(Lg, L0),
+            "relerr_S_vs_S0": relerr(Sg, Mb - L0)}
 
 
 def relerr(a, b):
@@ -203,9 +248,10 @@ def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    P, M32 = make_problem(args.seed, args.small)
+    large = args.workload == "large"
+    P, M32 = make_problem(args.seed, args.small, large, args.size)
     mn = P.m * P.n
-    frac = 1.0 if args.small else 0.1
+    frac = 1.0 if args.small else (0.01 if large else 0.1)
     cores = os.cpu_count()
     for _ in range(args.warmup):
         oracle_solve(P, M32, frac)
@@ -225,8 +271,9 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * t_mean,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": ("c1_500_r5" if args.small else WORKLOAD),
-                   "desc": WORKLOAD_DESC, "parallelism": "host cores"},
+        "config": {"workload": workload_name(args)[0],
+                   "desc": workload_name(args)[1],
+                   "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0,
@@ -252,7 +299,9 @@ def run_ours(args):
     pkbuild.build()
     pk.load()
 
-    P, M32 = make_problem(args.seed + 1000 * rank, args.small)
+    large = args.workload == "large"
+    pseed = args.seed + 1000 * rank
+    P, M32 = make_problem(pseed, args.small, large, args.size)
     m, n, r = P.m, P.n, P.r
     mn = m * n
     dev = torch.device("cuda", local)
@@ -262,6 +311,7 @@ def run_ours(args):
     Lv = pk.colmajor(n, r, device=dev)
     S = pk.colmajor(m, n, device=dev)
     params = pk.pcp_params_default(m, n, r)
+    params.precision = PRECISIONS[args.precision]
     plan = pk.Plan(params, P.rows, P.cols)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -309,12 +359,16 @@ def run_ours(args):
     last_info = info.as_dict()
 
     # parity of the last solve: exact recovery of the generated L0, S0
-    Lh = Lu.double().cpu().numpy()
-    Vh = Lv.double().cpu().numpy()
-    Sh = S.double().cpu().numpy()
-    Lrec = Lh @ Vh.T
-    parity = {"relerr_L_vs_L0": relerr(Lrec, P.L0),
-              "relerr_S_vs_S0": relerr(Sh, P.S0), "status": int(st)}
+    if P.L0 is not None:
+        Lh = Lu.double().cpu().numpy()
+        Vh = Lv.double().cpu().numpy()
+        Sh = S.double().cpu().numpy()
+        Lrec = Lh @ Vh.T
+        parity = {"relerr_L_vs_L0": relerr(Lrec, P.L0),
+                  "relerr_S_vs_S0": relerr(Sh, P.S0), "status": int(st)}
+    else:
+        parity = sampled_parity(P, pseed, Lu, Lv, S)
+        parity["status"] = int(st)
 
     # e2e through the public API from pinned host buffers
     e2e = None
@@ -379,7 +433,9 @@ def run_ours(args):
     dom = max(stages, key=lambda k: stages[k]["ms"])
     d = stages[dom]
     roofline = {"kernel": {"spass": "spass_kernel",
-                           "filter": "adm_f32_kernel",
+                           "filter": ("adm_f32_kernel"
+                                      if args.precision == "fp32simt"
+                                      else "adm_tc_kernel"),
                            "seed": "seed_alm_kernel"}[dom],
                 "bound": d["bound"], "achieved": d["achieved"],
                 "peak": d["peak"], "unit": d["unit"], "frac": d["frac"],
@@ -389,11 +445,15 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t_or, ref = oracle_solve(P, M32, 1.0)
+        frac = 0.01 if large else 1.0
+        t_or, ref = oracle_solve(P, M32, frac)
         cpu = {"value": mn / t_or, "unit": "entries/s",
                "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "one full FP64 oracle solve of the same workload "
-                         "(numpy, BLAS threads = host cores)"}
+               "sample": ("one full FP64 oracle solve of the same workload "
+                          "(numpy, BLAS threads = host cores)" if frac >= 1
+                          else "full FP64 seed PCP + Algorithm 1 on 1% of "
+                          "the column and row problems + 1% of the S pass, "
+                          "non-seed time scaled by 100")}
         if ref is not None:
             parity["relerr_L_vs_oracle"] = relerr(Lrec, ref.L)
             parity["relerr_S_vs_oracle"] = relerr(Sh, ref.S)
@@ -404,10 +464,12 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "entries/s",
             "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup),
             "ms_per_step": t_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32 (split tf32)", "tf32": "tf32+f32",
+                      "fp32simt": "f32"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": ("c1_500_r5" if args.small else WORKLOAD),
-                       "desc": WORKLOAD_DESC, "global_batch": ws,
+            "config": {"workload": workload_name(args)[0],
+                       "desc": workload_name(args)[1], "global_batch": ws,
                        "parallelism": f"replicas{ws}",
                        "l2": "flushed between steps (256 MB memset outside "
                              "the timed span)",
@@ -715,7 +777,7 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
-    else:
+    else:  # single, large
         run_ours(args)
 
 

@@ -56,12 +56,19 @@ typedef enum pcp_status {
   PCP_ERR_UNSUPPORTED = -11   /* option not available on this device */
 } pcp_status;
 
+/* Arithmetic of Algorithm 1 (the seed PCP is FP64 in every mode). */
 typedef enum pcp_precision {
-  PCP_FP32 = 0,          /* Algorithm 1 in FP32 FMA (SIMT) */
-  PCP_BF16_REFINED = 1,  /* BF16 tensor-core products, FP32 accumulation,
-                            then FP32 refinement iterations */
-  PCP_TF32_REFINED = 2,  /* reserved */
-  PCP_FP64 = 3           /* reserved */
+  PCP_FP32 = 0,          /* FP32-accurate: split-TF32 tensor-core products
+                            (three passes, ~2^-21 relative) */
+  PCP_BF16_REFINED = 1,  /* not built: PCP_ERR_UNSUPPORTED */
+  PCP_TF32_REFINED = 2,  /* one-pass TF32 tensor-core products with FP32
+                            accumulation for the first lowp_iters
+                            iterations, then split-TF32 products (three
+                            passes, ~2^-21 relative, the FP32 refinement)
+                            until filter_tol */
+  PCP_FP64 = 3,          /* reserved: PCP_ERR_UNSUPPORTED */
+  PCP_FP32_TENSOR = 4,   /* same as PCP_FP32 */
+  PCP_FP32_SIMT = 5      /* FP32 FMA on the CUDA cores (p <= 256, r <= 32) */
 } pcp_precision;
 
 /* Parameters of one solve.  Fill with pcp_params_default() first. */
@@ -93,8 +100,9 @@ typedef struct pcp_params {
   int32_t seed_subspace;    /* initial subspace size of the seed's partial
                                SVD; <= 0 means r + max(6, r/4), rounded up to
                                even */
-  int32_t refine_iters;     /* PCP_BF16_REFINED: FP32 iterations after the
-                               BF16 phase, default 8 (0 = until filter_tol) */
+  int32_t lowp_iters;       /* PCP_TF32_REFINED: Algorithm 1 iterations with
+                               one-pass TF32 products before the FP32-
+                               accurate refinement, default 12 */
   uint64_t rng_seed;        /* seed sampling when seed_rows/cols are NULL */
   const int64_t* seed_rows; /* optional host array, m' distinct row indices */
   const int64_t* seed_cols; /* optional host array, n' distinct col indices */
@@ -152,7 +160,8 @@ const char* pcp_version(void);
  * size (seed buffers, index sets, per-problem status).  The plan copies
  * *params (and the optional seed index arrays) and owns its workspace until
  * pcp_plan_destroy().  One plan serves any number of sequential solves of
- * the same shape; concurrent solves need separate plans. */
+ * the same shape; concurrent solves need separate plans.  Limits: r <= 64,
+ * seeds up to 512 x 512 and smaller than M in both sides (PCP_ERR_ARG). */
 pcp_status pcp_l1filter_plan(const pcp_params* params, pcp_plan** out);
 
 /* Run Algorithm 2 on M.
@@ -193,8 +202,8 @@ void pcp_plan_destroy(pcp_plan* plan);
  * the stream reaches the end of the batch.  With infos (count entries) the
  * call synchronises and fills one pcp_info per instance, including its
  * status; the return value is then the first non-OK status.  Without infos
- * the call is asynchronous.  Limits: count <= 65535, r <= 32, seeds up to
- * 256 x 256; violations give PCP_ERR_ARG before any device work. */
+ * the call is asynchronous.  Limits: count <= 65535, r <= 64, seeds up to
+ * 512 x 512; violations give PCP_ERR_ARG before any device work. */
 pcp_status pcp_l1filter_batch(int32_t count, const pcp_problem* probs,
                               pcp_info* infos, void* stream);
 
@@ -277,7 +286,8 @@ size_t pcp_seed_workspace_bytes(int32_t mp, int32_t np, int32_t kmax);
  *   rank_cut * largest, capped at r_cap when r_cap > 0);
  *   *h_iters, *h_residual: ALM iterations and final relative residual.
  * lambda <= 0 means 1/sqrt(max(mp,np)).  k0 is the initial subspace size
- * (even, <= kmax).  d_work must hold pcp_seed_workspace_bytes() bytes.
+ * (even, <= kmax <= 64); 2 <= mp, np <= 512.  d_work must hold
+ * pcp_seed_workspace_bytes() bytes.
  * Returns PCP_ERR_SEED_NOCONV when max_iter is reached (outputs written),
  * PCP_ERR_TIMEOUT if a device barrier wait ran out. */
 pcp_status pcp_seed_pcp(const double* dD, int32_t mp, int32_t np,
@@ -341,9 +351,10 @@ int32_t pcp_plan_seed_trace(const pcp_plan* plan, uint64_t* h_out,
  * read from *d_rank when d_rank is non-NULL (device int32, <= r; columns
  * past it are written as zero).  d_iters (N int32, optional) receives each
  * problem's iteration count, negated when it hit max_iter.
- * precision: PCP_FP32 or PCP_BF16_REFINED (refine_iters FP32 iterations
- * follow the BF16 phase; 0 = continue in FP32 until eps).
- * Limits: p <= 1024, r <= 64. */
+ * precision: PCP_FP32 / PCP_FP32_TENSOR (split TF32), PCP_TF32_REFINED
+ * (lowp_iters one-pass TF32 iterations, then split TF32 until eps) or
+ * PCP_FP32_SIMT; the stop test is only taken on FP32-accurate iterations.
+ * Limits: p <= 512, r <= 64 (PCP_FP32_SIMT: p <= 256, r <= 32). */
 pcp_status pcp_l1_filter(const float* dM, const int32_t* d_pidx, int32_t p,
                          int64_t sp, const int32_t* d_qidx, int32_t N,
                          int64_t sq, const float* dA, int32_t lda, int32_t r,
@@ -351,7 +362,7 @@ pcp_status pcp_l1_filter(const float* dM, const int32_t* d_pidx, int32_t p,
                          float* dZ, int64_t ldz, double eps, double rho,
                          double beta0_scale, double beta_bar_ratio,
                          int32_t max_iter, int32_t precision,
-                         int32_t refine_iters, int32_t* d_iters,
+                         int32_t lowp_iters, int32_t* d_iters,
                          void* stream);
 
 /* Stage 5: factor assembly (Eq. l1s').  From the seed's FP64 skinny SVD

@@ -330,14 +330,14 @@ SEED_PHASES = {1: "prologue", 2: "T=G^T Omega", 3: "gram(T)", 4: "cholqr(T)",
 
 def pcp_l1_filter(M, d_pidx, sp, d_qidx, sq, A, r, Z, ldz, eps, rho,
                   beta0_scale=1.0, beta_bar_ratio=1e10, max_iter=500,
-                  precision=PCP_FP32, refine_iters=8, d_rank=None,
+                  precision=PCP_FP32, lowp_iters=12, d_rank=None,
                   d_scale=None, d_iters=None, stream=None):
     pA, lda = _cm(A, "A")
     check(load().pcp_l1_filter(
         _ptr(M), _ptr(d_pidx), d_pidx.numel(), sp, _ptr(d_qidx),
         d_qidx.numel(), sq, pA, lda, r, _ptr(d_rank), _ptr(d_scale), _ptr(Z),
         ldz, eps, rho, beta0_scale, beta_bar_ratio, max_iter, precision,
-        refine_iters, _ptr(d_iters), _stream(stream)), "pcp_l1_filter")
+        lowp_iters, _ptr(d_iters), _stream(stream)), "pcp_l1_filter")
 
 
 def pcp_assemble_factors(U, Sigma, V, d_rank, r, d_rows, d_cols, Lu, Lv, U32,

@@ -35,6 +35,8 @@ PCP_FP32 = 0
 PCP_BF16_REFINED = 1
 PCP_TF32_REFINED = 2
 PCP_FP64 = 3
+PCP_FP32_TENSOR = 4
+PCP_FP32_SIMT = 5
 
 
 class PCPParams(C.Structure):
@@ -49,7 +51,7 @@ class PCPParams(C.Structure):
         ("filter_tol", C.c_double), ("filter_rho", C.c_double),
         ("beta0_scale", C.c_double), ("beta_bar_ratio", C.c_double),
         ("seed_max_iter", C.c_int32), ("filter_max_iter", C.c_int32),
-        ("seed_subspace", C.c_int32), ("refine_iters", C.c_int32),
+        ("seed_subspace", C.c_int32), ("lowp_iters", C.c_int32),
         ("rng_seed", C.c_uint64),
         ("seed_rows", C.POINTER(C.c_int64)),
         ("seed_cols", C.POINTER(C.c_int64)),

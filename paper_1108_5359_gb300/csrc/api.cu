@@ -147,7 +147,7 @@ extern "C" pcp_status pcp_params_default(pcp_params* p, int64_t m, int64_t n,
   p->seed_max_iter = 500;
   p->filter_max_iter = 500;
   p->seed_subspace = 0;
-  p->refine_iters = 8;
+  p->lowp_iters = 12;
   p->rng_seed = 0x1108535900000001ull;
   p->seed_rows = nullptr;
   p->seed_cols = nullptr;
@@ -176,18 +176,23 @@ extern "C" pcp_status pcp_l1filter_plan(const pcp_params* params,
   PCP_ARG(q.m >= 2 && q.n >= 2 && q.m < (1LL << 31) && q.n < (1LL << 31),
           "pcp_l1filter_plan: m=%lld n=%lld out of range", (long long)q.m,
           (long long)q.n);
-  PCP_ARG(q.r >= 1 && q.r <= 32, "pcp_l1filter_plan: r=%d outside [1, 32]",
+  PCP_ARG(q.r >= 1 && q.r <= 64, "pcp_l1filter_plan: r=%d outside [1, 64]",
           q.r);
   PCP_ARG(q.s_r > 0 && q.s_c > 0, "pcp_l1filter_plan: oversampling <= 0");
-  PCP_ARG(q.precision == PCP_FP32,
+  PCP_ARG(q.precision == PCP_FP32 || q.precision == PCP_TF32_REFINED ||
+              q.precision == PCP_FP32_TENSOR || q.precision == PCP_FP32_SIMT,
           "pcp_l1filter_plan: precision %d not available", q.precision);
+  PCP_ARG(q.lowp_iters >= 0, "pcp_l1filter_plan: lowp_iters < 0");
   const int mp = (int)std::llround(q.s_r * q.r);
   const int np = (int)std::llround(q.s_c * q.r);
   PCP_ARG(mp >= 2 && np >= 2 && mp < q.m && np < q.n,
           "pcp_l1filter_plan: seed %dx%d does not fit in %lldx%lld", mp, np,
           (long long)q.m, (long long)q.n);
-  PCP_ARG(mp <= 256 && np <= 256,
-          "pcp_l1filter_plan: seed %dx%d larger than 256", mp, np);
+  PCP_ARG(mp <= 512 && np <= 512,
+          "pcp_l1filter_plan: seed %dx%d larger than 512", mp, np);
+  PCP_ARG(q.precision != PCP_FP32_SIMT || (q.r <= 32 && mp <= 256 && np <= 256),
+          "pcp_l1filter_plan: PCP_FP32_SIMT takes r <= 32 and seeds up to "
+          "256 (r=%d, seed %dx%d)", q.r, mp, np);
   PCP_ARG(q.filter_tol > 0 && q.filter_rho > 1 && q.beta0_scale > 0 &&
               q.beta_bar_ratio >= 1 && q.filter_max_iter >= 1,
           "pcp_l1filter_plan: bad filter parameters");
@@ -391,13 +396,13 @@ extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
                     P->d_U32, P->mp, P->r, d_rank, nullptr, dLv, P->n,
                     q.filter_tol, q.filter_rho, q.beta0_scale,
                     q.beta_bar_ratio, q.filter_max_iter, q.precision,
-                    q.refine_iters, P->d_iters, st);
+                    q.lowp_iters, P->d_iters, st);
   if (s != PCP_OK) return s;
   s = pcp_l1_filter(dM, P->d_cols, P->np, ldm, P->d_rbar, (int32_t)nrb, 1,
                     P->d_V32, P->np, P->r, d_rank, P->d_inv_sigma, dLu, P->m,
                     q.filter_tol, q.filter_rho, q.beta0_scale,
                     q.beta_bar_ratio, q.filter_max_iter, q.precision,
-                    q.refine_iters, P->d_iters + ncb, st);
+                    q.lowp_iters, P->d_iters + ncb, st);
   if (s != PCP_OK) return s;
   if (timed) PCP_CUDA(cudaEventRecord(P->ev[2], st));
   // stage 6: S = M - Lu Lv^T

@@ -98,17 +98,21 @@ pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi) {
   const pcp_params& q = pr.params;
   PCP_ARG(q.m >= 2 && q.n >= 2 && q.m < (1LL << 31) && q.n < (1LL << 31),
           "batch: m=%lld n=%lld out of range", (long long)q.m, (long long)q.n);
-  PCP_ARG(q.r >= 1 && q.r <= 32, "batch: r=%d outside [1, 32]", q.r);
-  PCP_ARG(q.precision == PCP_FP32, "batch: precision %d not available",
-          q.precision);
+  PCP_ARG(q.r >= 1 && q.r <= 64, "batch: r=%d outside [1, 64]", q.r);
+  PCP_ARG(q.precision == PCP_FP32 || q.precision == PCP_TF32_REFINED ||
+              q.precision == PCP_FP32_TENSOR || q.precision == PCP_FP32_SIMT,
+          "batch: precision %d not available", q.precision);
+  PCP_ARG(q.lowp_iters >= 0, "batch: lowp_iters < 0");
   PCP_ARG(pr.dM && pr.dLu && pr.dLv && pr.ldm >= q.m &&
               (!pr.dS || pr.lds >= q.m),
           "batch: null pointer or leading dimension too small");
   const int mp = (int)std::llround(q.s_r * q.r);
   const int np = (int)std::llround(q.s_c * q.r);
-  PCP_ARG(mp >= 2 && np >= 2 && mp < q.m && np < q.n && mp <= 256 && np <= 256,
+  PCP_ARG(mp >= 2 && np >= 2 && mp < q.m && np < q.n && mp <= 512 && np <= 512,
           "batch: seed %dx%d invalid for %lldx%lld", mp, np, (long long)q.m,
           (long long)q.n);
+  PCP_ARG(q.precision != PCP_FP32_SIMT || (q.r <= 32 && mp <= 256 && np <= 256),
+          "batch: PCP_FP32_SIMT takes r <= 32 and seeds up to 256");
   PCP_ARG(q.filter_tol > 0 && q.filter_rho > 1 && q.seed_tol > 0 &&
               q.seed_rho > 1 && q.seed_max_iter >= 1 &&
               q.filter_max_iter >= 1 && q.beta0_scale > 0 &&
@@ -299,12 +303,13 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
                             pr.ldm, U32, b.mp, q.r, b.d_rank, nullptr, pr.dLv,
                             q.n, b.d_iters, q.filter_tol, q.filter_rho,
                             q.beta0_scale, q.beta_bar_ratio,
-                            q.filter_max_iter};
+                            q.filter_max_iter, q.precision, q.lowp_iters};
     sets[2 * i + 1] = FilterSet{pr.dM, b.d_cols, b.np, pr.ldm, b.d_rbar,
                                 (int)nrb, 1, V32, b.np, q.r, b.d_rank, isg,
                                 pr.dLu, q.m, b.d_iters + ncb, q.filter_tol,
                                 q.filter_rho, q.beta0_scale,
-                                q.beta_bar_ratio, q.filter_max_iter};
+                                q.beta_bar_ratio, q.filter_max_iter,
+                                q.precision, q.lowp_iters};
   }
   // host blocks for the argument copies must outlive the async copies; the
   // handle keeps them

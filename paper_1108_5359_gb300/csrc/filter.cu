@@ -38,25 +38,6 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 
-struct FilterArgs {
-  const float* M;
-  const int32_t* pidx;
-  int p;
-  int64_t sp;
-  const int32_t* qidx;
-  int N;
-  int64_t sq;
-  const float* A;
-  int lda;
-  int r;
-  const int32_t* d_rank;
-  const float* scale;
-  float* Z;
-  int64_t ldz;
-  float eps, rho, beta0_scale, beta_bar_ratio;
-  int max_iter;
-  int32_t* iters_out;
-};
 
 template <int RMAX>
 __device__ __forceinline__ void load_arow(const float* __restrict__ As, int t,
@@ -299,7 +280,9 @@ cudaError_t dispatch_batched_r(int ri, const FilterArgs* d_sets,
   return cudaErrorInvalidValue;
 }
 
-constexpr int kShapeClasses = 12;
+// SIMT classes 0..11, tensor-core classes 12..35 (12 + tc_shape_class)
+constexpr int kSimtClasses = 12;
+constexpr int kShapeClasses = kSimtClasses + 24;
 
 size_t args_block_bytes(int nsets) {
   return (sizeof(FilterArgs) * (size_t)nsets + 255) / 256 * 256;
@@ -307,9 +290,13 @@ size_t args_block_bytes(int nsets) {
 
 }  // namespace
 
+bool filter_uses_simt(int precision, int p, int r) {
+  return precision == PCP_FP32_SIMT && p <= 256 && r <= 32;
+}
+
 size_t filter_batch_bytes(const FilterSet* sets, int nsets) {
   size_t tiles = 0;
-  for (int i = 0; i < nsets; ++i) tiles += (size_t)(sets[i].N + 31) / 32;
+  for (int i = 0; i < nsets; ++i) tiles += (size_t)(sets[i].N + 15) / 16;
   return args_block_bytes(nsets) + 8 * tiles + 16 * kShapeClasses;
 }
 
@@ -322,8 +309,9 @@ pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
   std::vector<std::vector<int32_t>> by_class(kShapeClasses);
   for (int i = 0; i < nsets; ++i) {
     const FilterSet& f = sets[i];
-    PCP_ARG(f.p >= 1 && f.p <= 256 && f.r >= 1 && f.r <= 32 && f.N >= 0,
+    PCP_ARG(f.p >= 1 && f.p <= 512 && f.r >= 1 && f.r <= 64 && f.N >= 0,
             "batched filter: set %d has p=%d r=%d N=%d", i, f.p, f.r, f.N);
+    const bool simt = filter_uses_simt(f.precision, f.p, f.r);
     FilterArgs a;
     a.M = f.M;
     a.pidx = f.pidx;
@@ -344,10 +332,14 @@ pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
     a.beta0_scale = (float)f.beta0_scale;
     a.beta_bar_ratio = (float)f.beta_bar_ratio;
     a.max_iter = f.max_iter;
+    a.lowp_iters = f.precision == PCP_TF32_REFINED ? f.lowp_iters : 0;
     a.iters_out = f.iters_out;
     std::memcpy(ha + i, &a, sizeof(a));
-    std::vector<int32_t>& t = by_class[shape_class(f.p, f.r)];
-    for (int b = 0; b < (f.N + 31) / 32; ++b) {
+    const int cls = simt ? shape_class(f.p, f.r)
+                         : kSimtClasses + tc_shape_class(f.p, f.r);
+    const int per_tile = simt ? 32 : 16;
+    std::vector<int32_t>& t = by_class[cls];
+    for (int b = 0; b < (f.N + per_tile - 1) / per_tile; ++b) {
       t.push_back(i);
       t.push_back(b);
     }
@@ -368,8 +360,16 @@ pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
     if (by_class[c].empty()) continue;
     const int ntiles = (int)(by_class[c].size() / 2);
     const int32_t* d_tiles = reinterpret_cast<const int32_t*>(db + class_off[c]);
-    const int si = c / 4, ri = c % 4;
     cudaError_t e;
+    if (c >= kSimtClasses) {
+      e = l1_filter_tc_batched_launch(c - kSimtClasses, d_sets, d_tiles,
+                                      ntiles, st);
+      if (e != cudaSuccess)
+        return cuda_fail(e, "adm_tc_batched_kernel launch", __FILE__,
+                         __LINE__);
+      continue;
+    }
+    const int si = c / 4, ri = c % 4;
     if (si == 0)
       e = dispatch_batched_r<8>(ri, d_sets, d_tiles, ntiles, st);
     else if (si == 1)
@@ -390,10 +390,9 @@ extern "C" pcp_status pcp_l1_filter(
     int32_t r, const int32_t* d_rank, const float* d_scale, float* dZ,
     int64_t ldz, double eps, double rho, double beta0_scale,
     double beta_bar_ratio, int32_t max_iter, int32_t precision,
-    int32_t refine_iters, int32_t* d_iters, void* stream) {
-  (void)refine_iters;
-  PCP_ARG(p >= 1 && p <= 256, "pcp_l1_filter: p=%d outside [1, 256]", p);
-  PCP_ARG(r >= 1 && r <= 32, "pcp_l1_filter: r=%d outside [1, 32]", r);
+    int32_t lowp_iters, int32_t* d_iters, void* stream) {
+  PCP_ARG(p >= 1 && p <= 512, "pcp_l1_filter: p=%d outside [1, 512]", p);
+  PCP_ARG(r >= 1 && r <= 64, "pcp_l1_filter: r=%d outside [1, 64]", r);
   PCP_ARG(N >= 0, "pcp_l1_filter: N=%d < 0", N);
   PCP_ARG(lda >= p, "pcp_l1_filter: lda=%d < p=%d", lda, p);
   PCP_ARG(ldz >= 1, "pcp_l1_filter: ldz < 1");
@@ -401,9 +400,13 @@ extern "C" pcp_status pcp_l1_filter(
           "pcp_l1_filter: need eps > 0, rho > 1, beta0_scale > 0, "
           "beta_bar_ratio >= 1");
   PCP_ARG(max_iter >= 1, "pcp_l1_filter: max_iter < 1");
-  PCP_ARG(precision == PCP_FP32 || precision == PCP_BF16_REFINED,
+  PCP_ARG(lowp_iters >= 0, "pcp_l1_filter: lowp_iters < 0");
+  PCP_ARG(precision >= PCP_FP32 && precision <= PCP_FP32_SIMT,
           "pcp_l1_filter: unknown precision %d", precision);
-  if (precision != PCP_FP32) {
+  PCP_ARG(precision != PCP_FP32_SIMT || (p <= 256 && r <= 32),
+          "pcp_l1_filter: the SIMT form takes p <= 256 and r <= 32 "
+          "(p=%d r=%d)", p, r);
+  if (precision == PCP_BF16_REFINED || precision == PCP_FP64) {
     pcp::set_error("pcp_l1_filter: precision %d not built", precision);
     return PCP_ERR_UNSUPPORTED;
   }
@@ -429,16 +432,23 @@ extern "C" pcp_status pcp_l1_filter(
   a.beta0_scale = (float)beta0_scale;
   a.beta_bar_ratio = (float)beta_bar_ratio;
   a.max_iter = max_iter;
+  a.lowp_iters = precision == PCP_TF32_REFINED ? lowp_iters : 0;
   a.iters_out = d_iters;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
-  if (p <= 64)
-    e = pcp::dispatch_r<8>(a, st);
-  else if (p <= 128)
-    e = pcp::dispatch_r<16>(a, st);
-  else
-    e = pcp::dispatch_r<32>(a, st);
-  if (e != cudaSuccess)
-    return pcp::cuda_fail(e, "adm_f32_kernel launch", __FILE__, __LINE__);
+  if (pcp::filter_uses_simt(precision, p, r)) {
+    if (p <= 64)
+      e = pcp::dispatch_r<8>(a, st);
+    else if (p <= 128)
+      e = pcp::dispatch_r<16>(a, st);
+    else
+      e = pcp::dispatch_r<32>(a, st);
+    if (e != cudaSuccess)
+      return pcp::cuda_fail(e, "adm_f32_kernel launch", __FILE__, __LINE__);
+  } else {
+    e = pcp::l1_filter_tc_launch(a, st);
+    if (e != cudaSuccess)
+      return pcp::cuda_fail(e, "adm_tc_kernel launch", __FILE__, __LINE__);
+  }
   return PCP_OK;
 }

@@ -50,6 +50,41 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
 SeedCtl* seed_ctl_ptr_cta(void* d_work, int mp, int np, int kmax);
 int* seed_rank_ptr_cta(void* d_work, int mp, int np, int kmax);
 
+// Device arguments of one set of Algorithm 1 problems (see pcp_l1_filter).
+// lowp_iters: tensor-core kernel only, iterations with one-pass TF32
+// products before the split (FP32-accurate) products; 0 = split throughout.
+struct FilterArgs {
+  const float* M;
+  const int32_t* pidx;
+  int p;
+  int64_t sp;
+  const int32_t* qidx;
+  int N;
+  int64_t sq;
+  const float* A;
+  int lda;
+  int r;
+  const int32_t* d_rank;
+  const float* scale;
+  float* Z;
+  int64_t ldz;
+  float eps, rho, beta0_scale, beta_bar_ratio;
+  int max_iter;
+  int lowp_iters;
+  int32_t* iters_out;
+};
+
+// Tensor-core form of Algorithm 1 (filter_tc.cu): 16 problems per CTA,
+// p <= 512, r <= 64.  Single launch over a.N problems.
+bool l1_filter_tc_fits(int p, int r);
+cudaError_t l1_filter_tc_launch(const FilterArgs& a, cudaStream_t st);
+// Batched: CTA b runs 16-problem tile tiles[2b+1] of set tiles[2b]; every
+// set of one launch has the same kernel shape (tc_shape_class).
+int tc_shape_class(int p, int r);
+cudaError_t l1_filter_tc_batched_launch(int shape, const FilterArgs* d_sets,
+                                        const int32_t* d_tiles, int ntiles,
+                                        cudaStream_t st);
+
 // One set of Algorithm 1 problems for the batched filter (the arguments of
 // pcp_l1_filter, constants included, so that every set keeps its own).
 struct FilterSet {
@@ -70,7 +105,12 @@ struct FilterSet {
   int32_t* iters_out;
   double eps, rho, beta0_scale, beta_bar_ratio;
   int max_iter;
+  int precision;   // pcp_precision
+  int lowp_iters;  // PCP_TF32_REFINED
 };
+// The FP32 SIMT kernel serves PCP_FP32_SIMT (p <= 256, r <= 32); every
+// other precision runs on the tensor-core kernel.
+bool filter_uses_simt(int precision, int p, int r);
 // Bytes of the device argument block for these sets (h_buf and d_buf).
 size_t filter_batch_bytes(const FilterSet* sets, int nsets);
 // All sets, 32 problems per CTA, one launch per kernel shape present (the

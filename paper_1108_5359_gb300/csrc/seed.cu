@@ -50,6 +50,7 @@ constexpr int kSeedThreads = 256;
 constexpr int kSeedKmaxLimit = 64;
 constexpr int kSeedTraceCap = 4096;  // (timestamp, phase) records
 constexpr int kSeedTeamMax = 64;     // largest team of the batched solver
+constexpr int kSeedMaxSide = 512;    // largest m', n'
 
 struct SeedLayout {
   size_t ctl, part, colsq, S, Y, G, Gt, Om, P, Pt, T, Psi, PsiT, Gam, Gam2,
@@ -515,8 +516,8 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
   extern __shared__ __align__(16) double sm[];
   const int kmax = a.kmax;
   double* red = sm;                      // kSeedThreads
-  double* xs = red + kSeedThreads;       // 256 (staged column, len <= 256)
-  double* lam = xs + 256;                // kmax (singular values s_c)
+  double* xs = red + kSeedThreads;       // kSeedMaxSide (staged column)
+  double* lam = xs + kSeedMaxSide;       // kmax (singular values s_c)
   double* dsc = lam + kmax;              // kmax
   double* xi = dsc + kmax;               // kmax
   double* rowb = xi + kmax;              // kmax
@@ -1063,8 +1064,8 @@ __global__ void seed_ctl_zero_kernel(const SeedArgs* __restrict__ args,
 }
 
 size_t seed_smem_bytes(int kmax) {
-  return sizeof(double) * ((size_t)kmax * kmax + kSeedThreads + 256 +
-                           4 * kmax) +
+  return sizeof(double) * ((size_t)kmax * kmax + kSeedThreads +
+                           kSeedMaxSide + 4 * kmax) +
          sizeof(float) * ((size_t)3 * kmax * kmax) +
          sizeof(int) * 2 * kmax + (size_t)kmax * kmax;
 }
@@ -1300,8 +1301,10 @@ extern "C" pcp_status pcp_seed_pcp(const double* dD, int32_t mp, int32_t np,
                                    double* dU, double* dSigma, double* dV,
                                    int32_t* h_rank, int32_t* h_iters,
                                    double* h_residual, void* stream) {
-  PCP_ARG(mp >= 2 && np >= 2 && mp <= 256 && np <= 256,
-          "pcp_seed_pcp: seed %dx%d outside [2, 256]", mp, np);
+  PCP_ARG(mp >= 2 && np >= 2 && mp <= pcp::kSeedMaxSide &&
+              np <= pcp::kSeedMaxSide,
+          "pcp_seed_pcp: seed %dx%d outside [2, %d]", mp, np,
+          pcp::kSeedMaxSide);
   PCP_ARG(kmax >= 2 && kmax <= pcp::kSeedKmaxLimit && kmax % 2 == 0 &&
               kmax <= std::min(mp, np) + (std::min(mp, np) & 1),
           "pcp_seed_pcp: kmax=%d must be even, <= %d and <= min(mp,np)", kmax,

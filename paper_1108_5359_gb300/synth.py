@@ -30,6 +30,7 @@ __all__ = [
     "seed_indices",
     "make_config",
     "CONFIGS",
+    "lowrank_factors",
     "uneven_instances",
     "video_like",
     "checkerboard",
@@ -115,6 +116,15 @@ def lowrank_plus_sparse(m, n, r, density, lo, hi, seed=0, factor_std=1.0,
     if not keep_truth:
         return M, None, None
     return M, L0.astype(dtype, copy=False), S0.astype(dtype, copy=False)
+
+
+def lowrank_factors(m, n, r, seed=0, factor_std=1.0):
+    """The X (m x r) and Y (n x r) that lowrank_plus_sparse draws for the
+    same seed (L0 = X Y^T), for checking sampled entries of a large L0."""
+    rng = _rng(seed)
+    X = rng.standard_normal((m, r)) * factor_std
+    Y = rng.standard_normal((n, r)) * factor_std
+    return X, Y
 
 
 def seed_indices(m, n, mp, np_, seed=0):

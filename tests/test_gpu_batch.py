@@ -152,7 +152,7 @@ def test_empty_batch_and_bad_instance_rejected():
     assert lib.pcp_l1filter_batch(0, None, None, None) == 0
     P = synth.make_config("c1_500_r5", seed=3)
     dM, Lu, Lv, S = _buffers(P)
-    p = pk.pcp_params_default(P.m, P.n, 40)      # r > 32
+    p = pk.pcp_params_default(P.m, P.n, 70)      # r > 64
     q = pk.problem(p, dM, Lu, Lv, S)
     arr = (_abi.PCPProblem * 1)(q.c)
     assert lib.pcp_l1filter_batch(1, arr, None, None) == _abi.PCP_ERR_ARG

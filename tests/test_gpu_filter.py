@@ -1,7 +1,8 @@
 """GPU parity of Algorithm 1 (pcp_l1_filter) against the FP64 oracle.
 
 Each column of X is an independent l1 regression on an orthonormal basis A
-(Eq. l1g).  The CUDA kernel (FP32, eps = 3e-7) must give A z within relative
+(Eq. l1g).  The FP32 SIMT kernel (PCP_FP32_SIMT, eps = 3e-7; the tensor-core
+kernel is covered by test_gpu_filter_tc.py) must give A z within relative
 Frobenius error 1e-5 of the oracle's FP64 answer (eps = 1e-10), for column
 problems (entries strided by 1) and row problems (entries strided by ldm),
 ragged counts (N not a multiple of the 32 problems per CTA, p not a multiple
@@ -28,7 +29,11 @@ def _problem(seed, p, r, N, dens=0.1, mag=50.0):
     return A, X
 
 
-def _run(A, X, orientation, eps=3e-7, max_iter=500, rank=None, scale=None):
+PCP_FP32_SIMT = 5
+
+
+def _run(A, X, orientation, eps=3e-7, max_iter=500, rank=None, scale=None,
+         precision=PCP_FP32_SIMT, lowp_iters=12):
     import torch
     import paper_1108_5359_gb300 as pk
     build_and_load()
@@ -50,7 +55,8 @@ def _run(A, X, orientation, eps=3e-7, max_iter=500, rank=None, scale=None):
         np.asarray(scale, np.float32), device="cuda")
     pk.pcp_l1_filter(M, pidx, sp, qidx, sq, dA, r, Z, Z.stride(1), eps, 1.5,
                      max_iter=max_iter, d_rank=d_rank, d_scale=d_scale,
-                     d_iters=iters)
+                     d_iters=iters, precision=precision,
+                     lowp_iters=lowp_iters)
     torch.cuda.synchronize()
     return to_host(Z[:N, :]).T, iters.cpu().numpy()
 
