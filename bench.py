@@ -408,25 +408,39 @@ def run_ours(args):
     np_ = P.cols.size
     spass_bytes = 8 * mn + 4 * r * (m + n)
     kiter = last_info["filter_iters_max"]
-    filt_flops = 4.0 * r * ((n - np_) * mp + (m - mp) * np_)  # per iteration
+    kmean = last_info.get("filter_iters_mean") or kiter
+    # algorithmic flops of Algorithm 1: 4 p r per problem-iteration (A z and
+    # A^T u), summed over problems at their own iteration counts
+    filt_flops = 4.0 * r * ((n - np_) * mp + (m - mp) * np_) * kmean
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s, SIMT FMA
     fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12     # TFLOP/s
+    # dense TF32 tensor peak: the measured bf16 figure times the nominal
+    # tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s)
+    tf32_peak = pk_d["bf16_tflops"] * 1.1 / 2.25
+    k_seed = r + max(6, r // 4)
+    seed_flops = (last_info["seed_iters"] + 3) * (
+        6.0 * mp * np_ * k_seed + 4.0 * (mp + np_) * k_seed ** 2)
+    tc = args.precision != "fp32simt"
     stages = {
         "spass": {"bound": "hbm", "ms": mean["spass"],
                   "achieved": spass_bytes / (mean["spass"] * 1e-3) / 1e9,
                   "peak": pk_d["hbm_gbs"], "unit": "GB/s",
                   "algorithmic_bytes": spass_bytes},
-        "filter": {"bound": "alu", "ms": mean["filter"],
-                   "achieved": filt_flops * kiter / (mean["filter"] * 1e-3)
-                   / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                   "note": "FP32 FMA; flops = 4 p r per problem-iteration "
-                           "at the slowest problem's iteration count"},
+        "filter": {"bound": "tensor" if tc else "alu", "ms": mean["filter"],
+                   "achieved": filt_flops / (mean["filter"] * 1e-3) / 1e12,
+                   "peak": tf32_peak if tc else fp32_peak, "unit": "TFLOP/s",
+                   "iters_mean": kmean, "iters_max": kiter,
+                   "note": ("algorithmic flops 4 p r per problem-iteration "
+                            "at each problem's own count; " +
+                            ("TF32 tensor peak (measured bf16 x 1.1/2.25); "
+                             "split-TF32 executes 3 passes per product"
+                             if tc else "FP32 FMA peak derived"))},
         "seed": {"bound": "alu", "ms": mean["seed"], "unit": "TFLOP/s",
                  "peak": fp64_peak,
-                 "achieved": (28 * 6.0 * mp * np_ * (r + 6))
-                 / (mean["seed"] * 1e-3) / 1e12,
-                 "note": "FP64; ~6 m'n'k flops per ALM iteration, ~28 "
-                         "iterations incl. prologue"},
+                 "achieved": seed_flops / (mean["seed"] * 1e-3) / 1e12,
+                 "note": "FP64; 6 m'n'k + 4 (m'+n') k^2 flops per ALM "
+                         "iteration (k = r + max(6, r/4)), seed iterations "
+                         "+ 3 prologue passes"},
     }
     for v in stages.values():
         v["frac"] = v["achieved"] / v["peak"]
@@ -440,8 +454,11 @@ def run_ours(args):
                 "bound": d["bound"], "achieved": d["achieved"],
                 "peak": d["peak"], "unit": d["unit"], "frac": d["frac"],
                 "traffic": None,
-                "peak_source": pk_src if d["bound"] == "hbm" else
-                "derived: 152 SMs x FMA lanes x 2 x 2.07 GHz"}
+                "peak_source": (pk_src + " hbm_gbs" if d["bound"] == "hbm"
+                                else (pk_src + " bf16_tflops x 1.1/2.25"
+                                      if d["bound"] == "tensor" else
+                                      "derived: 152 SMs x FP64 FMA/clk x 2 "
+                                      "x 2.07 GHz"))}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

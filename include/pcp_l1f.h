@@ -126,6 +126,7 @@ typedef struct pcp_info {
                                batch / request end to end) */
   int32_t status;           /* pcp_status of this solve */
   int32_t reserved;
+  double filter_iters_mean; /* mean Algorithm 1 iterations per problem */
 } pcp_info;
 
 /* One instance of a batched or served solve: its parameters and buffers

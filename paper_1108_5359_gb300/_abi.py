@@ -68,6 +68,7 @@ class PCPInfo(C.Structure):
         ("t_seed_ms", C.c_float), ("t_filter_ms", C.c_float),
         ("t_spass_ms", C.c_float), ("t_total_ms", C.c_float),
         ("status", C.c_int32), ("reserved", C.c_int32),
+        ("filter_iters_mean", C.c_double),
     ]
 
     def as_dict(self):

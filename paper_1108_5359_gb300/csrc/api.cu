@@ -436,12 +436,15 @@ extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
   info->lambda = P->lam_full;
   int imax = 0;
   int64_t unconv = 0;
+  double isum = 0.0;
   for (int32_t v : it) {
     imax = std::max(imax, v < 0 ? -v : v);
     unconv += (v < 0);
+    isum += v < 0 ? -v : v;
   }
   info->filter_iters_max = imax;
   info->problems_unconverged = unconv;
+  info->filter_iters_mean = it.empty() ? 0.0 : isum / (double)it.size();
   // Eq. rank_test on the numerical rank before the cap at the target r
   info->rank_ok = (rank_raw >= 1 &&
                    (double)P->mp / rank_raw >= q.s_r - 1e-9 &&

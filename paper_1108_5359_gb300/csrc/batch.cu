@@ -56,31 +56,36 @@ __global__ void batch_summary_kernel(const SummaryTask* __restrict__ tasks,
                                      BatchSummary* __restrict__ out) {
   const SummaryTask t = tasks[blockIdx.x];
   int imax = 0;
-  long long unconv = 0;
+  long long unconv = 0, isum = 0;
   for (int64_t j = threadIdx.x; j < t.nprob; j += blockDim.x) {
     const int v = t.iters[j];
     imax = max(imax, v < 0 ? -v : v);
     unconv += (v < 0);
+    isum += v < 0 ? -v : v;
   }
   __shared__ int smax[8];
-  __shared__ long long scnt[8];
+  __shared__ long long scnt[8], ssum[8];
   for (int o = 16; o > 0; o >>= 1) {
     imax = max(imax, __shfl_xor_sync(0xffffffffu, imax, o));
     unconv += __shfl_xor_sync(0xffffffffu, unconv, o);
+    isum += __shfl_xor_sync(0xffffffffu, isum, o);
   }
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
     smax[w] = imax;
     scnt[w] = unconv;
+    ssum[w] = isum;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     BatchSummary r;
     r.iters_max = 0;
     r.unconverged = 0;
+    r.iters_sum = 0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
       r.iters_max = max(r.iters_max, smax[q]);
       r.unconverged += scnt[q];
+      r.iters_sum += ssum[q];
     }
     r.rank = t.ctl->rank;
     r.iters = t.ctl->iters;
@@ -390,6 +395,8 @@ pcp_status batch_finish(BatchHandle* h, pcp_info* infos, cudaStream_t st,
       inf.lambda = b.lam_full;
       inf.filter_iters_max = u.iters_max;
       inf.problems_unconverged = u.unconverged;
+      inf.filter_iters_mean =
+          inf.problems > 0 ? (double)u.iters_sum / (double)inf.problems : 0.0;
       inf.rank_ok = (u.rank_raw >= 1 &&
                      (double)b.mp / u.rank_raw >= q.s_r - 1e-9 &&
                      (double)b.np / u.rank_raw >= q.s_c - 1e-9)

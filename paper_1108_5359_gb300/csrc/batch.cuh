@@ -23,7 +23,7 @@ struct BatchInstance {
 // Per-instance diagnostics, reduced on the device at the end of a batch.
 struct BatchSummary {
   int rank, iters, converged, rank_raw, bad, iters_max;
-  long long unconverged;
+  long long unconverged, iters_sum;
   double residual;
 };
 

@@ -321,20 +321,31 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
   __syncthreads();
   // scaled Gram in FP32 (redundant per CTA: FP64 here would occupy the
   // chip's narrow FP64 pipe in every CTA at once)
+  int coupled = 0;
   for (int a = tid >> 4; a < k; a += kSeedThreads / 16) {
     const float da = (float)dsc[a];
     for (int b = tid & 15; b < k; b += 16) {
       float v = (float)ldg_cg(Gm + a * kmax + b) * da * (float)dsc[b];
-      if (dead[a] || dead[b]) v = (a == b) ? 1.0f : 0.0f;
+      if (dead[a] || dead[b]) {
+        v = (a == b) ? 1.0f : 0.0f;
+        coupled = 1;
+      } else if (a != b && !(fabsf(v) <= 1e-3f)) {
+        coupled = 1;
+      }
       A32[a * k + b] = v;
     }
   }
+  // Nearly orthogonal columns (warm-started iterations): the Cholesky
+  // factor of I + F with |F| <= 1e-3 is R = I + triu(F) + O(1e-6); the
+  // O(1e-6) non-orthogonality it leaves is removed with E downstream, so
+  // the k sequential pivot steps are skipped.
+  const bool near_orth = !__syncthreads_or(coupled);
   long long q1 = prof ? clock64() : 0;
   // Right-looking Cholesky, R in the upper triangle.  Step j's trailing
   // update reads row j unscaled (times 1/pivot^2); row j is scaled at the
   // start of step j+1.  The reciprocal alternates between two slots so step
   // j+1's pivot never overwrites the value step j's scaling still reads.
-  for (int j = 0; j < k; ++j) {
+  for (int j = 0; j < (near_orth ? 0 : k); ++j) {
     __syncthreads();
     if (j > 0) {
       const float inv = s_inv[(j - 1) & 1];
@@ -442,6 +453,7 @@ __device__ float* block_jacobi32(float* A0, float* A1, float* V, int k,
     tab[e] = (unsigned char)(x == 0 ? 0 : 1 + (x - 1 + round) % (k - 1));
   }
   __shared__ int s_rot[2];
+  __shared__ float s_cs[kSeedKmaxLimit];  // (c, s) of each pair
   const bool prof = cyc && blockIdx.x == 0 && tid == 0;
   long long c0 = 0;
   for (int idx = tid; idx < k * k; idx += kSeedThreads)
@@ -457,6 +469,25 @@ __device__ float* block_jacobi32(float* A0, float* A1, float* V, int k,
       const long long t0 = prof ? clock64() : 0;
       __syncthreads();
       if (prof) c0 += clock64() - t0;
+      // Wide matrices (more than 16 pairs): the pair angles are computed
+      // once each and shared (one more barrier per round); narrow ones
+      // recompute them per block (independent, so they overlap) and keep
+      // one barrier per round.
+      const bool shared_angles = half > 16;
+      if (shared_angles) {
+        const unsigned char* tr = tab + round * k;
+        for (int i = tid; i < half; i += kSeedThreads) {
+          int pi = tr[i], qi = tr[k - 1 - i];
+          if (pi > qi) { const int t = pi; pi = qi; qi = t; }
+          float ci, si;
+          if (jacobi_angle(A[pi * k + pi], A[qi * k + qi], A[pi * k + qi],
+                           ci, si))
+            s_rot[flip] = 1;
+          s_cs[2 * i] = ci;
+          s_cs[2 * i + 1] = si;
+        }
+        __syncthreads();
+      }
       // 2-D thread map without integer division: 16 x 16 for half <= 16,
       // 8 x 32 otherwise
       const int jsh = half <= 16 ? 4 : 5;
@@ -469,11 +500,20 @@ __device__ float* block_jacobi32(float* A0, float* A1, float* V, int k,
         if (pi > qi) { const int t = pi; pi = qi; qi = t; }
         if (pj > qj) { const int t = pj; pj = qj; qj = t; }
         float ci, si, cj, sj;
-        const bool ri = jacobi_angle(A[pi * k + pi], A[qi * k + qi],
-                                     A[pi * k + qi], ci, si);
-        const bool rj = jacobi_angle(A[pj * k + pj], A[qj * k + qj],
-                                     A[pj * k + qj], cj, sj);
-        if (ri && i == j) s_rot[flip] = 1;
+        bool rj;
+        if (shared_angles) {
+          ci = s_cs[2 * i];
+          si = s_cs[2 * i + 1];
+          cj = s_cs[2 * j];
+          sj = s_cs[2 * j + 1];
+          rj = sj != 0.0f;
+        } else {
+          const bool ri = jacobi_angle(A[pi * k + pi], A[qi * k + qi],
+                                       A[pi * k + qi], ci, si);
+          rj = jacobi_angle(A[pj * k + pj], A[qj * k + qj], A[pj * k + qj],
+                            cj, sj);
+          if (ri && i == j) s_rot[flip] = 1;
+        }
         const float b00 = A[pi * k + pj], b01 = A[pi * k + qj];
         const float b10 = A[qi * k + pj], b11 = A[qi * k + qj];
         const float r00 = ci * b00 - si * b10, r01 = ci * b01 - si * b11;
@@ -536,8 +576,9 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
   const unsigned long long tmo = a.timeout_ns;
   // warps per CTA for the row-wise forward substitutions: one per CTA on a
   // wide team (rows spread over many SMs' FP64 pipes), more on small teams
-  const int row_warps = kGrid ? max(1, min(kSeedThreads / 32, 128 / nb))
-                              : kSeedThreads / 32;
+  const int row_warps =
+      kGrid ? max(1, min(kSeedThreads / 32, (max(mp, np) + nb - 1) / nb))
+            : kSeedThreads / 32;
   auto team_sync = [&]() -> bool {
     if (kGrid) return grid_sync(ctl, nb, tmo);
     __syncthreads();
@@ -689,11 +730,52 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
       // 1e-5) and on the first Rayleigh-Ritz the sweeps run to completion so
       // the returned factors are orthonormal to FP32 accuracy.
       const int max_sweeps = (stage == 2 || res < 1e-5) ? 30 : 1;
-      float* Afin = block_jacobi32(C32, cs, W0, k,
-                                   reinterpret_cast<unsigned char*>(prs + kmax),
-                                   max_sweeps, kGrid ? &ctl->jsweeps : nullptr,
-                                   kGrid ? ctl->jcyc : nullptr);
-      (void)Afin;
+      // Warm-started iterations: in the carried Ritz basis C1 is nearly
+      // diagonal.  When every pair that matters has |c_pq| <= gate
+      // |c_qq - c_pp|, the eigenvectors are I + Theta, Theta_pq =
+      // c_pq / (c_qq - c_pp), to O(gate^2) (first-order perturbation), and
+      // that replaces the sweeps.  Pairs whose values both lie at or below
+      // the SVT threshold (tau^2 / cmax in these units) are left unmixed:
+      // both are shrunk to zero, so a rotation between them changes neither
+      // L nor the spanned subspace.
+      bool fast = false;
+      if (stage == 3) {
+        const float t2 = (float)((1.0 / mu) * (1.0 / mu) * (double)inv);
+        // far from convergence a coarser rotation is enough (the FP64
+        // refinement of the last iterations removes what it leaves)
+        const float gate = res < 1e-5 ? 1e-3f : 1e-2f;
+        int bad = 0;
+        for (int idx = tid; idx < k * k; idx += kSeedThreads) {
+          const int p = idx / k, q = idx - p * k;
+          if (p < q) {
+            const float cpp = C32[p * k + p], cqq = C32[q * k + q];
+            const float cpq = C32[p * k + q];
+            const bool exempt = cpp <= t2 && cqq <= t2;
+            if (!exempt && !(fabsf(cpq) <= gate * fabsf(cqq - cpp))) bad = 1;
+          }
+        }
+        fast = !__syncthreads_or(bad);
+        if (fast) {
+          for (int idx = tid; idx < k * k; idx += kSeedThreads) {
+            const int p = idx / k, q = idx - p * k;
+            float x = (p == q) ? 1.0f : 0.0f;
+            if (p != q) {
+              const float cpp = C32[p * k + p], cqq = C32[q * k + q];
+              if (!(cpp <= t2 && cqq <= t2))
+                x = __fdividef(C32[p * k + q], cqq - cpp);
+            }
+            W0[idx] = x;  // V[p][q]
+          }
+          __syncthreads();
+        }
+      }
+      if (!fast) {
+        float* Afin = block_jacobi32(
+            C32, cs, W0, k, reinterpret_cast<unsigned char*>(prs + kmax),
+            max_sweeps, kGrid ? &ctl->jsweeps : nullptr,
+            kGrid ? ctl->jcyc : nullptr);
+        (void)Afin;
+      }
       const long long tj1 = clock64();
       if (b == 0 && tid == 0) ctl->jcyc[1] += tj1 - tj0;
       // W = V - (E/2) V (E kept as floats in Vd, V in W0), written to J0,
@@ -915,39 +997,108 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     const double mu_next = fmin(a.rho * mu, mu_max);
     const double inv_mu = 1.0 / mu, inv_mu_next = 1.0 / mu_next;
     const double lam_mu = a.lam * inv_mu;
-    for (int v = b; v < nv; v += nb) {
-      double zz = 0.0;
-      for (int j = v; j < np; j += nv) {
-        for (int c = tid; c < k; c += kSeedThreads)
-          xi[c] = dsc[c] * ldg_cg(PsiTc + (size_t)j * kmax + c);
-        __syncthreads();
-        for (int i = tid; i < mp; i += kSeedThreads) {
-          const double* pr = Ptc + (size_t)i * kmax;
-          double l0 = 0.0, l1 = 0.0;
-          int c = 0;
-          for (; c + 1 < k; c += 2) {
-            l0 = fma(ldg_cg(pr + c), xi[c], l0);
-            l1 = fma(ldg_cg(pr + c + 1), xi[c + 1], l1);
+    // Tiled form: TT x TT tiles of L from Pt / PsiT rows staged in the
+    // shared memory the k x k phases are done with (Vd .. cs, 20 kmax^2
+    // bytes); G^T is written through a staged tile so both G and G^T
+    // stores are coalesced.  Tile t belongs to partial-sum slot t mod nv.
+    // Tile side: 32 when that still gives every CTA of the team about one
+    // tile or more, else 16 (32 x 32 tiles on a 200 x 200 seed left three
+    // quarters of a 200-CTA team idle: 43 us against 29 us per update for
+    // the per-column form).
+    auto tiles_of = [&](int t) { return ((mp + t - 1) / t) * ((np + t - 1) / t); };
+    const bool fit32 = 8 * (64 * (kmax + 1) + 32 * 33) <= 20 * kmax * kmax;
+    const bool fit16 = 8 * (32 * (kmax + 1) + 16 * 17) <= 20 * kmax * kmax;
+    const int TT = (fit32 && 2 * tiles_of(32) >= nv) ? 32 : (fit16 ? 16 : 0);
+    auto alm_elem = [&](const double l, const int i, const int j,
+                        double& zz) -> double {
+      const size_t e = (size_t)j * mp + i;
+      const double d = __ldg(a.D + e);
+      const double y = ldg_cg(a.Y + e);
+      const double s = shrink(d - l + y * inv_mu, lam_mu);
+      const double z = d - l - s;
+      const double yn = fma(mu, z, y);
+      zz = fma(z, z, zz);
+      __stcg(a.S + e, s);
+      __stcg(a.Y + e, yn);
+      const double g = d - s + yn * inv_mu_next;
+      __stcg(a.G + e, g);
+      return g;
+    };
+    if (TT > 0) {
+      const int kp = k | 1;  // odd row pitch: conflict-free FP64 reads
+      double* Pts = Vd;                 // [TT][kp]
+      double* Qs = Pts + TT * kp;       // [TT][kp], scaled by d
+      double* Gs = Qs + TT * kp;        // [TT][TT + 1]
+      const int tcn = (np + TT - 1) / TT;
+      const int ntile = ((mp + TT - 1) / TT) * tcn;
+      for (int v = b; v < nv; v += nb) {
+        double zz = 0.0;
+        for (int tile = v; tile < ntile; tile += nv) {
+          const int i0 = (tile / tcn) * TT, j0 = (tile % tcn) * TT;
+          for (int idx = tid; idx < TT * k; idx += kSeedThreads) {
+            const int ii = idx / k, c = idx - ii * k;
+            Pts[ii * kp + c] =
+                (i0 + ii < mp) ? ldg_cg(Ptc + (size_t)(i0 + ii) * kmax + c)
+                               : 0.0;
+            Qs[ii * kp + c] =
+                (j0 + ii < np)
+                    ? dsc[c] * ldg_cg(PsiTc + (size_t)(j0 + ii) * kmax + c)
+                    : 0.0;
           }
-          if (c < k) l0 = fma(ldg_cg(pr + c), xi[c], l0);
-          const double l = l0 + l1;
-          const size_t e = (size_t)j * mp + i;
-          const double d = __ldg(a.D + e);
-          const double y = ldg_cg(a.Y + e);
-          const double s = shrink(d - l + y * inv_mu, lam_mu);
-          const double z = d - l - s;
-          const double yn = fma(mu, z, y);
-          zz = fma(z, z, zz);
-          __stcg(a.S + e, s);
-          __stcg(a.Y + e, yn);
-          const double g = d - s + yn * inv_mu_next;
-          __stcg(a.G + e, g);
-          __stcg(a.Gt + (size_t)i * np + j, g);
+          __syncthreads();
+          for (int q = tid; q < TT * TT; q += kSeedThreads) {
+            const int ii = q % TT, jj = q / TT;
+            const int i = i0 + ii, j = j0 + jj;
+            if (i < mp && j < np) {
+              const double* pr = Pts + ii * kp;
+              const double* qr = Qs + jj * kp;
+              double l0 = 0.0, l1 = 0.0;
+              int c = 0;
+              for (; c + 1 < k; c += 2) {
+                l0 = fma(pr[c], qr[c], l0);
+                l1 = fma(pr[c + 1], qr[c + 1], l1);
+              }
+              if (c < k) l0 = fma(pr[c], qr[c], l0);
+              Gs[jj * (TT + 1) + ii] = alm_elem(l0 + l1, i, j, zz);
+            }
+          }
+          __syncthreads();
+          for (int q = tid; q < TT * TT; q += kSeedThreads) {
+            const int ii = q / TT, jj = q % TT;
+            const int i = i0 + ii, j = j0 + jj;
+            if (i < mp && j < np)
+              __stcg(a.Gt + (size_t)i * np + j, Gs[jj * (TT + 1) + ii]);
+          }
+          __syncthreads();
         }
-        __syncthreads();
+        zz = block_reduce_sum(zz, red);
+        if (tid == 0) __stcg(a.part + 4 * v + 2, zz);
       }
-      zz = block_reduce_sum(zz, red);
-      if (tid == 0) __stcg(a.part + 4 * v + 2, zz);
+    } else {
+      // narrow subspace: one column at a time
+      for (int v = b; v < nv; v += nb) {
+        double zz = 0.0;
+        for (int j = v; j < np; j += nv) {
+          for (int c = tid; c < k; c += kSeedThreads)
+            xi[c] = dsc[c] * ldg_cg(PsiTc + (size_t)j * kmax + c);
+          __syncthreads();
+          for (int i = tid; i < mp; i += kSeedThreads) {
+            const double* pr = Ptc + (size_t)i * kmax;
+            double l0 = 0.0, l1 = 0.0;
+            int c = 0;
+            for (; c + 1 < k; c += 2) {
+              l0 = fma(ldg_cg(pr + c), xi[c], l0);
+              l1 = fma(ldg_cg(pr + c + 1), xi[c + 1], l1);
+            }
+            if (c < k) l0 = fma(ldg_cg(pr + c), xi[c], l0);
+            const double g = alm_elem(l0 + l1, i, j, zz);
+            __stcg(a.Gt + (size_t)i * np + j, g);
+          }
+          __syncthreads();
+        }
+        zz = block_reduce_sum(zz, red);
+        if (tid == 0) __stcg(a.part + 4 * v + 2, zz);
+      }
     }
     ++it;
     if (!team_sync()) return;
