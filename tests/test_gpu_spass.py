@@ -55,3 +55,17 @@ def test_spass_in_place():
 def test_spass_large_ragged():
     S, ref, _ = _case(4099, 1031, 20, seed=3)
     assert relerr(S, ref) < 1e-6
+
+
+@pytest.mark.parametrize("m,n,r,ldm,lds,inplace", [
+    (4099, 1031, 50, None, None, False),   # ragged tails
+    (301, 97, 40, 303, 305, False),        # odd leading dimensions
+    (256, 130, 64, None, None, True),      # in place
+    (129, 33, 33, None, None, False)])
+def test_spass_high_rank(m, n, r, ldm, lds, inplace):
+    # ranks above 32 (the 20000 x 20000 rank-50 workload's range)
+    S, ref, r = _case(m, n, r, ldm=ldm, lds=lds, seed=r, inplace=inplace)
+    err = np.abs(S - ref).max()
+    bound = 4 * np.finfo(np.float32).eps * (10 * 4 + 2 * r * 4)
+    assert err <= bound * np.sqrt(r), err
+    assert relerr(S, ref) < 1e-6
