@@ -150,6 +150,7 @@ class L1FilterResult:
     V: np.ndarray
     rank: int
     rank_ok: bool
+    rank_raw: int
     seed_iters: int
     seed_residual: float
     col_iters: np.ndarray
@@ -204,6 +205,44 @@ def l1_filter_pcp(M, rows, cols, r=None, seed_tol=1e-7, lam_seed=None,
     else:
         L = S = None
     return L1FilterResult(L=L, S=S, Lu=Lu, Lv=Lv, W=W, U=U, sigma=sigma, V=V,
-                          rank=rk, rank_ok=ok, seed_iters=seed.iters,
+                          rank=rk, rank_ok=ok, rank_raw=rk_raw,
+                          seed_iters=seed.iters,
                           seed_residual=seed.residual, col_iters=col.iters,
                           row_iters=row.iters, Qt=col.Z, Pt=row.Z)
+
+
+def l1_filter_pcp_grow(M, row_order, col_order, r, s_r=10.0, s_c=10.0,
+                       max_frac=0.5, **kw):
+    """Algorithm 2 with the seed-size rule of Section 3.5.
+
+    The seed is the first m' = round(s_r r) entries of ``row_order`` and the
+    first n' = round(s_c r) of ``col_order`` (each sorted).  If the seed's
+    rank r' fails Eq. rank_test, the seed grows to (s_r r') x (s_c r')
+    (prefixes of the same orders) and the procedure repeats, until the test
+    holds or the next seed would exceed max_frac of a side (Eq. rank_test1),
+    where the method gives up.  The target rank r only sizes the first seed
+    and caps the rank kept.
+
+    Returns (result, sizes): the result of the last seed tried (rank_ok
+    tells whether it was accepted) and the list of (m', n') tried.
+    """
+    M = np.asarray(M, dtype=np.float64)
+    m, n = M.shape
+    row_order = np.asarray(row_order, dtype=np.int64)
+    col_order = np.asarray(col_order, dtype=np.int64)
+    mp, np_ = int(round(s_r * r)), int(round(s_c * r))
+    sizes = []
+    res = None
+    while mp <= max_frac * m and np_ <= max_frac * n:
+        rows = np.sort(row_order[:mp])
+        cols = np.sort(col_order[:np_])
+        res = l1_filter_pcp(M, rows, cols, r=r, s_r=s_r, s_c=s_c, **kw)
+        sizes.append((mp, np_))
+        if res.rank_ok:
+            break
+        nmp = int(round(s_r * res.rank_raw))
+        nnp = int(round(s_c * res.rank_raw))
+        if nmp <= mp and nnp <= np_:
+            break  # the rule would not grow the seed
+        mp, np_ = max(nmp, mp), max(nnp, np_)
+    return res, sizes
