@@ -106,6 +106,19 @@ typedef struct pcp_params {
   uint64_t rng_seed;        /* seed sampling when seed_rows/cols are NULL */
   const int64_t* seed_rows; /* optional host array, m' distinct row indices */
   const int64_t* seed_cols; /* optional host array, n' distinct col indices */
+  const int64_t* row_order; /* optional host array, a permutation of 0..m-1:
+                               the seed rows are its first m' entries
+                               (sorted); excludes seed_rows */
+  const int64_t* col_order; /* same for the columns; excludes seed_cols */
+  int32_t seed_m, seed_n;   /* > 0: seed size m', n' instead of s_r r, s_c r */
+  int32_t grow_seed;        /* 1: on a failed Eq. rank_test, grow the seed to
+                               (s_r r') x (s_c r') and solve again, until the
+                               test holds or the seed would pass half of a
+                               side (Section 3.5); needs seeds taken by order
+                               (row_order / col_order or the library's own
+                               sampling, not seed_rows / seed_cols) and a
+                               pcp_info for the solve */
+  int32_t reserved0;
 } pcp_params;
 
 /* Diagnostics of one solve. */
@@ -125,7 +138,8 @@ typedef struct pcp_info {
   float t_total_ms;         /* whole solve (batched and served forms: the
                                batch / request end to end) */
   int32_t status;           /* pcp_status of this solve */
-  int32_t reserved;
+  int32_t seed_rank_raw;    /* rank of L^s before the cap at r (Eq.
+                               rank_test uses it) */
   double filter_iters_mean; /* mean Algorithm 1 iterations per problem */
 } pcp_info;
 
@@ -175,7 +189,9 @@ pcp_status pcp_l1filter_plan(const pcp_params* params, pcp_plan** out);
  *   dS  (m x n, lds >= m), FP32, written with S = M - Lu Lv^T.  May be NULL
  *       to skip the S pass (factors only).
  *   h_seed_rows_out / h_seed_cols_out: optional host arrays of m' / n'
- *       entries receiving I_s and J_s.
+ *       entries receiving I_s and J_s (with grow_seed: room for
+ *       min(512, m/2) / min(512, n/2) entries; info->seed_m / seed_n give
+ *       the sizes of the seed the solve ended with).
  *   info: optional.  When non-NULL the call synchronises the stream and
  *       fills *info (stage times by CUDA events); when NULL the call is
  *       asynchronous except for the seed index upload.

@@ -79,27 +79,35 @@ def pcp_params_default(m, n, r) -> PCPParams:
     return p
 
 
+def _set_index_arrays(params, keep, seed_rows, seed_cols, row_order,
+                      col_order):
+    """Point params' optional host index arrays at int64 copies kept alive
+    in ``keep``."""
+    import numpy as np
+    for name, v in (("seed_rows", seed_rows), ("seed_cols", seed_cols),
+                    ("row_order", row_order), ("col_order", col_order)):
+        if v is not None:
+            a = np.ascontiguousarray(v, dtype=np.int64)
+            keep.append(a)
+            setattr(params, name, a.ctypes.data_as(C.POINTER(C.c_int64)))
+
+
 class Plan:
     """Owns a pcp_plan (device workspace) and the index arrays it points to."""
 
-    def __init__(self, params: PCPParams, seed_rows=None, seed_cols=None):
-        import numpy as np
+    def __init__(self, params: PCPParams, seed_rows=None, seed_cols=None,
+                 row_order=None, col_order=None):
         self._keep = []
-        if seed_rows is not None:
-            a = np.ascontiguousarray(seed_rows, dtype=np.int64)
-            self._keep.append(a)
-            params.seed_rows = a.ctypes.data_as(C.POINTER(C.c_int64))
-        if seed_cols is not None:
-            a = np.ascontiguousarray(seed_cols, dtype=np.int64)
-            self._keep.append(a)
-            params.seed_cols = a.ctypes.data_as(C.POINTER(C.c_int64))
+        _set_index_arrays(params, self._keep, seed_rows, seed_cols,
+                          row_order, col_order)
         self.params = params
         self.handle = C.c_void_p()
         check(load().pcp_l1filter_plan(C.byref(params), C.byref(self.handle)),
               "pcp_l1filter_plan")
         self.m, self.n, self.r = params.m, params.n, params.r
-        self.mp = int(round(params.s_r * params.r))
-        self.np = int(round(params.s_c * params.r))
+        self.mp = params.seed_m or int(round(params.s_r * params.r))
+        self.np = params.seed_n or int(round(params.s_c * params.r))
+        self.grow = bool(params.grow_seed)
 
     def close(self):
         if self.handle:
@@ -113,8 +121,9 @@ class Plan:
             pass
 
 
-def pcp_l1filter_plan(params: PCPParams, seed_rows=None, seed_cols=None):
-    return Plan(params, seed_rows, seed_cols)
+def pcp_l1filter_plan(params: PCPParams, seed_rows=None, seed_cols=None,
+                      row_order=None, col_order=None):
+    return Plan(params, seed_rows, seed_cols, row_order, col_order)
 
 
 def pcp_plan_destroy(plan: Plan):
@@ -129,14 +138,21 @@ def pcp_l1filter_solve(plan: Plan, M, Lu, Lv, S=None, info=True,
     pLu, _ = _cm(Lu, "Lu")
     pLv, _ = _cm(Lv, "Lv")
     pS, lds = _cm(S, "S")
-    rows = np.zeros(plan.mp, dtype=np.int64)
-    cols = np.zeros(plan.np, dtype=np.int64)
+    # a grown seed (Section 3.5) can reach min(512, m/2) x min(512, n/2)
+    cap_r = max(plan.mp, min(512, plan.m // 2)) if plan.grow else plan.mp
+    cap_c = max(plan.np, min(512, plan.n // 2)) if plan.grow else plan.np
+    rows = np.zeros(cap_r, dtype=np.int64)
+    cols = np.zeros(cap_c, dtype=np.int64)
     inf = PCPInfo() if info else None
     st = load().pcp_l1filter_solve(
         plan.handle, pM, ldm, pLu, pLv, pS, lds if S is not None else plan.m,
         rows.ctypes.data_as(C.POINTER(C.c_int64)),
         cols.ctypes.data_as(C.POINTER(C.c_int64)),
         C.byref(inf) if inf is not None else None, _stream(stream))
+    if inf is not None and inf.seed_m:
+        rows, cols = rows[:inf.seed_m], cols[:inf.seed_n]
+    else:
+        rows, cols = rows[:plan.mp], cols[:plan.np]
     if raise_on_error and st not in (PCP_OK,):
         check(st, "pcp_l1filter_solve")
     return st, inf, rows, cols
@@ -146,18 +162,11 @@ class _Problem:
     """A pcp_problem plus the host arrays its seed index pointers refer to."""
 
     def __init__(self, params, M, Lu, Lv, S=None, seed_rows=None,
-                 seed_cols=None):
-        import numpy as np
+                 seed_cols=None, row_order=None, col_order=None):
         self._keep = [M, Lu, Lv, S]
         p = PCPParams.from_buffer_copy(params)
-        if seed_rows is not None:
-            a = np.ascontiguousarray(seed_rows, dtype=np.int64)
-            self._keep.append(a)
-            p.seed_rows = a.ctypes.data_as(C.POINTER(C.c_int64))
-        if seed_cols is not None:
-            a = np.ascontiguousarray(seed_cols, dtype=np.int64)
-            self._keep.append(a)
-            p.seed_cols = a.ctypes.data_as(C.POINTER(C.c_int64))
+        _set_index_arrays(p, self._keep, seed_rows, seed_cols, row_order,
+                          col_order)
         pM, ldm = _cm(M, "M")
         pLu, _ = _cm(Lu, "Lu")
         pLv, _ = _cm(Lv, "Lv")
@@ -166,10 +175,12 @@ class _Problem:
                             lds if S is not None else p.m)
 
 
-def problem(params, M, Lu, Lv, S=None, seed_rows=None, seed_cols=None):
+def problem(params, M, Lu, Lv, S=None, seed_rows=None, seed_cols=None,
+            row_order=None, col_order=None):
     """One instance for pcp_l1filter_batch / pcp_serve_submit (tensors as
     for pcp_l1filter_solve; Lu must be m x r and Lv n x r with ld m / n)."""
-    return _Problem(params, M, Lu, Lv, S, seed_rows, seed_cols)
+    return _Problem(params, M, Lu, Lv, S, seed_rows, seed_cols, row_order,
+                    col_order)
 
 
 def pcp_l1filter_batch(problems, info=True, stream=None,

@@ -55,6 +55,10 @@ class PCPParams(C.Structure):
         ("rng_seed", C.c_uint64),
         ("seed_rows", C.POINTER(C.c_int64)),
         ("seed_cols", C.POINTER(C.c_int64)),
+        ("row_order", C.POINTER(C.c_int64)),
+        ("col_order", C.POINTER(C.c_int64)),
+        ("seed_m", C.c_int32), ("seed_n", C.c_int32),
+        ("grow_seed", C.c_int32), ("reserved0", C.c_int32),
     ]
 
 
@@ -67,7 +71,7 @@ class PCPInfo(C.Structure):
         ("seed_residual", C.c_double), ("lambda_", C.c_double),
         ("t_seed_ms", C.c_float), ("t_filter_ms", C.c_float),
         ("t_spass_ms", C.c_float), ("t_total_ms", C.c_float),
-        ("status", C.c_int32), ("reserved", C.c_int32),
+        ("status", C.c_int32), ("seed_rank_raw", C.c_int32),
         ("filter_iters_mean", C.c_double),
     ]
 

@@ -89,11 +89,33 @@ static std::vector<int64_t> sample_sorted(int64_t n, int64_t k,
   return out;
 }
 
+// A random permutation of [0, n) (Fisher-Yates on splitmix64): the library's
+// sampling order when seeds may grow (every prefix is a uniform sample).
+static std::vector<int64_t> sample_order(int64_t n, uint64_t seed) {
+  std::vector<int64_t> all(n);
+  std::iota(all.begin(), all.end(), 0);
+  uint64_t s = seed;
+  for (int64_t i = 0; i + 1 < n; ++i) {
+    const int64_t j = i + (int64_t)(splitmix64(s) % (uint64_t)(n - i));
+    std::swap(all[i], all[j]);
+  }
+  return all;
+}
+
+static std::vector<int64_t> sorted_prefix(const std::vector<int64_t>& order,
+                                          int64_t k) {
+  std::vector<int64_t> v(order.begin(), order.begin() + k);
+  std::sort(v.begin(), v.end());
+  return v;
+}
+
 }  // namespace pcp
 
 struct pcp_plan {
   pcp_params p;
   std::vector<int64_t> given_rows, given_cols;
+  std::vector<int64_t> row_order, col_order;  // seeds by order (prefixes)
+  pcp_plan* child = nullptr;                   // grown seed (Section 3.5)
   int64_t m, n;
   int r, mp, np, kmax, k0;
   double lam_seed, lam_full;
@@ -183,8 +205,14 @@ extern "C" pcp_status pcp_l1filter_plan(const pcp_params* params,
               q.precision == PCP_FP32_TENSOR || q.precision == PCP_FP32_SIMT,
           "pcp_l1filter_plan: precision %d not available", q.precision);
   PCP_ARG(q.lowp_iters >= 0, "pcp_l1filter_plan: lowp_iters < 0");
-  const int mp = (int)std::llround(q.s_r * q.r);
-  const int np = (int)std::llround(q.s_c * q.r);
+  const int mp = q.seed_m > 0 ? q.seed_m : (int)std::llround(q.s_r * q.r);
+  const int np = q.seed_n > 0 ? q.seed_n : (int)std::llround(q.s_c * q.r);
+  PCP_ARG(!(q.row_order && q.seed_rows) && !(q.col_order && q.seed_cols),
+          "pcp_l1filter_plan: give seed_rows or row_order, not both (same "
+          "for columns)");
+  PCP_ARG(!q.grow_seed || (!q.seed_rows && !q.seed_cols),
+          "pcp_l1filter_plan: grow_seed needs seeds taken by order "
+          "(row_order / col_order or sampling), not seed_rows / seed_cols");
   PCP_ARG(mp >= 2 && np >= 2 && mp < q.m && np < q.n,
           "pcp_l1filter_plan: seed %dx%d does not fit in %lldx%lld", mp, np,
           (long long)q.m, (long long)q.n);
@@ -207,13 +235,31 @@ extern "C" pcp_status pcp_l1filter_plan(const pcp_params* params,
     pcp_status s = check_index_set(q.seed_cols, np, q.n, "seed_cols");
     if (s != PCP_OK) return s;
   }
+  if (q.row_order) {
+    pcp_status s = check_index_set(q.row_order, q.m, q.m, "row_order");
+    if (s != PCP_OK) return s;
+  }
+  if (q.col_order) {
+    pcp_status s = check_index_set(q.col_order, q.n, q.n, "col_order");
+    if (s != PCP_OK) return s;
+  }
 
   pcp_plan* P = new pcp_plan();
   P->p = q;
   if (q.seed_rows) P->given_rows.assign(q.seed_rows, q.seed_rows + mp);
   if (q.seed_cols) P->given_cols.assign(q.seed_cols, q.seed_cols + np);
+  if (q.row_order)
+    P->row_order.assign(q.row_order, q.row_order + q.m);
+  else if (q.grow_seed)
+    P->row_order = pcp::sample_order(q.m, q.rng_seed);
+  if (q.col_order)
+    P->col_order.assign(q.col_order, q.col_order + q.n);
+  else if (q.grow_seed)
+    P->col_order = pcp::sample_order(q.n, q.rng_seed ^ 0xC01C01C0ull);
   P->p.seed_rows = nullptr;
   P->p.seed_cols = nullptr;
+  P->p.row_order = nullptr;
+  P->p.col_order = nullptr;
   P->m = q.m;
   P->n = q.n;
   P->r = q.r;
@@ -296,6 +342,7 @@ extern "C" pcp_status pcp_l1filter_plan(const pcp_params* params,
 
 extern "C" void pcp_plan_destroy(pcp_plan* P) {
   if (!P) return;
+  pcp_plan_destroy(P->child);
   for (auto& ev : P->ev)
     if (ev) cudaEventDestroy(ev);
   if (P->h_idx) cudaFreeHost(P->h_idx);
@@ -306,13 +353,18 @@ extern "C" void pcp_plan_destroy(pcp_plan* P) {
 // Upload I_s, J_s and their sorted complements (only when they changed).
 static pcp_status upload_indices(pcp_plan* P, cudaStream_t st) {
   std::vector<int64_t> rows =
-      P->given_rows.empty()
-          ? pcp::sample_sorted(P->m, P->mp, P->p.rng_seed)
-          : P->given_rows;
+      !P->row_order.empty()
+          ? pcp::sorted_prefix(P->row_order, P->mp)
+          : (P->given_rows.empty()
+                 ? pcp::sample_sorted(P->m, P->mp, P->p.rng_seed)
+                 : P->given_rows);
   std::vector<int64_t> cols =
-      P->given_cols.empty()
-          ? pcp::sample_sorted(P->n, P->np, P->p.rng_seed ^ 0xC01C01C0ull)
-          : P->given_cols;
+      !P->col_order.empty()
+          ? pcp::sorted_prefix(P->col_order, P->np)
+          : (P->given_cols.empty()
+                 ? pcp::sample_sorted(P->n, P->np,
+                                      P->p.rng_seed ^ 0xC01C01C0ull)
+                 : P->given_cols);
   if (P->idx_uploaded && rows == P->cur_rows && cols == P->cur_cols)
     return PCP_OK;
   // the previous upload may still be read by in-flight work on this stream
@@ -350,12 +402,57 @@ static pcp_status upload_indices(pcp_plan* P, cudaStream_t st) {
   return PCP_OK;
 }
 
+static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
+                             float* dLu, float* dLv, float* dS, int64_t lds,
+                             int64_t* h_seed_rows_out,
+                             int64_t* h_seed_cols_out, pcp_info* info,
+                             void* stream);
+
 extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
                                          int64_t ldm, float* dLu, float* dLv,
                                          float* dS, int64_t lds,
                                          int64_t* h_seed_rows_out,
                                          int64_t* h_seed_cols_out,
                                          pcp_info* info, void* stream) {
+  pcp_status st = solve_once(P, dM, ldm, dLu, dLv, dS, lds, h_seed_rows_out,
+                             h_seed_cols_out, info, stream);
+  if (!P || !info || !P->p.grow_seed) return st;
+  // Section 3.5: a seed whose rank r' fails Eq. rank_test grows to
+  // (s_r r') x (s_c r') (prefixes of the same orders) and the solve repeats,
+  // until the test holds or the seed would pass half of a side.
+  const pcp_params& q = P->p;
+  const pcp_plan* cur = P;
+  while (st == PCP_ERR_RANK_TEST) {
+    const int rr = info->seed_rank_raw;
+    const int gm = std::max(cur->mp, (int)std::llround(q.s_r * rr));
+    const int gn = std::max(cur->np, (int)std::llround(q.s_c * rr));
+    if (rr < 1 || (gm == cur->mp && gn == cur->np) || 2 * (int64_t)gm > q.m ||
+        2 * (int64_t)gn > q.n || gm > 512 || gn > 512)
+      break;
+    if (!P->child || P->child->mp != gm || P->child->np != gn) {
+      pcp_plan_destroy(P->child);
+      P->child = nullptr;
+      pcp_params q2 = q;
+      q2.seed_m = gm;
+      q2.seed_n = gn;
+      q2.grow_seed = 0;
+      q2.row_order = P->row_order.data();
+      q2.col_order = P->col_order.data();
+      pcp_status s2 = pcp_l1filter_plan(&q2, &P->child);
+      if (s2 != PCP_OK) return s2;
+    }
+    cur = P->child;
+    st = solve_once(P->child, dM, ldm, dLu, dLv, dS, lds, h_seed_rows_out,
+                    h_seed_cols_out, info, stream);
+  }
+  return st;
+}
+
+static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
+                             float* dLu, float* dLv, float* dS, int64_t lds,
+                             int64_t* h_seed_rows_out,
+                             int64_t* h_seed_cols_out, pcp_info* info,
+                             void* stream) {
   PCP_ARG(P, "pcp_l1filter_solve: null plan");
   PCP_ARG(dM && dLu && dLv, "pcp_l1filter_solve: null pointer");
   PCP_ARG(ldm >= P->m, "pcp_l1filter_solve: ldm < m");
@@ -432,6 +529,7 @@ extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
   info->seed_residual = resid;
   info->seed_m = P->mp;
   info->seed_n = P->np;
+  info->seed_rank_raw = rank_raw;
   info->problems = ncb + nrb;
   info->lambda = P->lam_full;
   int imax = 0;

@@ -99,6 +99,29 @@ __global__ void batch_summary_kernel(const SummaryTask* __restrict__ tasks,
 
 }  // namespace
 
+// The whole sampling order behind sample(): its first k entries, sorted,
+// are sample(n, k, seed), so seeds grown along it keep their first rows.
+std::vector<int64_t> sample_order(int64_t n, uint64_t seed) {
+  std::vector<int64_t> all(n);
+  std::iota(all.begin(), all.end(), 0);
+  uint64_t s = seed;
+  for (int64_t i = 0; i + 1 < n; ++i) {
+    const int64_t j = i + (int64_t)(splitmix(s) % (uint64_t)(n - i));
+    std::swap(all[i], all[j]);
+  }
+  return all;
+}
+
+bool grown_seed_size(const pcp_params& q, const pcp_info& inf, int* gm,
+                     int* gn) {
+  const int rr = inf.seed_rank_raw;
+  *gm = std::max((int)inf.seed_m, (int)std::llround(q.s_r * rr));
+  *gn = std::max((int)inf.seed_n, (int)std::llround(q.s_c * rr));
+  return rr >= 1 && !(*gm == inf.seed_m && *gn == inf.seed_n) &&
+         2 * (int64_t)*gm <= q.m && 2 * (int64_t)*gn <= q.n && *gm <= 512 &&
+         *gn <= 512;
+}
+
 pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi) {
   const pcp_params& q = pr.params;
   PCP_ARG(q.m >= 2 && q.n >= 2 && q.m < (1LL << 31) && q.n < (1LL << 31),
@@ -111,8 +134,13 @@ pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi) {
   PCP_ARG(pr.dM && pr.dLu && pr.dLv && pr.ldm >= q.m &&
               (!pr.dS || pr.lds >= q.m),
           "batch: null pointer or leading dimension too small");
-  const int mp = (int)std::llround(q.s_r * q.r);
-  const int np = (int)std::llround(q.s_c * q.r);
+  const int mp = q.seed_m > 0 ? q.seed_m : (int)std::llround(q.s_r * q.r);
+  const int np = q.seed_n > 0 ? q.seed_n : (int)std::llround(q.s_c * q.r);
+  PCP_ARG(!(q.row_order && q.seed_rows) && !(q.col_order && q.seed_cols),
+          "batch: give seed_rows or row_order, not both");
+  PCP_ARG(!q.grow_seed || (!q.seed_rows && !q.seed_cols),
+          "batch: grow_seed needs seeds taken by order (row_order / "
+          "col_order or sampling), not seed_rows / seed_cols");
   PCP_ARG(mp >= 2 && np >= 2 && mp < q.m && np < q.n && mp <= 512 && np <= 512,
           "batch: seed %dx%d invalid for %lldx%lld", mp, np, (long long)q.m,
           (long long)q.n);
@@ -148,6 +176,10 @@ pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi) {
           "batch: seed_rows out of range or repeated");
   PCP_ARG(!q.seed_cols || check(q.seed_cols, np, q.n),
           "batch: seed_cols out of range or repeated");
+  PCP_ARG(!q.row_order || check(q.row_order, q.m, q.m),
+          "batch: row_order is not a permutation");
+  PCP_ARG(!q.col_order || check(q.col_order, q.n, q.n),
+          "batch: col_order is not a permutation");
   return PCP_OK;
 }
 
@@ -231,12 +263,20 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
   for (int i = 0; i < count; ++i) {
     const pcp_params& q = probs[i].params;
     BatchInstance& b = h->inst[i];
+    auto prefix = [](const int64_t* order, int64_t k) {
+      std::vector<int64_t> v(order, order + k);
+      std::sort(v.begin(), v.end());
+      return v;
+    };
     std::vector<int64_t> rows =
         q.seed_rows ? std::vector<int64_t>(q.seed_rows, q.seed_rows + b.mp)
-                    : sample(q.m, b.mp, q.rng_seed);
+                    : (q.row_order ? prefix(q.row_order, b.mp)
+                                   : sample(q.m, b.mp, q.rng_seed));
     std::vector<int64_t> cols =
         q.seed_cols ? std::vector<int64_t>(q.seed_cols, q.seed_cols + b.np)
-                    : sample(q.n, b.np, q.rng_seed ^ 0xC01C01C0ull);
+                    : (q.col_order ? prefix(q.col_order, b.np)
+                                   : sample(q.n, b.np,
+                                            q.rng_seed ^ 0xC01C01C0ull));
     b.rows = rows;
     b.cols = cols;
     std::vector<char> in_r(q.m, 0), in_c(q.n, 0);
@@ -391,6 +431,7 @@ pcp_status batch_finish(BatchHandle* h, pcp_info* infos, cudaStream_t st,
       inf.seed_residual = u.residual;
       inf.seed_m = b.mp;
       inf.seed_n = b.np;
+      inf.seed_rank_raw = u.rank_raw;
       inf.problems = (q.m - b.mp) + (q.n - b.np);
       inf.lambda = b.lam_full;
       inf.filter_iters_max = u.iters_max;
@@ -465,5 +506,55 @@ extern "C" pcp_status pcp_l1filter_batch(int32_t count,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
-  return pcp::batch_finish(&h, infos, st, ms);
+  s = pcp::batch_finish(&h, infos, st, ms);
+  if (!infos) return s;
+  // Section 3.5 for the instances that ask for it: a seed failing Eq.
+  // rank_test grows to (s_r r') x (s_c r') along the same orders, and the
+  // grown instances run again as one batch, until none is left to grow.
+  std::vector<std::vector<int64_t>> orders(2 * (size_t)count);
+  for (int round = 0; round < 16; ++round) {
+    std::vector<int> idx;
+    std::vector<pcp_problem> g;
+    for (int i = 0; i < count; ++i) {
+      const pcp_params& q = probs[i].params;
+      int gm = 0, gn = 0;
+      if (!q.grow_seed || infos[i].status != PCP_ERR_RANK_TEST ||
+          !pcp::grown_seed_size(q, infos[i], &gm, &gn))
+        continue;
+      if (orders[2 * i].empty()) {
+        orders[2 * i] = q.row_order
+                            ? std::vector<int64_t>(q.row_order, q.row_order + q.m)
+                            : pcp::sample_order(q.m, q.rng_seed);
+        orders[2 * i + 1] =
+            q.col_order ? std::vector<int64_t>(q.col_order, q.col_order + q.n)
+                        : pcp::sample_order(q.n, q.rng_seed ^ 0xC01C01C0ull);
+      }
+      pcp_problem pr = probs[i];
+      pr.params.seed_m = gm;
+      pr.params.seed_n = gn;
+      pr.params.row_order = orders[2 * i].data();
+      pr.params.col_order = orders[2 * i + 1].data();
+      idx.push_back(i);
+      g.push_back(pr);
+    }
+    if (g.empty()) break;
+    std::vector<pcp_info> gi(g.size());
+    pcp::BatchHandle h2;
+    s = pcp::batch_launch((int)g.size(), g.data(), st, &h2, true);
+    if (s != PCP_OK) {
+      if (h2.d_base) cudaFreeAsync(h2.d_base, st);
+      for (cudaEvent_t e : h2.ev)
+        if (e) cudaEventDestroy(e);
+      return s;
+    }
+    pcp::batch_finish(&h2, gi.data(), st, 0.0f);
+    for (size_t u = 0; u < idx.size(); ++u) {
+      gi[u].t_total_ms += infos[idx[u]].t_total_ms;
+      infos[idx[u]] = gi[u];
+    }
+  }
+  s = PCP_OK;
+  for (int i = 0; i < count && s == PCP_OK; ++i)
+    s = (pcp_status)infos[i].status;
+  return s;
 }

@@ -42,6 +42,11 @@ struct BatchHandle {
 };
 
 pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi);
+// Section 3.5: the whole sampling order behind the library's seed sample,
+// and the grown seed size for a failed rank test (false: stop growing).
+std::vector<int64_t> sample_order(int64_t n, uint64_t seed);
+bool grown_seed_size(const pcp_params& q, const pcp_info& inf, int* gm,
+                     int* gn);
 // Device workspace one instance needs (its share of a batch).
 size_t batch_footprint(const pcp_problem& pr, const BatchInstance& bi);
 // Enqueue the whole batch on st (asynchronous; allocates with

@@ -36,7 +36,8 @@ enum ReqState { kQueued, kRunning, kDone };
 
 struct Request {
   pcp_problem prob;
-  std::vector<int64_t> rows, cols;  // copies of the optional seed sets
+  std::vector<int64_t> rows, cols;      // copies of the optional seed sets
+  std::vector<int64_t> rorder, corder;  // and sampling orders
   size_t bytes = 0;
   ReqState state = kQueued;
   pcp_status status = PCP_OK;
@@ -120,6 +121,7 @@ void finish_group(pcp_server* S, Flight* f) {
   cudaEventDestroy(f->done);
   const double t = now_ms();
   std::lock_guard<std::mutex> lock(S->mu);
+  std::vector<uint64_t> requeue;
   for (size_t i = 0; i < f->tickets.size(); ++i) {
     Request& r = S->reqs[f->tickets[i]];
     if (launch_status == PCP_OK && i < f->h.status.size()) {
@@ -129,10 +131,35 @@ void finish_group(pcp_server* S, Flight* f) {
       std::memset(&r.info, 0, sizeof(r.info));
       r.info.status = (int32_t)r.status;
     }
+    // Section 3.5: a seed failing Eq. rank_test grows and the request goes
+    // back to the head of the queue
+    pcp_params& q = r.prob.params;
+    int gm = 0, gn = 0;
+    if (q.grow_seed && r.status == PCP_ERR_RANK_TEST &&
+        pcp::grown_seed_size(q, r.info, &gm, &gn)) {
+      if (r.rorder.empty()) r.rorder = pcp::sample_order(q.m, q.rng_seed);
+      if (r.corder.empty())
+        r.corder = pcp::sample_order(q.n, q.rng_seed ^ 0xC01C01C0ull);
+      q.seed_m = gm;
+      q.seed_n = gn;
+      q.row_order = r.rorder.data();
+      q.col_order = r.corder.data();
+      pcp::BatchInstance bi;
+      if (pcp::batch_validate(r.prob, &bi) == PCP_OK) {
+        r.bytes = pcp::batch_footprint(r.prob, bi);
+        r.status = PCP_OK;
+        r.state = kQueued;
+        requeue.push_back(f->tickets[i]);
+        continue;
+      }
+    }
     r.t_done = t;
     r.info.t_total_ms = (float)(t - r.t_submit);
     r.state = kDone;
   }
+  for (auto it = requeue.rbegin(); it != requeue.rend(); ++it)
+    S->queue.push_front(*it);
+  if (!requeue.empty()) S->cv.notify_all();
   S->used_bytes -= f->bytes;
   S->used_slots -= (int)f->tickets.size();
   S->stream_busy[f->stream_slot] = 0;
@@ -272,6 +299,16 @@ extern "C" pcp_status pcp_serve_submit(pcp_server* S, const pcp_problem* prob,
   if (prob->params.seed_cols) {
     r.cols.assign(prob->params.seed_cols, prob->params.seed_cols + bi.np);
     r.prob.params.seed_cols = r.cols.data();
+  }
+  if (prob->params.row_order) {
+    r.rorder.assign(prob->params.row_order,
+                    prob->params.row_order + prob->params.m);
+    r.prob.params.row_order = r.rorder.data();
+  }
+  if (prob->params.col_order) {
+    r.corder.assign(prob->params.col_order,
+                    prob->params.col_order + prob->params.n);
+    r.prob.params.col_order = r.corder.data();
   }
   r.bytes = pcp::batch_footprint(*prob, bi);
   r.t_submit = now_ms();

@@ -31,6 +31,7 @@ __all__ = [
     "make_config",
     "CONFIGS",
     "lowrank_factors",
+    "seed_orders",
     "uneven_instances",
     "video_like",
     "checkerboard",
@@ -125,6 +126,20 @@ def lowrank_factors(m, n, r, seed=0, factor_std=1.0):
     X = rng.standard_normal((m, r)) * factor_std
     Y = rng.standard_normal((n, r)) * factor_std
     return X, Y
+
+
+def seed_orders(m, n, rows, cols, seed=0):
+    """Row and column sampling orders whose first entries are the given
+    seed sets (then the remaining indices in random order), for seeds that
+    may grow by prefixes (Section 3.5)."""
+    rng = _rng((seed, 0x0DE2))
+    out = []
+    for size, first in ((m, rows), (n, cols)):
+        first = np.asarray(first, dtype=np.int64)
+        rest = np.setdiff1d(np.arange(size), first)
+        out.append(np.concatenate([rng.permutation(first),
+                                   rng.permutation(rest)]))
+    return out[0], out[1]
 
 
 def seed_indices(m, n, mp, np_, seed=0):

@@ -157,3 +157,36 @@ def test_empty_batch_and_bad_instance_rejected():
     arr = (_abi.PCPProblem * 1)(q.c)
     assert lib.pcp_l1filter_batch(1, arr, None, None) == _abi.PCP_ERR_ARG
     assert b"instance 0" in lib.pcp_last_error()
+
+
+def test_batch_grows_failed_seeds():
+    # Section 3.5 in the batched form: an instance whose 50 x 50 seed fails
+    # Eq. rank_test is grown and rerun; the other instance is untouched
+    import torch
+    import paper_1108_5359_gb300 as pk
+    from tests.test_gpu_grow import _instance
+    build_and_load()
+    M, L0, S0, ro, co = _instance(0)
+    P2 = synth.make_config("c1_500_r5", seed=3)
+    probs, bufs = [], []
+    for Mx, r, rows, cols, order in ((M, 5, None, None, (ro, co)),
+                                     (P2.M, 5, P2.rows, P2.cols, None)):
+        m, n = Mx.shape
+        dM = to_dev_cm(Mx.astype(np.float32))
+        Lu, Lv, S = pk.colmajor(m, r), pk.colmajor(n, r), pk.colmajor(m, n)
+        p = pk.pcp_params_default(m, n, r)
+        if order is not None:
+            p.grow_seed = 1
+            probs.append(pk.problem(p, dM, Lu, Lv, S, row_order=order[0],
+                                    col_order=order[1]))
+        else:
+            probs.append(pk.problem(p, dM, Lu, Lv, S, rows, cols))
+        bufs.append((Lu, Lv, S))
+    st, infos = pk.pcp_l1filter_batch(probs, raise_on_error=False)
+    torch.cuda.synchronize()
+    assert st == 0
+    assert infos[0].seed_m > 50 and infos[0].rank == 5
+    Lu, Lv, S = bufs[0]
+    L = to_host(Lu) @ to_host(Lv).T
+    assert relerr(L, L0) < TOL and relerr(to_host(S), S0) < TOL
+    assert infos[1].seed_m == 50

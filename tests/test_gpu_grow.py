@@ -1,0 +1,79 @@
+"""GPU parity of the seed-size rule of Section 3.5 (pcp_params.grow_seed).
+
+A 600 x 560 rank-5 matrix with 12% corruption: its 50 x 50 seed fails Eq.
+rank_test, the seed grows to (s_r r') x (s_c r') as prefixes of the same row
+/ column orders, and the grown solve must match the oracle's grown solve
+(same final seed size, rank, L and S within 1e-5) and recover L0, S0.
+"""
+import numpy as np
+import pytest
+
+from oracle import l1filter
+from paper_1108_5359_gb300 import synth
+from tests.gpuhelp import build_and_load, relerr, to_dev_cm, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _instance(seed=0):
+    M, L0, S0 = synth.lowrank_plus_sparse(600, 560, 5, 0.12, -50, 50,
+                                          seed=(seed, 77))
+    rng = np.random.default_rng(seed)
+    return M, L0, S0, rng.permutation(600), rng.permutation(560)
+
+
+def _solve(M, r, grow, row_order=None, col_order=None):
+    import torch
+    import paper_1108_5359_gb300 as pk
+    build_and_load()
+    m, n = M.shape
+    dM = to_dev_cm(M.astype(np.float32))
+    p = pk.pcp_params_default(m, n, r)
+    p.grow_seed = 1 if grow else 0
+    plan = pk.Plan(p, row_order=row_order, col_order=col_order)
+    Lu, Lv, S = pk.colmajor(m, r), pk.colmajor(n, r), pk.colmajor(m, n)
+    st, info, rows, cols = pk.pcp_l1filter_solve(plan, dM, Lu, Lv, S,
+                                                 raise_on_error=False)
+    torch.cuda.synchronize()
+    plan.close()
+    return st, info.as_dict(), rows, cols, to_host(Lu) @ to_host(Lv).T, \
+        to_host(S)
+
+
+def test_grown_solve_matches_oracle():
+    M, L0, S0, ro, co = _instance(0)
+    M32 = M.astype(np.float32).astype(np.float64)
+    _, sizes = l1filter.l1_filter_pcp_grow(M32, ro, co, r=5)
+    assert len(sizes) >= 2        # the oracle grows this seed too
+    st, info, rows, cols, L, S = _solve(M, 5, True, ro, co)
+    assert st == 0, info
+    gm, gn = info["seed_m"], info["seed_n"]
+    # the failed 50 x 50 seed is outside the recovery regime, so its rank r'
+    # (and the grown size 10 r') need not agree to the unit between the two
+    # solvers; the grown seed is a prefix of the same orders and the solve
+    # on it must agree with the oracle's on the same seed
+    assert gm > 50 and gn > 50
+    np.testing.assert_array_equal(rows, np.sort(ro[:gm]))
+    np.testing.assert_array_equal(cols, np.sort(co[:gn]))
+    ref = l1filter.l1_filter_pcp(M32, rows, cols, r=5)
+    assert ref.rank_ok and info["rank"] == ref.rank == 5
+    assert relerr(L, ref.L) < TOL
+    assert relerr(S, ref.S) < TOL
+    assert relerr(L, L0) < TOL
+
+
+def test_without_growth_the_rank_test_fails():
+    M, L0, S0, ro, co = _instance(0)
+    st, info, *_ = _solve(M, 5, False, ro, co)
+    assert st == -5 and info["seed_m"] == 50
+    assert info["seed_rank_raw"] > 5
+
+
+def test_growth_with_library_sampling():
+    M, L0, S0, _, _ = _instance(1)
+    st, info, rows, cols, L, S = _solve(M, 5, True)
+    assert st == 0, info
+    assert info["seed_m"] >= 50 and rows.size == info["seed_m"]
+    assert relerr(L, L0) < TOL and relerr(S, S0) < TOL

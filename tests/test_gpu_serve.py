@@ -130,3 +130,25 @@ def test_stop_cancels_queued_requests():
     with pytest.raises(pk.PCPError):
         srv.submit(keep[0][0])
     srv.close()
+
+
+def test_served_request_grows_its_seed():
+    # a request whose 50 x 50 seed fails Eq. rank_test goes back to the head
+    # of the queue with the grown seed (Section 3.5) and completes
+    import paper_1108_5359_gb300 as pk
+    from tests.gpuhelp import to_host
+    from tests.test_gpu_grow import _instance
+    build_and_load()
+    M, L0, S0, ro, co = _instance(0)
+    m, n = M.shape
+    dM = to_dev_cm(M.astype(np.float32))
+    Lu, Lv, S = pk.colmajor(m, 5), pk.colmajor(n, 5), pk.colmajor(m, n)
+    p = pk.pcp_params_default(m, n, 5)
+    p.grow_seed = 1
+    q = pk.problem(p, dM, Lu, Lv, S, row_order=ro, col_order=co)
+    srv = pk.Server(hbm_budget_bytes=1 << 30, max_slots=4, streams=2)
+    st, inf = srv.wait(srv.submit(q))
+    srv.close()
+    assert st == 0 and inf.seed_m > 50 and inf.rank == 5
+    L = to_host(Lu) @ to_host(Lv).T
+    assert relerr(L, L0) < TOL
