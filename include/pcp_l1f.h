@@ -58,8 +58,12 @@ typedef enum pcp_status {
 
 /* Arithmetic of Algorithm 1 (the seed PCP is FP64 in every mode). */
 typedef enum pcp_precision {
-  PCP_FP32 = 0,          /* FP32-accurate: split-TF32 tensor-core products
-                            (three passes, ~2^-21 relative) */
+  PCP_FP32 = 0,          /* FP32-accurate, kernel chosen by the library:
+                            split-TF32 tensor-core products (three passes,
+                            ~2^-21 relative), or, where both kernels take
+                            the shape (p <= 256, r <= 32), whichever of it
+                            and the SIMT FP32 kernel the first call on that
+                            shape class measured faster */
   PCP_BF16_REFINED = 1,  /* not built: PCP_ERR_UNSUPPORTED */
   PCP_TF32_REFINED = 2,  /* one-pass TF32 tensor-core products with FP32
                             accumulation for the first lowp_iters
@@ -67,7 +71,7 @@ typedef enum pcp_precision {
                             passes, ~2^-21 relative, the FP32 refinement)
                             until filter_tol */
   PCP_FP64 = 3,          /* reserved: PCP_ERR_UNSUPPORTED */
-  PCP_FP32_TENSOR = 4,   /* same as PCP_FP32 */
+  PCP_FP32_TENSOR = 4,   /* split-TF32 tensor-core products, always */
   PCP_FP32_SIMT = 5      /* FP32 FMA on the CUDA cores (p <= 256, r <= 32) */
 } pcp_precision;
 

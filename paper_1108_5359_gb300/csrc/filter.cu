@@ -25,6 +25,7 @@
 //     converged writes its z and is frozen (its lanes keep computing but
 //     never write again) so every problem stops exactly at its own test.
 #include <algorithm>
+#include <mutex>
 #include <cstring>
 #include <vector>
 
@@ -290,8 +291,26 @@ size_t args_block_bytes(int nsets) {
 
 }  // namespace
 
+// ---- kernel choice for PCP_FP32 (autotuned) --------------------------------
+// PCP_FP32 asks for FP32 accuracy without naming a kernel.  For shapes both
+// kernels take (p <= 256, r <= 32) the first pcp_l1_filter call of each
+// (p class, r class) times the two kernels on its own problems and keeps the
+// faster one for the rest of the process; the tensor-core kernel is the
+// choice until then (and for the batched form, which never tunes).
+namespace {
+std::mutex g_tune_mu;
+int g_tune[3][4] = {};  // [p <= 64/128/256][r class]: 0 untuned, 1 SIMT, 2 TC
+
+int tune_slot_p(int p) { return p <= 64 ? 0 : (p <= 128 ? 1 : 2); }
+int tune_slot_r(int r) { return (r - 1) / 8; }
+}  // namespace
+
 bool filter_uses_simt(int precision, int p, int r) {
-  return precision == PCP_FP32_SIMT && p <= 256 && r <= 32;
+  if (p > 256 || r > 32) return false;
+  if (precision == PCP_FP32_SIMT) return true;
+  if (precision != PCP_FP32) return false;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  return g_tune[tune_slot_p(p)][tune_slot_r(r)] == 1;
 }
 
 size_t filter_batch_bytes(const FilterSet* sets, int nsets) {
@@ -436,14 +455,44 @@ extern "C" pcp_status pcp_l1_filter(
   a.iters_out = d_iters;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
+  auto run_simt = [&]() {
+    if (p <= 64) return pcp::dispatch_r<8>(a, st);
+    if (p <= 128) return pcp::dispatch_r<16>(a, st);
+    return pcp::dispatch_r<32>(a, st);
+  };
+  int tuned = 0;
+  if (precision == PCP_FP32 && p <= 256 && r <= 32) {
+    std::lock_guard<std::mutex> lock(pcp::g_tune_mu);
+    tuned = pcp::g_tune[pcp::tune_slot_p(p)][pcp::tune_slot_r(r)];
+  }
+  if (precision == PCP_FP32 && p <= 256 && r <= 32 && tuned == 0) {
+    // time both kernels on these problems (each writes the full result),
+    // keep the faster, and make sure its result is the one left in Z
+    cudaEvent_t ev[3];
+    for (auto& x : ev) PCP_CUDA(cudaEventCreate(&x));
+    PCP_CUDA(cudaEventRecord(ev[0], st));
+    if ((e = run_simt()) != cudaSuccess)
+      return pcp::cuda_fail(e, "adm_f32_kernel launch", __FILE__, __LINE__);
+    PCP_CUDA(cudaEventRecord(ev[1], st));
+    if ((e = pcp::l1_filter_tc_launch(a, st)) != cudaSuccess)
+      return pcp::cuda_fail(e, "adm_tc_kernel launch", __FILE__, __LINE__);
+    PCP_CUDA(cudaEventRecord(ev[2], st));
+    PCP_CUDA(cudaEventSynchronize(ev[2]));
+    float t_simt = 0.0f, t_tc = 0.0f;
+    cudaEventElapsedTime(&t_simt, ev[0], ev[1]);
+    cudaEventElapsedTime(&t_tc, ev[1], ev[2]);
+    for (auto& x : ev) cudaEventDestroy(x);
+    const int choice = t_simt < t_tc ? 1 : 2;
+    {
+      std::lock_guard<std::mutex> lock(pcp::g_tune_mu);
+      pcp::g_tune[pcp::tune_slot_p(p)][pcp::tune_slot_r(r)] = choice;
+    }
+    if (choice == 1 && (e = run_simt()) != cudaSuccess)
+      return pcp::cuda_fail(e, "adm_f32_kernel launch", __FILE__, __LINE__);
+    return PCP_OK;
+  }
   if (pcp::filter_uses_simt(precision, p, r)) {
-    if (p <= 64)
-      e = pcp::dispatch_r<8>(a, st);
-    else if (p <= 128)
-      e = pcp::dispatch_r<16>(a, st);
-    else
-      e = pcp::dispatch_r<32>(a, st);
-    if (e != cudaSuccess)
+    if ((e = run_simt()) != cudaSuccess)
       return pcp::cuda_fail(e, "adm_f32_kernel launch", __FILE__, __LINE__);
   } else {
     e = pcp::l1_filter_tc_launch(a, st);

@@ -93,5 +93,9 @@ def test_tc_deterministic_and_matches_simt():
     np.testing.assert_array_equal(z1, z2)
     zs, _ = _run(A, X, "row", precision=5)     # PCP_FP32_SIMT
     assert relerr(A @ z1, A @ zs) < TOL
-    zd, _ = _run(A, X, "row", precision=0)     # PCP_FP32 = split TF32
-    np.testing.assert_array_equal(zd, z1)
+    # PCP_FP32 runs whichever of the two kernels measured faster on this
+    # shape class: its result is bit-identical to that kernel's
+    zd, _ = _run(A, X, "row", precision=0)
+    assert np.array_equal(zd, z1) or np.array_equal(zd, zs)
+    zd2, _ = _run(A, X, "row", precision=0)
+    np.testing.assert_array_equal(zd2, zd)
