@@ -122,7 +122,9 @@ typedef struct pcp_params {
                                (row_order / col_order or the library's own
                                sampling, not seed_rows / seed_cols) and a
                                pcp_info for the solve */
-  int32_t reserved0;
+  int32_t seed_ctas;        /* CTAs of the whole-GPU seed PCP; 0 = one per
+                               row / column of the seed up to the co-resident
+                               limit.  The result does not depend on it. */
 } pcp_params;
 
 /* Diagnostics of one solve. */

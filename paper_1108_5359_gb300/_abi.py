@@ -58,7 +58,7 @@ class PCPParams(C.Structure):
         ("row_order", C.POINTER(C.c_int64)),
         ("col_order", C.POINTER(C.c_int64)),
         ("seed_m", C.c_int32), ("seed_n", C.c_int32),
-        ("grow_seed", C.c_int32), ("reserved0", C.c_int32),
+        ("grow_seed", C.c_int32), ("seed_ctas", C.c_int32),
     ]
 
 

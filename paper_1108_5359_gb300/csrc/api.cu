@@ -44,7 +44,7 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
                           double mu_max_ratio, int max_iter, int k0, int kmax,
                           double rank_cut, int r_cap, void* d_work,
                           double* dU, double* dSigma, double* dV,
-                          cudaStream_t st, int** d_rank_out);
+                          cudaStream_t st, int** d_rank_out, int ctas);
 pcp_status seed_read_ctl(void* d_work, int mp, int np, int kmax,
                          cudaStream_t st, int* rank, int* iters,
                          double* residual, int* converged, int* error,
@@ -205,6 +205,7 @@ extern "C" pcp_status pcp_l1filter_plan(const pcp_params* params,
               q.precision == PCP_FP32_TENSOR || q.precision == PCP_FP32_SIMT,
           "pcp_l1filter_plan: precision %d not available", q.precision);
   PCP_ARG(q.lowp_iters >= 0, "pcp_l1filter_plan: lowp_iters < 0");
+  PCP_ARG(q.seed_ctas >= 0, "pcp_l1filter_plan: seed_ctas < 0");
   const int mp = q.seed_m > 0 ? q.seed_m : (int)std::llround(q.s_r * q.r);
   const int np = q.seed_n > 0 ? q.seed_n : (int)std::llround(q.s_c * q.r);
   PCP_ARG(!(q.row_order && q.seed_rows) && !(q.col_order && q.seed_cols),
@@ -479,7 +480,7 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
                           q.seed_rho, q.seed_mu_scale, q.seed_mu_max_ratio,
                           q.seed_max_iter, P->k0, P->kmax, q.rank_cut, P->r,
                           P->d_seed_work, P->d_U, P->d_Sigma, P->d_V, st,
-                          &d_rank);
+                          &d_rank, q.seed_ctas);
   if (s != PCP_OK) return s;
   // stage 5 (seed rows of the factors) + FP32 bases for the filters
   s = pcp_assemble_factors(P->d_U, P->d_Sigma, P->d_V, P->mp, P->np, P->kmax,

@@ -94,3 +94,27 @@ def test_gather_is_exact():
     torch.cuda.synchronize()
     np.testing.assert_array_equal(to_host(out),
                                   M[np.ix_(rows, cols)].astype(np.float64))
+
+
+def test_seed_result_does_not_depend_on_grid_size():
+    # the grid solver sums fixed partial-sum slots, so any CTA count gives
+    # bit-identical factors
+    import torch
+    import paper_1108_5359_gb300 as pk
+    build_and_load()
+    P = synth.make_config("c1_500_r5", seed=3)
+    dM = to_dev_cm(P.M.astype(np.float32))
+    outs = []
+    for ctas in (0, 24, 57):
+        p = pk.pcp_params_default(P.m, P.n, P.r)
+        p.seed_ctas = ctas
+        plan = pk.Plan(p, P.rows, P.cols)
+        Lu, Lv = pk.colmajor(P.m, P.r), pk.colmajor(P.n, P.r)
+        st, info, _, _ = pk.pcp_l1filter_solve(plan, dM, Lu, Lv, None)
+        torch.cuda.synchronize()
+        plan.close()
+        outs.append((Lu.cpu().numpy(), Lv.cpu().numpy(), info.seed_iters))
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o[0], outs[0][0])
+        np.testing.assert_array_equal(o[1], outs[0][1])
+        assert o[2] == outs[0][2]
