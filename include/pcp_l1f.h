@@ -405,11 +405,27 @@ pcp_status pcp_assemble_factors(const double* dU, const double* dSigma,
 
 /* Stage 6, the S pass (Algorithm 2 output): dS = dM - dLu * dLv^T over the
  * full m x n matrix, FP32, with dLu m x r (ld ldu) and dLv n x r (ld ldv).
- * dS may alias dM only if lds == ldm (in-place update). */
+ * dS may alias dM only if lds == ldm (in-place update).  Same as
+ * pcp_spass_impl(..., PCP_SPASS_AUTO, stream). */
 pcp_status pcp_spass(const float* dM, int64_t ldm, const float* dLu,
                      int64_t ldu, const float* dLv, int64_t ldv, int32_t r,
                      float* dS, int64_t lds, int64_t m, int64_t n,
                      void* stream);
+
+/* S-pass kernels.  PCP_SPASS_TENSOR: tcgen05 tensor cores (split TF32, FP32
+ * accumulation, ~2^-21 relative error per product) with TMA tiles of M and
+ * S; needs 1 <= r <= 64, m >= 128, n >= 64, dM and dS 16-byte aligned and
+ * ldm, lds multiples of 4, else PCP_ERR_UNSUPPORTED.  PCP_SPASS_SIMT: FP32
+ * FMA, any shape.  PCP_SPASS_AUTO: the tensor form where it applies. */
+enum {
+  PCP_SPASS_AUTO = 0,
+  PCP_SPASS_SIMT = 1,
+  PCP_SPASS_TENSOR = 2
+};
+pcp_status pcp_spass_impl(const float* dM, int64_t ldm, const float* dLu,
+                          int64_t ldu, const float* dLv, int64_t ldv,
+                          int32_t r, float* dS, int64_t lds, int64_t m,
+                          int64_t n, int32_t impl, void* stream);
 
 #ifdef __cplusplus
 }

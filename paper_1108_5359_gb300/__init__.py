@@ -15,7 +15,8 @@ import ctypes as C
 
 from . import _abi
 from ._abi import (PCPError, PCPInfo, PCPParams, PCPProblem,
-                   PCP_BF16_REFINED, PCP_ERR_BUSY, PCP_FP32, PCP_OK, check,
+                   PCP_BF16_REFINED, PCP_ERR_BUSY, PCP_FP32, PCP_OK,
+                   PCP_SPASS_AUTO, PCP_SPASS_SIMT, PCP_SPASS_TENSOR, check,
                    load)
 
 __all__ = [
@@ -24,7 +25,8 @@ __all__ = [
     "pcp_l1filter_solve", "pcp_plan_destroy", "pcp_gather_seed",
     "pcp_seed_workspace_bytes", "pcp_seed_pcp", "pcp_seed_pcp_static",
     "pcp_l1_filter",
-    "pcp_assemble_factors", "pcp_spass", "pcp_plan_seed_trace", "Plan",
+    "pcp_assemble_factors", "pcp_spass", "PCP_SPASS_AUTO", "PCP_SPASS_SIMT",
+    "PCP_SPASS_TENSOR", "pcp_plan_seed_trace", "Plan",
     "solve", "load", "SEED_PHASES", "PCPProblem", "problem",
     "pcp_l1filter_batch", "Server", "pcp_serve_create", "pcp_serve_submit",
     "pcp_serve_poll", "pcp_serve_wait", "pcp_serve_stop", "pcp_serve_destroy",
@@ -363,15 +365,22 @@ def pcp_assemble_factors(U, Sigma, V, d_rank, r, d_rows, d_cols, Lu, Lv, U32,
         _ptr(inv_sigma32), _stream(stream)), "pcp_assemble_factors")
 
 
-def pcp_spass(M, Lu, Lv, S, stream=None):
+def pcp_spass(M, Lu, Lv, S, stream=None, impl=None):
+    """S = M - Lu Lv^T; impl None (library choice) or PCP_SPASS_AUTO /
+    PCP_SPASS_SIMT / PCP_SPASS_TENSOR."""
     pM, ldm = _cm(M, "M")
     pLu, ldu = _cm(Lu, "Lu")
     pLv, ldv = _cm(Lv, "Lv")
     pS, lds = _cm(S, "S")
     m, n = M.shape
     r = Lu.shape[1]
-    check(load().pcp_spass(pM, ldm, pLu, ldu, pLv, ldv, r, pS, lds, m, n,
-                           _stream(stream)), "pcp_spass")
+    if impl is None:
+        check(load().pcp_spass(pM, ldm, pLu, ldu, pLv, ldv, r, pS, lds, m, n,
+                               _stream(stream)), "pcp_spass")
+    else:
+        check(load().pcp_spass_impl(pM, ldm, pLu, ldu, pLv, ldv, r, pS, lds,
+                                    m, n, int(impl), _stream(stream)),
+              "pcp_spass_impl")
 
 
 def solve(M, r, seed_rows=None, seed_cols=None, want_S=True, stream=None,

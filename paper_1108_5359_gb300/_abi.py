@@ -38,6 +38,10 @@ PCP_FP64 = 3
 PCP_FP32_TENSOR = 4
 PCP_FP32_SIMT = 5
 
+PCP_SPASS_AUTO = 0
+PCP_SPASS_SIMT = 1
+PCP_SPASS_TENSOR = 2
+
 
 class PCPParams(C.Structure):
     _fields_ = [
@@ -131,6 +135,8 @@ PROTOTYPES = {
                                     _vp, _vp]),
     "pcp_spass": (_i32, [_vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _i64,
                          _i64, _i64, _vp]),
+    "pcp_spass_impl": (_i32, [_vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp,
+                              _i64, _i64, _i64, _i32, _vp]),
 }
 
 _lib = None

@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libpcpl1f.so")
 
-SOURCES = ["api.cu", "seed.cu", "filter.cu", "filter_tc.cu", "spass.cu",
+SOURCES = ["api.cu", "seed.cu", "filter.cu", "filter_tc.cu", "spass.cu", "spass_tc.cu",
            "batch.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",

@@ -1,6 +1,7 @@
 // Host side of the C ABI: parameters, plans, the whole solve (Algorithm 2),
 // error reporting and seed sampling.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -52,6 +53,7 @@ pcp_status seed_read_ctl(void* d_work, int mp, int np, int kmax,
 pcp_status gather_seed(const float* dM, int64_t ldm, const int32_t* d_rows,
                        int32_t mp, const int32_t* d_cols, int32_t np,
                        double* dMs, int32_t* d_bad, cudaStream_t st);
+pcp_status spass_tc_read_timeouts(int* out);
 
 // splitmix64: the library's own generator for seed sampling.
 static uint64_t splitmix64(uint64_t& s) {
@@ -518,6 +520,18 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
   s = pcp::seed_read_ctl(P->d_seed_work, P->mp, P->np, P->kmax, st, &rank,
                          &iters, &resid, &conv, &err, &rank_raw);
   if (s != PCP_OK) return s;
+  if (dS) {
+    // bounded waits of the tensor-core S pass that ran out since the last
+    // check (a device-wide counter)
+    static std::atomic<int> seen{0};
+    int tmo = 0;
+    s = pcp::spass_tc_read_timeouts(&tmo);
+    if (s != PCP_OK) return s;
+    if (tmo > seen.exchange(tmo)) {
+      pcp::set_error("S pass: a device wait timed out");
+      return PCP_ERR_TIMEOUT;
+    }
+  }
   std::vector<int32_t> it(ncb + nrb);
   int32_t bad = 0;
   PCP_CUDA(cudaMemcpy(it.data(), P->d_iters, sizeof(int32_t) * it.size(),

@@ -143,4 +143,14 @@ struct AssembleTask {
 pcp_status assemble_batched_async(const AssembleTask* tasks, int count,
                                   void* h_buf, void* d_buf, cudaStream_t st);
 
+// Tensor-core S pass (tcgen05 + TMA): applicability, launch, and the device
+// count of bounded waits that ran out.
+bool spass_tc_fits(const float* dM, int64_t ldm, float* dS, int64_t lds,
+                   int r, int64_t m, int64_t n);
+pcp_status spass_tc_launch(const float* dM, int64_t ldm, const float* dLu,
+                           int64_t ldu, const float* dLv, int64_t ldv, int r,
+                           float* dS, int64_t lds, int64_t m, int64_t n,
+                           cudaStream_t st);
+pcp_status spass_tc_read_timeouts(int* out);
+
 }  // namespace pcp

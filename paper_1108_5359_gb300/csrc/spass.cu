@@ -293,13 +293,37 @@ extern "C" pcp_status pcp_spass(const float* dM, int64_t ldm, const float* dLu,
                                 int64_t ldu, const float* dLv, int64_t ldv,
                                 int32_t r, float* dS, int64_t lds, int64_t m,
                                 int64_t n, void* stream) {
+  return pcp_spass_impl(dM, ldm, dLu, ldu, dLv, ldv, r, dS, lds, m, n,
+                        PCP_SPASS_AUTO, stream);
+}
+
+extern "C" pcp_status pcp_spass_impl(const float* dM, int64_t ldm,
+                                     const float* dLu, int64_t ldu,
+                                     const float* dLv, int64_t ldv, int32_t r,
+                                     float* dS, int64_t lds, int64_t m,
+                                     int64_t n, int32_t impl, void* stream) {
   PCP_ARG(m >= 0 && n >= 0, "pcp_spass: negative size");
   PCP_ARG(r >= 0 && r <= pcp::kSpassMaxR, "pcp_spass: r=%d outside [0, %d]",
           r, pcp::kSpassMaxR);
+  PCP_ARG(impl == PCP_SPASS_AUTO || impl == PCP_SPASS_SIMT ||
+              impl == PCP_SPASS_TENSOR,
+          "pcp_spass: unknown kernel choice %d", impl);
   if (m == 0 || n == 0) return PCP_OK;
   PCP_ARG(ldm >= m && lds >= m && ldu >= m && ldv >= n,
           "pcp_spass: leading dimension too small");
   PCP_ARG(dM && dS && (r == 0 || (dLu && dLv)), "pcp_spass: null pointer");
+  if (impl != PCP_SPASS_SIMT) {
+    if (pcp::spass_tc_fits(dM, ldm, dS, lds, r, m, n))
+      return pcp::spass_tc_launch(dM, ldm, dLu, ldu, dLv, ldv, r, dS, lds, m,
+                                  n, (cudaStream_t)stream);
+    if (impl == PCP_SPASS_TENSOR) {
+      pcp::set_error(
+          "pcp_spass: tensor-core form needs 1 <= r <= 64, m >= 128, n >= 64 "
+          "and 16-byte aligned M / S columns (r=%d m=%lld n=%lld)",
+          r, (long long)m, (long long)n);
+      return PCP_ERR_UNSUPPORTED;
+    }
+  }
   const int vec_ok = ((((uintptr_t)dM) | ((uintptr_t)dS)) % 16 == 0) &&
                      (ldm % 4 == 0) && (lds % 4 == 0);
   pcp::SpassArgs a;
