@@ -46,6 +46,18 @@ WORKLOAD_DESC = ("m=n=5000, r=20, L0=XY^T with X,Y iid N(0,1); S0 10% uniform "
                  "support, values U[-100,100]; seed 200x200 (10r x 10r); "
                  "lambda=1/sqrt(5000); FP32 M")
 FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch from one ncu capture of the same
+# kernel code on the same workload (profiles/ holds the summaries and the
+# commands); a kernel changed since its capture gets no entry.
+TRAFFIC = {
+    ("c2_5000_r20", "seed"): (
+        895488, "profiles/seed_alm_kernel_c2_5000_r20.md"),
+    ("c2_5000_r20", "spass"): (
+        158809600, "profiles/spass_tc_kernel_c2_5000_r20.md"),
+    ("c3_20000_r50", "spass"): (
+        2895202000, "profiles/spass_tc_kernel_c2_5000_r20.md: 8000^2 capture "
+        "(463.2 MB) scaled by the entry count (x 6.25)"),
+}
 PRECISIONS = {"fp32": 0, "tf32": 2, "fp32simt": 5}
 
 
@@ -182,8 +194,10 @@ def workload_name(args):
         return "c1_500_r5", "m=n=500, r=5, 5% support U[-50,50], seed 50x50"
     if args.workload == "large":
         if args.size:
+            gb = 4.0 * args.size * args.size / 1e9
             return (f"{LARGE}_at_{args.size}",
-                    LARGE_DESC.replace("m=n=20000", f"m=n={args.size}"))
+                    LARGE_DESC.replace("m=n=20000", f"m=n={args.size}")
+                    .replace("(1.6 GB)", f"({gb:.2g} GB)"))
         return LARGE, LARGE_DESC
     return WORKLOAD, WORKLOAD_DESC
 
@@ -446,14 +460,21 @@ def run_ours(args):
         v["frac"] = v["achieved"] / v["peak"]
     dom = max(stages, key=lambda k: stages[k]["ms"])
     d = stages[dom]
-    roofline = {"kernel": {"spass": "spass_kernel",
-                           "filter": ("adm_f32_kernel"
-                                      if args.precision == "fp32simt"
-                                      else "adm_tc_kernel"),
-                           "seed": "seed_alm_kernel"}[dom],
+    wl_name = workload_name(args)[0]
+    kernel = {"spass": "spass_tc_kernel",
+              "filter": ("adm_f32_kernel" if args.precision == "fp32simt"
+                         else "adm_tc_kernel"),
+              "seed": "seed_alm_kernel"}
+    for k, v in stages.items():
+        v["kernel"] = kernel[k]
+        t = TRAFFIC.get((wl_name, k))
+        v["traffic"] = t[0] if t else None
+        if t:
+            v["traffic_source"] = t[1]
+    roofline = {"kernel": kernel[dom],
                 "bound": d["bound"], "achieved": d["achieved"],
                 "peak": d["peak"], "unit": d["unit"], "frac": d["frac"],
-                "traffic": None,
+                "traffic": d["traffic"],
                 "peak_source": (pk_src + " hbm_gbs" if d["bound"] == "hbm"
                                 else (pk_src + " bf16_tflops x 1.1/2.25"
                                       if d["bound"] == "tensor" else
