@@ -58,7 +58,7 @@ TRAFFIC = {
         2895202000, "profiles/spass_tc_kernel_c2_5000_r20.md: 8000^2 capture "
         "(463.2 MB) scaled by the entry count (x 6.25)"),
 }
-PRECISIONS = {"fp32": 0, "tf32": 2, "fp32simt": 5}
+PRECISIONS = {"fp32": 0, "bf16": 1, "tf32": 2, "fp32simt": 5}
 
 
 def parse():
@@ -87,11 +87,14 @@ def parse():
                     help="instances (batch) / requests (serve)")
     ap.add_argument("--rate", type=float, default=50.0,
                     help="serve: arrival rate, requests/s")
-    ap.add_argument("--precision", choices=["fp32", "tf32", "fp32simt"],
+    ap.add_argument("--precision",
+                    choices=["fp32", "bf16", "tf32", "fp32simt"],
                     default="fp32",
-                    help="Algorithm 1 arithmetic: fp32 (split-TF32 tensor "
-                         "cores, FP32-accurate), tf32 (one-pass TF32 then "
-                         "split-TF32 refinement), fp32simt (FP32 FMA)")
+                    help="Algorithm 1 arithmetic: fp32 (autotuned between "
+                         "split-TF32 tensor cores and FP32 FMA, "
+                         "FP32-accurate), bf16 / tf32 (one-pass BF16 / TF32 "
+                         "tensor-core iterations then split-TF32 "
+                         "refinement), fp32simt (FP32 FMA)")
     ap.add_argument("--r-max", type=int, default=25,
                     help="batch: largest rank drawn (seed 10r <= 256)")
     return ap.parse_args()
@@ -503,8 +506,8 @@ def run_ours(args):
             "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup),
             "ms_per_step": t_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32 (split tf32)", "tf32": "tf32+f32",
-                      "fp32simt": "f32"}[args.precision],
+            "dtype": {"fp32": "f32", "bf16": "bf16+f32",
+                      "tf32": "tf32+f32", "fp32simt": "f32"}[args.precision],
             "data": "synthetic",
             "config": {"workload": workload_name(args)[0],
                        "desc": workload_name(args)[1], "global_batch": ws,

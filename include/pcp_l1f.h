@@ -64,7 +64,10 @@ typedef enum pcp_precision {
                             the shape (p <= 256, r <= 32), whichever of it
                             and the SIMT FP32 kernel the first call on that
                             shape class measured faster */
-  PCP_BF16_REFINED = 1,  /* not built: PCP_ERR_UNSUPPORTED */
+  PCP_BF16_REFINED = 1,  /* one-pass BF16 tensor-core products (inputs
+                            rounded to BF16, FP32 accumulation) for the
+                            first lowp_iters iterations, then split-TF32
+                            products until filter_tol, as below */
   PCP_TF32_REFINED = 2,  /* one-pass TF32 tensor-core products with FP32
                             accumulation for the first lowp_iters
                             iterations, then split-TF32 products (three

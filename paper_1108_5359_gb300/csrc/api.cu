@@ -204,6 +204,7 @@ extern "C" pcp_status pcp_l1filter_plan(const pcp_params* params,
           q.r);
   PCP_ARG(q.s_r > 0 && q.s_c > 0, "pcp_l1filter_plan: oversampling <= 0");
   PCP_ARG(q.precision == PCP_FP32 || q.precision == PCP_TF32_REFINED ||
+              q.precision == PCP_BF16_REFINED ||
               q.precision == PCP_FP32_TENSOR || q.precision == PCP_FP32_SIMT,
           "pcp_l1filter_plan: precision %d not available", q.precision);
   PCP_ARG(q.lowp_iters >= 0, "pcp_l1filter_plan: lowp_iters < 0");

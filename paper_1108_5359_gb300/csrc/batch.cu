@@ -128,6 +128,7 @@ pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi) {
           "batch: m=%lld n=%lld out of range", (long long)q.m, (long long)q.n);
   PCP_ARG(q.r >= 1 && q.r <= 64, "batch: r=%d outside [1, 64]", q.r);
   PCP_ARG(q.precision == PCP_FP32 || q.precision == PCP_TF32_REFINED ||
+              q.precision == PCP_BF16_REFINED ||
               q.precision == PCP_FP32_TENSOR || q.precision == PCP_FP32_SIMT,
           "batch: precision %d not available", q.precision);
   PCP_ARG(q.lowp_iters >= 0, "batch: lowp_iters < 0");

@@ -351,7 +351,10 @@ pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
     a.beta0_scale = (float)f.beta0_scale;
     a.beta_bar_ratio = (float)f.beta_bar_ratio;
     a.max_iter = f.max_iter;
-    a.lowp_iters = f.precision == PCP_TF32_REFINED ? f.lowp_iters : 0;
+    const bool refined = f.precision == PCP_TF32_REFINED ||
+                         f.precision == PCP_BF16_REFINED;
+    a.lowp_iters = refined ? f.lowp_iters : 0;
+    a.lowp_bf16 = f.precision == PCP_BF16_REFINED;
     a.iters_out = f.iters_out;
     std::memcpy(ha + i, &a, sizeof(a));
     const int cls = simt ? shape_class(f.p, f.r)
@@ -425,7 +428,7 @@ extern "C" pcp_status pcp_l1_filter(
   PCP_ARG(precision != PCP_FP32_SIMT || (p <= 256 && r <= 32),
           "pcp_l1_filter: the SIMT form takes p <= 256 and r <= 32 "
           "(p=%d r=%d)", p, r);
-  if (precision == PCP_BF16_REFINED || precision == PCP_FP64) {
+  if (precision == PCP_FP64) {
     pcp::set_error("pcp_l1_filter: precision %d not built", precision);
     return PCP_ERR_UNSUPPORTED;
   }
@@ -451,7 +454,10 @@ extern "C" pcp_status pcp_l1_filter(
   a.beta0_scale = (float)beta0_scale;
   a.beta_bar_ratio = (float)beta_bar_ratio;
   a.max_iter = max_iter;
-  a.lowp_iters = precision == PCP_TF32_REFINED ? lowp_iters : 0;
+  const bool refined =
+      precision == PCP_TF32_REFINED || precision == PCP_BF16_REFINED;
+  a.lowp_iters = refined ? lowp_iters : 0;
+  a.lowp_bf16 = precision == PCP_BF16_REFINED;
   a.iters_out = d_iters;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;

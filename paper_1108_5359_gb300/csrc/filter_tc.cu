@@ -19,11 +19,14 @@
 // 8 warps (each owns a slab of entries) through shared memory in a fixed
 // order and read back with the same permutation on the r index.
 //
-// Precision: one-pass TF32 products (10-bit mantissa) for the first
-// lowp_iters iterations, then split products (a = hi + lo, three passes:
-// lo*hi + hi*lo + hi*hi, ~2^-21 relative) until the stop test, which is
-// only taken on split-product iterations.  lowp_iters = 0 gives the
-// FP32-accurate form throughout.
+// Precision: one-pass low-precision products for the first lowp_iters
+// iterations (TF32, 10-bit mantissa, or BF16, 7-bit mantissa, as
+// mma.sync m16n8k8 bf16 whose A fragment holds the two entries 2t, 2t+1 of
+// a row in one register: the same values as the TF32 fragment's slots t and
+// t+4), then split products (a = hi + lo, three passes: lo*hi + hi*lo +
+// hi*hi, ~2^-21 relative) until the stop test, which is only taken on
+// split-product iterations.  lowp_iters = 0 gives the FP32-accurate form
+// throughout.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -61,15 +64,38 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t a0,
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// d += a * b with a, b given as FP32 values: one TF32 pass into d, or the
-// three passes of the split operands, hi*hi into d and the two cross terms
-// into dl (a second accumulator, so the dependent chains are half as long;
-// the caller adds dl into d at the end).
-template <bool kSplit>
+// two FP32 values rounded to BF16 in one register, lo in the low half
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t a01,
+                                         const uint32_t a23,
+                                         const uint32_t b01) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a01), "r"(a23), "r"(b01));
+}
+
+// Product modes: one-pass TF32, split TF32 (FP32-accurate), one-pass BF16.
+enum { kOneTf32 = 0, kSplitTf32 = 1, kOneBf16 = 2 };
+
+// d += a * b with a, b given as FP32 values (a in the TF32 fragment's slot
+// order): one low-precision pass into d, or the three passes of the split
+// operands, hi*hi into d and the two cross terms into dl (a second
+// accumulator, so the dependent chains are half as long; the caller adds
+// dl into d at the end).
+template <int kMode>
 __device__ __forceinline__ void mma_f32(float (&d)[4], float (&dl)[4],
                                         const float (&a)[4], const float b0,
                                         const float b1) {
-  if (kSplit) {
+  if (kMode == kOneBf16) {
+    mma_bf16(d, pack_bf16(a[0], a[2]), pack_bf16(a[1], a[3]),
+             pack_bf16(b0, b1));
+  } else if (kMode == kSplitTf32) {
     uint32_t ah[4], al[4], bh0, bl0, bh1, bl1;
 #pragma unroll
     for (int q = 0; q < 4; ++q) split_tf32(a[q], ah[q], al[q]);
@@ -90,11 +116,16 @@ struct TcFrag {
   uint32_t h[4], l[4];
 };
 
-template <bool kSplit>
+template <int kMode>
 __device__ __forceinline__ void tc_prep(TcFrag& f, const float (&a)[4]) {
+  if (kMode == kOneBf16) {
+    f.h[0] = pack_bf16(a[0], a[2]);
+    f.h[1] = pack_bf16(a[1], a[3]);
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    if (kSplit)
+    if (kMode == kSplitTf32)
       split_tf32(a[q], f.h[q], f.l[q]);
     else
       f.h[q] = tf32_rna(a[q]);
@@ -102,11 +133,13 @@ __device__ __forceinline__ void tc_prep(TcFrag& f, const float (&a)[4]) {
 }
 
 // d (+ dl) += a * b for a prepared fragment a.
-template <bool kSplit>
+template <int kMode>
 __device__ __forceinline__ void mma_pre(float (&d)[4], float (&dl)[4],
                                         const TcFrag& a, const float b0,
                                         const float b1) {
-  if (kSplit) {
+  if (kMode == kOneBf16) {
+    mma_bf16(d, a.h[0], a.h[1], pack_bf16(b0, b1));
+  } else if (kMode == kSplitTf32) {
     uint32_t bh0, bl0, bh1, bl1;
     split_tf32(b0, bh0, bl0);
     split_tf32(b1, bh1, bl1);
@@ -143,7 +176,7 @@ constexpr size_t tc_smem_bytes() {
 }
 
 // One CTA: 16 problems (tile) of one set, 8 warps x NT tiles of 8 entries.
-template <int RB, int NT>
+template <int RB, int NT, bool kBf16>
 __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
                                             const int tile) {
   constexpr int RP = tc_pitch<RB>();
@@ -261,10 +294,12 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
       for (int rb = 0; rb < RB; ++rb) {
         const float b0 = As[(n0 + 2 * t) * RP + rb * 8 + g];
         const float b1 = As[(n0 + 2 * t + 1) * RP + rb * 8 + g];
-        if (a.lowp_iters > 0)
-          mma_f32<false>(zacc[rb], zlo[rb], af, b0, b1);
+        if (a.lowp_iters == 0)
+          mma_f32<kSplitTf32>(zacc[rb], zlo[rb], af, b0, b1);
+        else if (kBf16)
+          mma_f32<kOneBf16>(zacc[rb], zlo[rb], af, b0, b1);
         else
-          mma_f32<true>(zacc[rb], zlo[rb], af, b0, b1);
+          mma_f32<kOneTf32>(zacc[rb], zlo[rb], af, b0, b1);
       }
     }
   }
@@ -354,6 +389,7 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
 
     // ---- one pass: A z_it, residual, dual step, next shrinkage, A^T u ----
     const bool split = it > a.lowp_iters;
+    const bool bf16 = !split && kBf16;
     float zf[RB][4];
     {
       const float* zc = zs + cur * kTcProblems * RP;
@@ -385,9 +421,11 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
 #pragma unroll
       for (int kb = 0; kb < RB; ++kb) {
         if (split)
-          tc_prep<true>(zpre[kPreZ ? kb : 0], zf[kb]);
+          tc_prep<kSplitTf32>(zpre[kPreZ ? kb : 0], zf[kb]);
+        else if (bf16)
+          tc_prep<kOneBf16>(zpre[kPreZ ? kb : 0], zf[kb]);
         else
-          tc_prep<false>(zpre[kPreZ ? kb : 0], zf[kb]);
+          tc_prep<kOneTf32>(zpre[kPreZ ? kb : 0], zf[kb]);
       }
     }
 #pragma unroll
@@ -401,14 +439,18 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
             As + (n0 + g) * RP + kb * 8 + 2 * t);
         if (kPreZ) {
           if (split)
-            mma_pre<true>(wz, wl, zpre[kPreZ ? kb : 0], bb.x, bb.y);
+            mma_pre<kSplitTf32>(wz, wl, zpre[kPreZ ? kb : 0], bb.x, bb.y);
+          else if (bf16)
+            mma_pre<kOneBf16>(wz, wl, zpre[kPreZ ? kb : 0], bb.x, bb.y);
           else
-            mma_pre<false>(wz, wl, zpre[kPreZ ? kb : 0], bb.x, bb.y);
+            mma_pre<kOneTf32>(wz, wl, zpre[kPreZ ? kb : 0], bb.x, bb.y);
         } else {
           if (split)
-            mma_f32<true>(wz, wl, zf[kb], bb.x, bb.y);
+            mma_f32<kSplitTf32>(wz, wl, zf[kb], bb.x, bb.y);
+          else if (bf16)
+            mma_f32<kOneBf16>(wz, wl, zf[kb], bb.x, bb.y);
           else
-            mma_f32<false>(wz, wl, zf[kb], bb.x, bb.y);
+            mma_f32<kOneTf32>(wz, wl, zf[kb], bb.x, bb.y);
         }
       }
 #pragma unroll
@@ -433,17 +475,21 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
         // widest shape splitting per product schedules better)
         TcFrag uf;
         if (split)
-          tc_prep<true>(uf, af);
+          tc_prep<kSplitTf32>(uf, af);
+        else if (bf16)
+          tc_prep<kOneBf16>(uf, af);
         else
-          tc_prep<false>(uf, af);
+          tc_prep<kOneTf32>(uf, af);
 #pragma unroll
         for (int rb = 0; rb < RB; ++rb) {
           const float b0 = As[(n0 + 2 * t) * RP + rb * 8 + g];
           const float b1 = As[(n0 + 2 * t + 1) * RP + rb * 8 + g];
           if (split)
-            mma_pre<true>(zacc[rb], zlo[rb], uf, b0, b1);
+            mma_pre<kSplitTf32>(zacc[rb], zlo[rb], uf, b0, b1);
+          else if (bf16)
+            mma_pre<kOneBf16>(zacc[rb], zlo[rb], uf, b0, b1);
           else
-            mma_pre<false>(zacc[rb], zlo[rb], uf, b0, b1);
+            mma_pre<kOneTf32>(zacc[rb], zlo[rb], uf, b0, b1);
         }
       } else {
 #pragma unroll
@@ -451,9 +497,11 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
           const float b0 = As[(n0 + 2 * t) * RP + rb * 8 + g];
           const float b1 = As[(n0 + 2 * t + 1) * RP + rb * 8 + g];
           if (split)
-            mma_f32<true>(zacc[rb], zlo[rb], af, b0, b1);
+            mma_f32<kSplitTf32>(zacc[rb], zlo[rb], af, b0, b1);
+          else if (bf16)
+            mma_f32<kOneBf16>(zacc[rb], zlo[rb], af, b0, b1);
           else
-            mma_f32<false>(zacc[rb], zlo[rb], af, b0, b1);
+            mma_f32<kOneTf32>(zacc[rb], zlo[rb], af, b0, b1);
         }
       }
     }
@@ -479,7 +527,12 @@ constexpr int tc_min_blocks() {
 template <int RB, int NT>
 __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<RB, NT>())
     adm_tc_kernel(const FilterArgs a) {
-  adm_tc_tile<RB, NT>(a, blockIdx.x);
+  // the BF16 low-precision passes get their own copy of the tile code (one
+  // more product mode in the same code raised register pressure into spills)
+  if (a.lowp_bf16)
+    adm_tc_tile<RB, NT, true>(a, blockIdx.x);
+  else
+    adm_tc_tile<RB, NT, false>(a, blockIdx.x);
 }
 
 template <int RB, int NT>
@@ -487,7 +540,10 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<RB, NT>())
     adm_tc_batched_kernel(const FilterArgs* __restrict__ sets,
                           const int32_t* __restrict__ tiles) {
   const FilterArgs a = sets[tiles[2 * blockIdx.x]];
-  adm_tc_tile<RB, NT>(a, tiles[2 * blockIdx.x + 1]);
+  if (a.lowp_bf16)
+    adm_tc_tile<RB, NT, true>(a, tiles[2 * blockIdx.x + 1]);
+  else
+    adm_tc_tile<RB, NT, false>(a, tiles[2 * blockIdx.x + 1]);
 }
 
 template <int RB, int NT>

@@ -71,6 +71,7 @@ struct FilterArgs {
   float eps, rho, beta0_scale, beta_bar_ratio;
   int max_iter;
   int lowp_iters;
+  int lowp_bf16;  // the low-precision passes use BF16 (else one-pass TF32)
   int32_t* iters_out;
 };
 

@@ -1,9 +1,10 @@
 """GPU parity of the tensor-core form of Algorithm 1 against the FP64 oracle.
 
-The two products of every ADM iteration run as TF32 mma.sync with FP32
+The two products of every ADM iteration run as mma.sync with FP32
 accumulation: split (three-pass) TF32 throughout for PCP_FP32_TENSOR, and
-one-pass TF32 for the first lowp_iters iterations followed by split TF32
-(the FP32 refinement) for PCP_TF32_REFINED.  Both must give A z within
+one-pass TF32 (PCP_TF32_REFINED) or one-pass BF16 (PCP_BF16_REFINED) for the
+first lowp_iters iterations followed by split TF32 (the FP32 refinement).
+All must give A z within
 relative Frobenius error 1e-5 of the oracle (eps = 1e-10), for column and
 row problems, ragged problem counts (not a multiple of the 16 problems per
 CTA), lengths that are not a multiple of 8, and the large shapes the SIMT
@@ -19,8 +20,8 @@ from tests.test_gpu_filter import _problem, _run
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-PCP_TF32_REFINED, PCP_FP32_TENSOR = 2, 4
-PRECISIONS = [PCP_FP32_TENSOR, PCP_TF32_REFINED]
+PCP_BF16_REFINED, PCP_TF32_REFINED, PCP_FP32_TENSOR = 1, 2, 4
+PRECISIONS = [PCP_FP32_TENSOR, PCP_TF32_REFINED, PCP_BF16_REFINED]
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
@@ -60,7 +61,8 @@ def test_tc_zero_and_clean_columns(precision):
     # met on the first split-product iteration or the one after
     # (after one-pass TF32 iterations, whose rounding leaves small nonzero
     # e entries, the refinement takes a few iterations more)
-    first, extra = (1, 2) if precision == PCP_FP32_TENSOR else (5, 4)
+    first, extra = {PCP_FP32_TENSOR: (1, 2), PCP_TF32_REFINED: (5, 4),
+                    PCP_BF16_REFINED: (5, 8)}[precision]
     assert (it[mask] >= first).all() and (it[mask] <= first + extra).all()
     assert relerr(Zg[:, mask], A.T @ X[:, mask]) < 1e-6
 

@@ -6,7 +6,7 @@ seed PCP at m' = n' = 500 with a 64-wide subspace, and Algorithm 1 on the
 tensor cores (p = 500 > 256, r = 50 > 32).  Checked:
   * a 3000 x 3000 instance of the same distribution against the full FP64
     oracle (relative Frobenius error 1e-5 on L and S) and against L0, S0,
-    for PCP_FP32 and PCP_TF32_REFINED;
+    for PCP_FP32, PCP_TF32_REFINED and PCP_BF16_REFINED;
   * the full 20000 x 20000 size on a sampled 96 x 96 block of L and S, which
     the oracle computes from its own seed PCP and Algorithm 1 on just those
     rows and columns (L = Lu Lv^T is unique; the factors are not).
@@ -22,7 +22,7 @@ from tests.test_gpu_solve import _check, _gpu_solve
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-PCP_FP32, PCP_TF32_REFINED = 0, 2
+PCP_FP32, PCP_BF16_REFINED, PCP_TF32_REFINED = 0, 1, 2
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +33,8 @@ def mid():
     return P, ref
 
 
-@pytest.mark.parametrize("precision", [PCP_FP32, PCP_TF32_REFINED])
+@pytest.mark.parametrize("precision", [PCP_FP32, PCP_TF32_REFINED,
+                                       PCP_BF16_REFINED])
 def test_rank50_seed500_matches_oracle(mid, precision):
     P, ref = mid
     g = _gpu_solve(P, precision=precision)
