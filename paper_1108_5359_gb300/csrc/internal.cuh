@@ -8,8 +8,8 @@ namespace pcp {
 // Control block of one seed PCP solve (device memory, start of its
 // workspace): barrier state, status and diagnostics.
 struct SeedCtl {
-  unsigned int bar_count;
-  unsigned int bar_gen;
+  unsigned int bar_count;  // grid barrier arrivals since the launch
+  unsigned int pad0;
   int error;
   int iters;
   int rank;

@@ -129,31 +129,38 @@ __device__ __forceinline__ double ldg_cg(const double* p) { return __ldcg(p); }
 // Software grid barrier (sense by generation), bounded by a timeout.
 __device__ bool grid_sync(SeedCtl* ctl, unsigned int nblocks,
                           unsigned long long timeout_ns) {
+  // Counter barrier on a monotonically increasing arrival count (the control
+  // block is zeroed per launch): barrier g completes when the count reaches
+  // (g + 1) * nblocks.  bar.sync orders the CTA's writes before thread 0's
+  // release-add, and thread 0's acquire-load before the CTA's later reads,
+  // so only one thread per CTA synchronises at GPU scope (no per-thread
+  // fences).
   __shared__ int s_ok;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* genp = &ctl->bar_gen;
-    const unsigned int gen = *genp;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&ctl->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&ctl->bar_gen, 1u);
-    } else {
-      const unsigned long long t0 = globaltimer_ns();
-      unsigned int spins = 0;
-      while (*genp == gen) {
-        if (*(volatile int*)&ctl->error) break;
-        if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
-          atomicExch(&ctl->error, (int)PCP_ERR_TIMEOUT);
-          break;
-        }
-        __nanosleep(32);
+    unsigned int* cnt = &ctl->bar_count;
+    unsigned int arrived;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;"
+                 : "=r"(arrived)
+                 : "l"(cnt)
+                 : "memory");
+    const unsigned int target = (arrived / nblocks + 1) * nblocks;
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned int spins = 0;
+    while (true) {
+      unsigned int cur;
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];"
+                   : "=r"(cur)
+                   : "l"(cnt)
+                   : "memory");
+      if ((int)(cur - target) >= 0) break;
+      if (*(volatile int*)&ctl->error) break;
+      if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
+        atomicExch(&ctl->error, (int)PCP_ERR_TIMEOUT);
+        break;
       }
+      __nanosleep(32);
     }
-    __threadfence();
     s_ok = (*(volatile int*)&ctl->error) == 0;
   }
   __syncthreads();
