@@ -51,7 +51,12 @@ constexpr int kSeedKmaxLimit = 64;
 constexpr int kSeedTraceCap = 4096;  // (timestamp, phase) records
 constexpr int kSeedTeamMax = 64;     // largest team of the batched solver
 constexpr int kSeedMaxSide = 512;    // largest m', n'
-constexpr int kSeedGridSlots = 512;  // partial-sum slots of the grid solver
+// Partial-sum slots of the grid solver: fixed, so a solve's result does not
+// depend on its CTA count; one per SM of this part (a sweep on the 200 x 200
+// seed: 3.34 ms with 512 slots, 3.05 ms with 152, 3.15 ms with 76; on the
+// 500 x 500 seed 11.19 / 10.63 / 11.80 ms; every slot costs each CTA a
+// k-vector read in the Ritz-value reduction).
+constexpr int kSeedGridSlots = 152;
 
 struct SeedLayout {
   size_t ctl, part, colsq, S, Y, G, Gt, Om, P, Pt, T, Psi, PsiT, Gam, Gam2,
