@@ -751,12 +751,16 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
       // the SVT threshold (tau^2 / cmax in these units) are left unmixed:
       // both are shrunk to zero, so a rotation between them changes neither
       // L nor the spanned subspace.
-      bool fast = false;
+      bool fast = false, cluster = false;
       if (stage == 3) {
         const float t2 = (float)((1.0 / mu) * (1.0 / mu) * (double)inv);
         // far from convergence a coarser rotation is enough (the FP64
         // refinement of the last iterations removes what it leaves)
         const float gate = res < 1e-5 ? 1e-3f : 1e-2f;
+        int* vio = prs;   // per index: in a pair that fails the gate
+        int* sub = dead;  // those indices, in order (both free here)
+        for (int c = tid; c < k; c += kSeedThreads) vio[c] = 0;
+        __syncthreads();
         int bad = 0;
         for (int idx = tid; idx < k * k; idx += kSeedThreads) {
           const int p = idx / k, q = idx - p * k;
@@ -764,25 +768,75 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
             const float cpp = C32[p * k + p], cqq = C32[q * k + q];
             const float cpq = C32[p * k + q];
             const bool exempt = cpp <= t2 && cqq <= t2;
-            if (!exempt && !(fabsf(cpq) <= gate * fabsf(cqq - cpp))) bad = 1;
+            if (!exempt && !(fabsf(cpq) <= gate * fabsf(cqq - cpp))) {
+              bad = 1;
+              vio[p] = 1;
+              vio[q] = 1;
+            }
           }
         }
         fast = !__syncthreads_or(bad);
-        if (fast) {
+        // Failing pairs usually lie within one cluster of nearly equal
+        // values (the directions around the SVT threshold); every pair
+        // with an index outside it passes the gate.  Then the first-order
+        // eigenvectors serve for all pairs but those inside the cluster,
+        // whose sub-block is rotated exactly by its own (small) Jacobi.
+        __shared__ int s_nsub;
+        if (!fast) {
+          if (tid == 0) {
+            int ns = 0;
+            for (int c = 0; c < k; ++c)
+              if (vio[c]) sub[ns++] = c;
+            s_nsub = ns;
+          }
+          __syncthreads();
+          const int ns = s_nsub, nsp = (ns + 1) & ~1;
+          cluster = ns <= 24 && 2 * ns <= k && 3 * nsp * nsp <= kmax * kmax;
+        }
+        if (fast || cluster) {
           for (int idx = tid; idx < k * k; idx += kSeedThreads) {
             const int p = idx / k, q = idx - p * k;
             float x = (p == q) ? 1.0f : 0.0f;
-            if (p != q) {
+            if (p != q && !(vio[p] && vio[q])) {
               const float cpp = C32[p * k + p], cqq = C32[q * k + q];
               if (!(cpp <= t2 && cqq <= t2))
                 x = __fdividef(C32[p * k + q], cqq - cpp);
             }
             W0[idx] = x;  // V[p][q]
           }
-          __syncthreads();
         }
+        if (cluster) {
+          const int ns = s_nsub, nsp = (ns + 1) & ~1;
+          float* As0 = cs;
+          float* As1 = cs + nsp * nsp;
+          float* Vs = cs + 2 * nsp * nsp;
+          for (int idx = tid; idx < nsp * nsp; idx += kSeedThreads) {
+            const int i = idx / nsp, j = idx - i * nsp;
+            As0[idx] = (i < ns && j < ns) ? C32[sub[i] * k + sub[j]] : 0.0f;
+          }
+          __syncthreads();
+          block_jacobi32(As0, As1, Vs, nsp,
+                         reinterpret_cast<unsigned char*>(prs + kmax),
+                         max_sweeps, kGrid ? &ctl->jsweeps : nullptr,
+                         kGrid ? ctl->jcyc : nullptr);
+          // cluster columns of V: V[:, sub_j] = sum_i V[:, sub_i] Vs[i][j]
+          // (through C32's storage, which is no longer needed)
+          for (int idx = tid; idx < k * ns; idx += kSeedThreads) {
+            const int r = idx / ns, j = idx - r * ns;
+            float acc = 0.0f;
+            for (int i = 0; i < ns; ++i)
+              acc = fmaf(W0[r * k + sub[i]], Vs[i * nsp + j], acc);
+            C32[idx] = acc;
+          }
+          __syncthreads();
+          for (int idx = tid; idx < k * ns; idx += kSeedThreads) {
+            const int r = idx / ns, j = idx - r * ns;
+            W0[r * k + sub[j]] = C32[idx];
+          }
+        }
+        __syncthreads();
       }
-      if (!fast) {
+      if (!fast && !cluster) {
         float* Afin = block_jacobi32(
             C32, cs, W0, k, reinterpret_cast<unsigned char*>(prs + kmax),
             max_sweeps, kGrid ? &ctl->jsweeps : nullptr,
