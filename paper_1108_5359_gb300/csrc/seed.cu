@@ -51,6 +51,7 @@ constexpr int kSeedKmaxLimit = 64;
 constexpr int kSeedTraceCap = 4096;  // (timestamp, phase) records
 constexpr int kSeedTeamMax = 64;     // largest team of the batched solver
 constexpr int kSeedMaxSide = 512;    // largest m', n'
+constexpr int kSeedGemmGroup = 4;    // tasks per pass of the tall products
 // Partial-sum slots of the grid solver: fixed, so a solve's result does not
 // depend on its CTA count; one per SM of this part (a sweep on the 200 x 200
 // seed: 3.34 ms with 512 slots, 3.05 ms with 152, 3.15 ms with 76; on the
@@ -232,44 +233,84 @@ __device__ double sum_partials(const double* src, int nb, int stride, int off,
 }
 
 // out[task*kmax + c] = sum_t X[t + task*ldx] * B[t*kmax + c], c < k.
-// The task's column of X is staged in shared memory; each thread owns one
-// c and a slice of t, with four independent accumulators so that its
-// loads of B overlap.
-__device__ void tall_gemm_t(const double* X, int ldx, int len, int ntask,
-                            const double* B, int k, int kmax, double* out,
-                            double* red, double* xs, int bid, int nblk) {
+// A CTA takes its tasks (task = bid + i nblk) kSeedGemmGroup at a time:
+// their columns of X are staged in shared memory (xs, kSeedMaxSide each)
+// and every row of B a thread loads serves all of them, so the L2 round
+// trips for B are shared.  Each thread owns one c and the slice t = part +
+// s nparts, with four accumulators per task; a task's partial sums go to
+// gred (kSeedThreads each) and are added in a fixed order, so a task's
+// result does not depend on how many tasks its CTA holds.
+template <int kG>
+__device__ void tall_gemm_group(const double* X, int ldx, int len, int ntask,
+                                const double* B, int k, int kmax, double* out,
+                                double* gred, double* xs, int bid, int nblk) {
   const int tid = threadIdx.x;
   const int nparts = kSeedThreads / k;
   const int c = tid % k, part = tid / k;
-  for (int task = bid; task < ntask; task += nblk) {
-    const double* x = X + (size_t)task * ldx;
-    for (int t = tid; t < len; t += kSeedThreads) xs[t] = ldg_cg(x + t);
-    __syncthreads();
-    if (part < nparts) {
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int t = part;
-      for (; t + 3 * nparts < len; t += 4 * nparts) {
-        const double b0 = ldg_cg(B + (size_t)t * kmax + c);
-        const double b1 = ldg_cg(B + (size_t)(t + nparts) * kmax + c);
-        const double b2 = ldg_cg(B + (size_t)(t + 2 * nparts) * kmax + c);
-        const double b3 = ldg_cg(B + (size_t)(t + 3 * nparts) * kmax + c);
-        a0 = fma(xs[t], b0, a0);
-        a1 = fma(xs[t + nparts], b1, a1);
-        a2 = fma(xs[t + 2 * nparts], b2, a2);
-        a3 = fma(xs[t + 3 * nparts], b3, a3);
-      }
-      for (; t < len; t += nparts)
-        a0 = fma(xs[t], ldg_cg(B + (size_t)t * kmax + c), a0);
-      red[part * k + c] = (a0 + a1) + (a2 + a3);
+  for (int t0 = bid; t0 < ntask; t0 += kG * nblk) {
+    const int ng = min(kG, (ntask - t0 + nblk - 1) / nblk);
+    for (int g = 0; g < ng; ++g) {
+      const double* x = X + (size_t)(t0 + g * nblk) * ldx;
+      for (int t = tid; t < len; t += kSeedThreads)
+        xs[g * kSeedMaxSide + t] = ldg_cg(x + t);
     }
     __syncthreads();
-    if (tid < k) {
+    if (part < nparts) {
+      double acc[kG][4];
+#pragma unroll
+      for (int g = 0; g < kG; ++g)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[g][i] = 0.0;
+      int t = part;
+#pragma unroll 2
+      for (; t + 3 * nparts < len; t += 4 * nparts) {
+        double bv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          bv[i] = ldg_cg(B + (size_t)(t + i * nparts) * kmax + c);
+#pragma unroll
+        for (int g = 0; g < kG; ++g)
+          if (g < ng)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              acc[g][i] = fma(xs[g * kSeedMaxSide + t + i * nparts], bv[i],
+                              acc[g][i]);
+      }
+      for (; t < len; t += nparts) {
+        const double bv = ldg_cg(B + (size_t)t * kmax + c);
+#pragma unroll
+        for (int g = 0; g < kG; ++g)
+          if (g < ng) acc[g][0] = fma(xs[g * kSeedMaxSide + t], bv, acc[g][0]);
+      }
+#pragma unroll
+      for (int g = 0; g < kG; ++g)
+        if (g < ng)
+          gred[g * kSeedThreads + part * k + c] =
+              (acc[g][0] + acc[g][1]) + (acc[g][2] + acc[g][3]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < ng * k; idx += kSeedThreads) {
+      const int g = idx / k, cc = idx - g * k;
       double s = 0.0;
-      for (int q = 0; q < nparts; ++q) s += red[q * k + tid];
-      __stcg(out + (size_t)task * kmax + tid, s);
+      for (int q = 0; q < nparts; ++q) s += gred[g * kSeedThreads + q * k + cc];
+      __stcg(out + (size_t)(t0 + g * nblk) * kmax + cc, s);
     }
     __syncthreads();
   }
+}
+
+// Group size by the tasks per CTA (the group's accumulators cost registers,
+// so a CTA with one or two tasks runs the narrower forms).
+__device__ void tall_gemm_t(const double* X, int ldx, int len, int ntask,
+                            const double* B, int k, int kmax, double* out,
+                            double* gred, double* xs, int bid, int nblk) {
+  if (ntask <= nblk)
+    tall_gemm_group<1>(X, ldx, len, ntask, B, k, kmax, out, gred, xs, bid, nblk);
+  else if (ntask <= 2 * nblk)
+    tall_gemm_group<2>(X, ldx, len, ntask, B, k, kmax, out, gred, xs, bid, nblk);
+  else
+    tall_gemm_group<kSeedGemmGroup>(X, ldx, len, ntask, B, k, kmax, out, gred,
+                                    xs, bid, nblk);
 }
 
 // Gm = X^T X (k x k) for X (nrows x k, row-major stride kmax); one warp per
@@ -569,8 +610,9 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
   extern __shared__ __align__(16) double sm[];
   const int kmax = a.kmax;
   double* red = sm;                      // kSeedThreads
-  double* xs = red + kSeedThreads;       // kSeedMaxSide (staged column)
-  double* lam = xs + kSeedMaxSide;       // kmax (singular values s_c)
+  double* xs = red + kSeedThreads;       // kSeedGemmGroup x kSeedMaxSide
+  double* gred = xs + kSeedGemmGroup * kSeedMaxSide;  // x kSeedThreads
+  double* lam = gred + kSeedGemmGroup * kSeedThreads;  // kmax (values s_c)
   double* dsc = lam + kmax;              // kmax
   double* xi = dsc + kmax;               // kmax
   double* rowb = xi + kmax;              // kmax
@@ -669,7 +711,7 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
 
   while (true) {
     // ---- T = G^T Omega ------------------------------------------------------
-    tall_gemm_t(a.G, mp, mp, np, a.Om, k, kmax, a.T, red, xs, b, nb);
+    tall_gemm_t(a.G, mp, mp, np, a.Om, k, kmax, a.T, gred, xs, b, nb);
     if (!team_sync()) return;
     trace_mark(a, 2);
     gram(a.T, np, k, kmax, a.Gam, b, nb);
@@ -680,7 +722,7 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     if (!team_sync()) return;
     trace_mark(a, 4);
     // ---- P = G Psi ------------------------------------------------------------
-    tall_gemm_t(a.Gt, np, np, mp, a.Psi, k, kmax, a.P, red, xs, b, nb);
+    tall_gemm_t(a.Gt, np, np, mp, a.Psi, k, kmax, a.P, gred, xs, b, nb);
     if (stage >= 2) gram(a.Psi, np, k, kmax, a.Gam2, b, nb);  // E = Psi1^T Psi1 - I
     if (!team_sync()) return;
     trace_mark(a, 5);
@@ -1283,7 +1325,8 @@ __global__ void seed_ctl_zero_kernel(const SeedArgs* __restrict__ args,
 
 size_t seed_smem_bytes(int kmax) {
   return sizeof(double) * ((size_t)kmax * kmax + kSeedThreads +
-                           kSeedMaxSide + 4 * kmax) +
+                           kSeedGemmGroup * (kSeedMaxSide + kSeedThreads) +
+                           4 * kmax) +
          sizeof(float) * ((size_t)3 * kmax * kmax) +
          sizeof(int) * 2 * kmax + (size_t)kmax * kmax;
 }
