@@ -366,7 +366,6 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
   const int tid = threadIdx.x;
   const bool prof = sub && bid == 0 && tid == 0;
   long long q0 = prof ? clock64() : 0;
-  __shared__ float s_inv[2];
   for (int c = tid; c < k; c += kSeedThreads) {
     const double g = ldg_cg(Gm + c * kmax + c);
     dead[c] = !(g > 0.0);
@@ -395,34 +394,44 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
   // the k sequential pivot steps are skipped.
   const bool near_orth = !__syncthreads_or(coupled);
   long long q1 = prof ? clock64() : 0;
-  // Right-looking Cholesky, R in the upper triangle.  Step j's trailing
-  // update reads row j unscaled (times 1/pivot^2); row j is scaled at the
-  // start of step j+1.  The reciprocal alternates between two slots so step
-  // j+1's pivot never overwrites the value step j's scaling still reads.
-  for (int j = 0; j < (near_orth ? 0 : k); ++j) {
-    __syncthreads();
-    if (j > 0) {
-      const float inv = s_inv[(j - 1) & 1];
-      for (int c = j + tid; c < k; c += kSeedThreads) A32[(j - 1) * k + c] *= inv;
-    }
-    if (tid == 0) {
-      const float piv = A32[j * k + j];
-      if (!(piv > 1e-6f) || dead[j]) {
-        dead[j] = 1;
-        s_inv[j & 1] = 0.0f;
-        A32[j * k + j] = 1.0f;
-      } else {
-        const float rs = rsqrtf(piv);
-        s_inv[j & 1] = rs;
-        A32[j * k + j] = piv * rs;
+  // Right-looking Cholesky, R in the upper triangle, one CTA barrier per
+  // step: at the start of step j row j is final (R_j. = a_j. / sqrt(a_jj));
+  // warp 0 updates row j+1 with it, takes that row's pivot and scales it
+  // (warp-synchronous), while warps 1.. update rows j+2.. (a_ab -= R_ja R_jb,
+  // b >= a).  A non-positive pivot marks the column dead (R_jj = 1, rest of
+  // the row 0).
+  if (!near_orth) {
+    const int lane = tid & 31, w = tid >> 5;
+    auto finish_row = [&](int r) {  // warp 0: pivot and scaling of row r
+      const float piv = A32[r * k + r];
+      const bool bad = !(piv > 1e-6f) || dead[r];
+      const float rs = bad ? 0.0f : rsqrtf(piv);
+      for (int c = r + 1 + lane; c < k; c += 32) A32[r * k + c] *= rs;
+      __syncwarp();
+      if (lane == 0) {
+        A32[r * k + r] = bad ? 1.0f : piv * rs;
+        if (bad) dead[r] = 1;
       }
-    }
-    __syncthreads();
-    const float inv2 = s_inv[j & 1] * s_inv[j & 1];
-    for (int a = j + 1 + (tid >> 4); a < k; a += kSeedThreads / 16) {
-      const float rja = A32[j * k + a] * inv2;
-      for (int b = a + (tid & 15); b < k; b += 16)
-        A32[a * k + b] -= rja * A32[j * k + b];
+    };
+    if (w == 0) finish_row(0);
+    for (int j = 0; j + 1 < k; ++j) {
+      __syncthreads();
+      if (w == 0) {
+        const int r = j + 1;
+        const float rjr = A32[j * k + r];
+        for (int c = r + lane; c < k; c += 32)
+          A32[r * k + c] -= rjr * A32[j * k + c];
+        __syncwarp();
+        finish_row(r);
+      } else {
+        const int t = tid - 32;  // 0 .. kSeedThreads - 33
+        constexpr int kRows = (kSeedThreads - 32) / 16;
+        for (int a = j + 2 + (t >> 4); a < k; a += kRows) {
+          const float rja = A32[j * k + a];
+          for (int c = a + (t & 15); c < k; c += 16)
+            A32[a * k + c] -= rja * A32[j * k + c];
+        }
+      }
     }
   }
   __syncthreads();
