@@ -18,6 +18,7 @@ struct SeedCtl {
   int rank_raw;
   int ntrace;
   int jsweeps;     // total Jacobi sweeps (block 0), for tracing
+  int jpath[3];    // Rayleigh-Ritz steps by form: first-order, cluster, full
   long long jcyc[4];  // block 0 Jacobi cycles: angles, A, V, end-of-round
   long long sub[8];   // block 0 sub-step cycle counters (tracing)
   double residual;

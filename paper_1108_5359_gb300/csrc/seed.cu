@@ -756,32 +756,26 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     // orthonormal to O(E^2).  The W correction is tiny, so an FP32 product
     // is exact enough for it.
     {
-      float* E32 = W0;  // E, then the Jacobi's V
       float* C32 = J0;  // C1 / cmax, then the Jacobi's A
+      // E is kept for the W correction after the Jacobi, as floats in the
+      // (still unused) storage of Vd; C1 and E in one pass over L2, then
+      // C1 scaled by its largest diagonal entry
+      float* Esave = reinterpret_cast<float*>(Vd);
       const long long ts0 = clock64();
-      const double cm = block_reduce_max(
-          tid < k ? ldg_cg(a.Gam + tid * kmax + tid) : 0.0, red);
+      double dmax = 0.0;
+      for (int p = tid >> 4; p < k; p += kSeedThreads / 16)
+        for (int q = tid & 15; q < k; q += 16) {
+          const double g = ldg_cg(a.Gam + p * kmax + q);
+          Esave[p * k + q] =
+              (float)ldg_cg(a.Gam2 + p * kmax + q) - (p == q ? 1.0f : 0.0f);
+          C32[p * k + q] = (float)g;
+          if (p == q) dmax = fmax(dmax, g);
+        }
+      const double cm = block_reduce_max(dmax, red);
       const long long ts1 = clock64();
       if (b == 0 && tid == 0) ctl->jcyc[0] += ts1 - ts0;
-      for (int p = tid >> 4; p < k; p += kSeedThreads / 16)
-        for (int q = tid & 15; q < k; q += 16)
-          E32[p * k + q] =
-              (float)ldg_cg(a.Gam2 + p * kmax + q) - (p == q ? 1.0f : 0.0f);
-      __syncthreads();
-      const long long ts2 = clock64();
-      if (b == 0 && tid == 0) ctl->sub[3] += ts2 - ts1;
       const float inv = cm > 0.0 ? (float)(1.0 / cm) : 1.0f;
-      for (int p = tid >> 4; p < k; p += kSeedThreads / 16)
-        for (int q = tid & 15; q < k; q += 16)
-          C32[p * k + q] = (float)ldg_cg(a.Gam + p * kmax + q) * inv;
-      __syncthreads();
-      const long long ts3 = clock64();
-      if (b == 0 && tid == 0) ctl->sub[4] += ts3 - ts2;
-      // keep E for the W correction after the Jacobi, as floats in the
-      // (still unused) storage of Vd
-      float* Esave = reinterpret_cast<float*>(Vd);
-      for (int idx = tid; idx < k * k; idx += kSeedThreads)
-        Esave[idx] = E32[idx];
+      for (int idx = tid; idx < k * k; idx += kSeedThreads) C32[idx] *= inv;
       __syncthreads();
       if (b == 0 && tid == 0) ctl->jcyc[3] += clock64() - ts0;
       trace_mark(a, 12);
@@ -887,6 +881,8 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
         }
         __syncthreads();
       }
+      if (kGrid && b == 0 && tid == 0)
+        ++ctl->jpath[fast ? 0 : (cluster ? 1 : 2)];
       if (!fast && !cluster) {
         float* Afin = block_jacobi32(
             C32, cs, W0, k, reinterpret_cast<unsigned char*>(prs + kmax),
@@ -974,6 +970,8 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     }
     if (!team_sync()) return;
     trace_mark(a, 9);
+    const bool prof_alm = kGrid && b == 0 && tid == 0 && a.trace;
+    long long pa0 = prof_alm ? clock64() : 0;
     // ---- FP64 Ritz values s_c = ||Pt e_c|| (fixed-order sum over blocks) ---
     {
       const int nparts = kSeedThreads / k;
@@ -1000,6 +998,11 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     }
     Ptc = a.Pt;
     PsiTc = a.PsiT;
+    if (prof_alm) {
+      const long long t = clock64();
+      ctl->sub[5] += t - pa0;  // Ritz values
+      pa0 = t;
+    }
     if (stage == 3 && res < 1e-5) {
       // ---- FP64 refinement of the Ritz basis (near convergence) -----------
       // The FP32 Jacobi leaves B = Pt^T Pt with off-diagonal entries of
@@ -1111,6 +1114,11 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
       continue;
     }
 
+    if (prof_alm) {
+      const long long t = clock64();
+      ctl->sub[6] += t - pa0;  // refinement, shrink factors, Omega_next
+      pa0 = t;
+    }
     // ---- ALM step: L = Pt diag(d) PsiT^T, S, Y, G for the next iteration ---
     const double mu_next = fmin(a.rho * mu, mu_max);
     const double inv_mu = 1.0 / mu, inv_mu_next = 1.0 / mu_next;
@@ -1218,6 +1226,7 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
         if (tid == 0) __stcg(a.part + 4 * v + 2, zz);
       }
     }
+    if (prof_alm) ctl->sub[7] += clock64() - pa0;  // elementwise update
     ++it;
     if (!team_sync()) return;
     trace_mark(a, 11);
@@ -1286,6 +1295,14 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
           a.trace[2 * i] = q < 4 ? (unsigned long long)ctl->jcyc[q]
                                  : (unsigned long long)ctl->jsweeps;
           a.trace[2 * i + 1] = 95ull + q;
+          ctl->ntrace = i + 1;
+        }
+      }
+      for (int q = 0; q < 3; ++q) {  // Rayleigh-Ritz forms, phases 88..90
+        const int i = ctl->ntrace;
+        if (i < kSeedTraceCap) {
+          a.trace[2 * i] = (unsigned long long)ctl->jpath[q];
+          a.trace[2 * i + 1] = 88ull + q;
           ctl->ntrace = i + 1;
         }
       }
