@@ -1150,11 +1150,19 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
       __stcg(a.G + e, g);
       return g;
     };
+    // Far from convergence (residual above 1e-4) the rank-k products of L
+    // run in FP32 (operands rounded once when staged, FP32 accumulation):
+    // their ~1e-7 relative error is far below what the inexact ALM leaves
+    // at that point, and this part's FP64 pipe (2 FMA/clk/SM) made them the
+    // update's cost on the 500 x 500 seed.  Every later iteration is FP64.
+    const bool lowp = res > 1e-4;
     if (TT > 0) {
-      const int kp = k | 1;  // odd row pitch: conflict-free FP64 reads
+      const int kp = k | 1;  // odd row pitch: conflict-free reads
       double* Pts = Vd;                 // [TT][kp]
       double* Qs = Pts + TT * kp;       // [TT][kp], scaled by d
       double* Gs = Qs + TT * kp;        // [TT][TT + 1]
+      float* Pf = reinterpret_cast<float*>(Pts);  // FP32 form of the same
+      float* Qf = Pf + TT * kp;
       const int tcn = (np + TT - 1) / TT;
       const int ntile = ((mp + TT - 1) / TT) * tcn;
       for (int v = b; v < nv; v += nb) {
@@ -1163,29 +1171,50 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
           const int i0 = (tile / tcn) * TT, j0 = (tile % tcn) * TT;
           for (int idx = tid; idx < TT * k; idx += kSeedThreads) {
             const int ii = idx / k, c = idx - ii * k;
-            Pts[ii * kp + c] =
+            const double pv =
                 (i0 + ii < mp) ? ldg_cg(Ptc + (size_t)(i0 + ii) * kmax + c)
                                : 0.0;
-            Qs[ii * kp + c] =
+            const double qv =
                 (j0 + ii < np)
                     ? dsc[c] * ldg_cg(PsiTc + (size_t)(j0 + ii) * kmax + c)
                     : 0.0;
+            if (lowp) {
+              Pf[ii * kp + c] = (float)pv;
+              Qf[ii * kp + c] = (float)qv;
+            } else {
+              Pts[ii * kp + c] = pv;
+              Qs[ii * kp + c] = qv;
+            }
           }
           __syncthreads();
           for (int q = tid; q < TT * TT; q += kSeedThreads) {
             const int ii = q % TT, jj = q / TT;
             const int i = i0 + ii, j = j0 + jj;
             if (i < mp && j < np) {
-              const double* pr = Pts + ii * kp;
-              const double* qr = Qs + jj * kp;
-              double l0 = 0.0, l1 = 0.0;
+              double l;
               int c = 0;
-              for (; c + 1 < k; c += 2) {
-                l0 = fma(pr[c], qr[c], l0);
-                l1 = fma(pr[c + 1], qr[c + 1], l1);
+              if (lowp) {
+                const float* pr = Pf + ii * kp;
+                const float* qr = Qf + jj * kp;
+                float l0 = 0.0f, l1 = 0.0f;
+                for (; c + 1 < k; c += 2) {
+                  l0 = fmaf(pr[c], qr[c], l0);
+                  l1 = fmaf(pr[c + 1], qr[c + 1], l1);
+                }
+                if (c < k) l0 = fmaf(pr[c], qr[c], l0);
+                l = (double)(l0 + l1);
+              } else {
+                const double* pr = Pts + ii * kp;
+                const double* qr = Qs + jj * kp;
+                double l0 = 0.0, l1 = 0.0;
+                for (; c + 1 < k; c += 2) {
+                  l0 = fma(pr[c], qr[c], l0);
+                  l1 = fma(pr[c + 1], qr[c + 1], l1);
+                }
+                if (c < k) l0 = fma(pr[c], qr[c], l0);
+                l = l0 + l1;
               }
-              if (c < k) l0 = fma(pr[c], qr[c], l0);
-              Gs[jj * (TT + 1) + ii] = alm_elem(l0 + l1, i, j, zz);
+              Gs[jj * (TT + 1) + ii] = alm_elem(l, i, j, zz);
             }
           }
           __syncthreads();
