@@ -61,7 +61,7 @@ constexpr int kSeedGridSlots = 152;
 
 struct SeedLayout {
   size_t ctl, part, colsq, S, Y, G, Gt, Om, P, Pt, T, Psi, PsiT, Gam, Gam2,
-      trace, total;
+      Om32, Psi32, trace, total;
 };
 
 SeedLayout seed_layout(int mp, int np, int kmax, int nbmax) {
@@ -88,6 +88,8 @@ SeedLayout seed_layout(int mp, int np, int kmax, int nbmax) {
   L.PsiT = take((size_t)np * kmax * sizeof(double));
   L.Gam = take((size_t)kmax * kmax * sizeof(double));
   L.Gam2 = take((size_t)kmax * kmax * sizeof(double));
+  L.Om32 = take((size_t)mp * kmax * sizeof(float));
+  L.Psi32 = take((size_t)np * kmax * sizeof(float));
   L.trace = take((size_t)kSeedTraceCap * 2 * sizeof(unsigned long long));
   L.total = off;
   return L;
@@ -126,13 +128,14 @@ struct alignas(16) SeedArgs {
   double *T, *Psi, *PsiT;  // np x kmax, row-major
   double* Gam;             // kmax x kmax
   double* Gam2;            // kmax x kmax: Psi1^T Psi1
+  float *Om32, *Psi32;     // FP32 copies of Om, Psi (early tall products)
   unsigned long long* trace;  // block 0's phase timestamps
   double *U, *Sigma, *V;   // outputs (column-major, ld mp / np)
 };
 
 __device__ __forceinline__ double ldg_cg(const double* p) { return __ldcg(p); }
 
-// Software grid barrier (sense by generation), bounded by a timeout.
+// Software grid barrier, bounded by a timeout.
 __device__ bool grid_sync(SeedCtl* ctl, unsigned int nblocks,
                           unsigned long long timeout_ns) {
   // Counter barrier on a monotonically increasing arrival count (the control
@@ -240,10 +243,12 @@ __device__ double sum_partials(const double* src, int nb, int stride, int off,
 // s nparts, with four accumulators per task; a task's partial sums go to
 // gred (kSeedThreads each) and are added in a fixed order, so a task's
 // result does not depend on how many tasks its CTA holds.
-template <int kG>
+template <int kG, typename TF>
 __device__ void tall_gemm_group(const double* X, int ldx, int len, int ntask,
-                                const double* B, int k, int kmax, double* out,
-                                double* gred, double* xs, int bid, int nblk) {
+                                const TF* B, int k, int kmax, double* out,
+                                double* gred, double* xs_raw, int bid,
+                                int nblk) {
+  TF* xs = reinterpret_cast<TF*>(xs_raw);
   const int tid = threadIdx.x;
   const int nparts = kSeedThreads / k;
   const int c = tid % k, part = tid / k;
@@ -252,22 +257,22 @@ __device__ void tall_gemm_group(const double* X, int ldx, int len, int ntask,
     for (int g = 0; g < ng; ++g) {
       const double* x = X + (size_t)(t0 + g * nblk) * ldx;
       for (int t = tid; t < len; t += kSeedThreads)
-        xs[g * kSeedMaxSide + t] = ldg_cg(x + t);
+        xs[g * kSeedMaxSide + t] = (TF)ldg_cg(x + t);
     }
     __syncthreads();
     if (part < nparts) {
-      double acc[kG][4];
+      TF acc[kG][4];
 #pragma unroll
       for (int g = 0; g < kG; ++g)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) acc[g][i] = 0.0;
+        for (int i = 0; i < 4; ++i) acc[g][i] = TF(0);
       int t = part;
 #pragma unroll 2
       for (; t + 3 * nparts < len; t += 4 * nparts) {
-        double bv[4];
+        TF bv[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-          bv[i] = ldg_cg(B + (size_t)(t + i * nparts) * kmax + c);
+          bv[i] = __ldcg(B + (size_t)(t + i * nparts) * kmax + c);
 #pragma unroll
         for (int g = 0; g < kG; ++g)
           if (g < ng)
@@ -277,7 +282,7 @@ __device__ void tall_gemm_group(const double* X, int ldx, int len, int ntask,
                               acc[g][i]);
       }
       for (; t < len; t += nparts) {
-        const double bv = ldg_cg(B + (size_t)t * kmax + c);
+        const TF bv = __ldcg(B + (size_t)t * kmax + c);
 #pragma unroll
         for (int g = 0; g < kG; ++g)
           if (g < ng) acc[g][0] = fma(xs[g * kSeedMaxSide + t], bv, acc[g][0]);
@@ -286,7 +291,7 @@ __device__ void tall_gemm_group(const double* X, int ldx, int len, int ntask,
       for (int g = 0; g < kG; ++g)
         if (g < ng)
           gred[g * kSeedThreads + part * k + c] =
-              (acc[g][0] + acc[g][1]) + (acc[g][2] + acc[g][3]);
+              (double)((acc[g][0] + acc[g][1]) + (acc[g][2] + acc[g][3]));
     }
     __syncthreads();
     for (int idx = tid; idx < ng * k; idx += kSeedThreads) {
@@ -300,10 +305,27 @@ __device__ void tall_gemm_group(const double* X, int ldx, int len, int ntask,
 }
 
 // Group size by the tasks per CTA (the group's accumulators cost registers,
-// so a CTA with one or two tasks runs the narrower forms).
+// so a CTA with one or two tasks runs the narrower forms).  With B32 (an
+// FP32 copy of B) the products run in FP32: the seed uses that while the
+// ALM residual is above 1e-4, where their ~1e-7 relative error is far below
+// what the inexact ALM leaves, and this part's FP64 pipe (2 FMA/clk/SM)
+// made the tall products FP64-throughput bound on the 500 x 500 seed.
 __device__ void tall_gemm_t(const double* X, int ldx, int len, int ntask,
-                            const double* B, int k, int kmax, double* out,
-                            double* gred, double* xs, int bid, int nblk) {
+                            const double* B, const float* B32, int k, int kmax,
+                            double* out, double* gred, double* xs, int bid,
+                            int nblk) {
+  if (B32) {
+    if (ntask <= nblk)
+      tall_gemm_group<1>(X, ldx, len, ntask, B32, k, kmax, out, gred, xs, bid,
+                         nblk);
+    else if (ntask <= 2 * nblk)
+      tall_gemm_group<2>(X, ldx, len, ntask, B32, k, kmax, out, gred, xs, bid,
+                         nblk);
+    else
+      tall_gemm_group<kSeedGemmGroup>(X, ldx, len, ntask, B32, k, kmax, out,
+                                      gred, xs, bid, nblk);
+    return;
+  }
   if (ntask <= nblk)
     tall_gemm_group<1>(X, ldx, len, ntask, B, k, kmax, out, gred, xs, bid, nblk);
   else if (ntask <= 2 * nblk)
@@ -359,7 +381,8 @@ __device__ void gram(const double* X, int nrows, int k, int kmax,
 // absorbs (tested against the full-SVD FP64 oracle).  Columns whose norm or
 // pivot vanishes are dead and come out zero.  A32: k x k shared; Ri32: k.
 __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
-                             const double* Gm, double* Out, float* A32,
+                             const double* Gm, double* Out, float* Out32,
+                             float* A32,
                              float* Ri32, double* dsc, int* dead,
                              double* rowb, int bid, int nblk, int row_warps,
                              long long* sub) {
@@ -463,8 +486,14 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
       if (c0 > j && c0 < k) p0 = fma(-xj, (double)A32[j * k + c0], p0);
       if (c1 > j && c1 < k) p1 = fma(-xj, (double)A32[j * k + c1], p1);
     }
-    if (c0 < k) __stcg(Out + (size_t)t * kmax + c0, o0);
-    if (c1 < k) __stcg(Out + (size_t)t * kmax + c1, o1);
+    if (c0 < k) {
+      __stcg(Out + (size_t)t * kmax + c0, o0);
+      Out32[(size_t)t * kmax + c0] = (float)o0;
+    }
+    if (c1 < k) {
+      __stcg(Out + (size_t)t * kmax + c1, o1);
+      Out32[(size_t)t * kmax + c1] = (float)o1;
+    }
   }
   if (prof) {
     const long long q3 = clock64();
@@ -674,7 +703,9 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     for (size_t e = (size_t)b * kSeedThreads + tid; e < (size_t)mp * a.k0;
          e += (size_t)nb * kSeedThreads) {
       const int i = (int)(e / a.k0), c = (int)(e - (size_t)i * a.k0);
-      __stcg(a.Om + (size_t)i * kmax + c, hash_normal(0x5EEDull + c, i));
+      const double v = hash_normal(0x5EEDull + c, i);
+      __stcg(a.Om + (size_t)i * kmax + c, v);
+      a.Om32[(size_t)i * kmax + c] = (float)v;
     }
   }
   if (!team_sync()) return;
@@ -720,18 +751,20 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
 
   while (true) {
     // ---- T = G^T Omega ------------------------------------------------------
-    tall_gemm_t(a.G, mp, mp, np, a.Om, k, kmax, a.T, gred, xs, b, nb);
+    tall_gemm_t(a.G, mp, mp, np, a.Om, res > 1e-4 ? a.Om32 : nullptr, k, kmax,
+                a.T, gred, xs, b, nb);
     if (!team_sync()) return;
     trace_mark(a, 2);
     gram(a.T, np, k, kmax, a.Gam, b, nb);
     if (!team_sync()) return;
     trace_mark(a, 3);
-    cholqr_apply(a.T, np, k, kmax, a.Gam, a.Psi, J0, W0, dsc, dead, rowb,
+    cholqr_apply(a.T, np, k, kmax, a.Gam, a.Psi, a.Psi32, J0, W0, dsc, dead, rowb,
                  b, nb, row_warps, kGrid ? ctl->sub : nullptr);
     if (!team_sync()) return;
     trace_mark(a, 4);
     // ---- P = G Psi ------------------------------------------------------------
-    tall_gemm_t(a.Gt, np, np, mp, a.Psi, k, kmax, a.P, gred, xs, b, nb);
+    tall_gemm_t(a.Gt, np, np, mp, a.Psi, res > 1e-4 ? a.Psi32 : nullptr, k,
+                kmax, a.P, gred, xs, b, nb);
     if (stage >= 2) gram(a.Psi, np, k, kmax, a.Gam2, b, nb);  // E = Psi1^T Psi1 - I
     if (!team_sync()) return;
     trace_mark(a, 5);
@@ -740,7 +773,7 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     trace_mark(a, 6);
     if (stage < 2) {
       // plain power step on D: Omega = orth(P)
-      cholqr_apply(a.P, mp, k, kmax, a.Gam, a.Om, J0, W0, dsc, dead, rowb, b, nb,
+      cholqr_apply(a.P, mp, k, kmax, a.Gam, a.Om, a.Om32, J0, W0, dsc, dead, rowb, b, nb,
                    row_warps, nullptr);
       if (!team_sync()) return;
       trace_mark(a, 7);
@@ -1091,6 +1124,7 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
           const double v = keep ? ldg_cg(Ptc + (size_t)i * kmax + c) * inv
                                 : hash_normal(0xA11CEull + 977ull * it + c, i);
           __stcg(a.Om + (size_t)i * kmax + c, v);
+          a.Om32[(size_t)i * kmax + c] = (float)v;
         }
       }
     }
@@ -1423,6 +1457,8 @@ void fill_seed_args(SeedArgs& a, const SeedLayout& L, char* w,
   a.Pt = reinterpret_cast<double*>(w + L.Pt);
   a.T = reinterpret_cast<double*>(w + L.T);
   a.Psi = reinterpret_cast<double*>(w + L.Psi);
+  a.Om32 = reinterpret_cast<float*>(w + L.Om32);
+  a.Psi32 = reinterpret_cast<float*>(w + L.Psi32);
   a.PsiT = reinterpret_cast<double*>(w + L.PsiT);
   a.Gam = reinterpret_cast<double*>(w + L.Gam);
   a.Gam2 = reinterpret_cast<double*>(w + L.Gam2);
