@@ -385,24 +385,22 @@ def run_ours(args):
         parity = sampled_parity(P, pseed, Lu, Lv, S)
         parity["status"] = int(st)
 
-    # e2e through the public API from pinned host buffers
+    # e2e through the public host-buffer call (pcp_l1filter_solve_host):
+    # M from pinned host memory, Lu, Lv and S back to pinned host memory,
+    # all copies inside the timed span
     e2e = None
     if not args.no_e2e:
-        hM = torch.from_numpy(np.ascontiguousarray(M32.T)).pin_memory()
-        hLu = torch.empty((r, m), dtype=torch.float32).pin_memory()
-        hLv = torch.empty((r, n), dtype=torch.float32).pin_memory()
-        hS = torch.empty((n, m), dtype=torch.float32).pin_memory()
+        hM = torch.from_numpy(np.ascontiguousarray(M32.T)).pin_memory().t()
+        hLu = torch.empty((r, m), dtype=torch.float32).pin_memory().t()
+        hLv = torch.empty((r, n), dtype=torch.float32).pin_memory().t()
+        hS = torch.empty((n, m), dtype=torch.float32).pin_memory().t()
         e_ms = []
         for it in range(max(3, args.warmup) + args.steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            dM.t().copy_(hM, non_blocking=True)
-            pk.pcp_l1filter_solve(plan, dM, Lu, Lv, S, info=False,
-                                  stream=stream)
-            hLu.copy_(Lu.t(), non_blocking=True)
-            hLv.copy_(Lv.t(), non_blocking=True)
-            hS.copy_(S.t(), non_blocking=True)
+            pk.pcp_l1filter_solve_host(plan, hM, hLu, hLv, hS, info=False,
+                                       stream=stream)
             e1.record(stream)
             e1.synchronize()
             if it >= max(3, args.warmup):

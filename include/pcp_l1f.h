@@ -212,6 +212,25 @@ pcp_status pcp_l1filter_solve(pcp_plan* plan, const float* dM, int64_t ldm,
                               int64_t* h_seed_cols_out, pcp_info* info,
                               void* stream);
 
+/* pcp_l1filter_solve on host buffers, with the copies overlapped with the
+ * compute.  hM (m x n, ldm >= m) is host memory; page-locked memory
+ * (cudaHostAlloc / cudaHostRegister) is read in place by the seed gather so
+ * the seed starts while M is still being copied, and the copies run
+ * asynchronously; pageable memory works with the copies serialised.
+ * hLu (m x r, ld m), hLv (n x r, ld n) and hS (m x n, lds >= m; NULL to
+ * skip S) receive the results: the factors while the S pass runs, S in
+ * column chunks while the next chunk is computed.  The plan keeps device
+ * copies of M, S and the factors (allocated on the first call, freed by
+ * pcp_plan_destroy) and a copy stream; successive calls on one stream reuse
+ * them in order.  info and the status codes as for pcp_l1filter_solve
+ * (with info, t_spass_ms includes the last copies of S).  Without info the
+ * call returns before the copies finish: synchronise `stream` before
+ * reading the outputs or reusing hM. */
+pcp_status pcp_l1filter_solve_host(pcp_plan* plan, const float* hM,
+                                   int64_t ldm, float* hLu, float* hLv,
+                                   float* hS, int64_t lds, pcp_info* info,
+                                   void* stream);
+
 void pcp_plan_destroy(pcp_plan* plan);
 
 /* Batched form of Algorithm 2 (Section 3.2: the column and row problems of

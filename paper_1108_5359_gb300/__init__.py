@@ -22,7 +22,8 @@ from ._abi import (PCPError, PCPInfo, PCPParams, PCPProblem,
 __all__ = [
     "PCPError", "PCPInfo", "PCPParams", "PCP_FP32", "PCP_BF16_REFINED",
     "colmajor", "pcp_params_default", "pcp_l1filter_plan",
-    "pcp_l1filter_solve", "pcp_plan_destroy", "pcp_gather_seed",
+    "pcp_l1filter_solve", "pcp_l1filter_solve_host", "pcp_plan_destroy",
+    "pcp_gather_seed",
     "pcp_seed_workspace_bytes", "pcp_seed_pcp", "pcp_seed_pcp_static",
     "pcp_l1_filter",
     "pcp_assemble_factors", "pcp_spass", "PCP_SPASS_AUTO", "PCP_SPASS_SIMT",
@@ -58,6 +59,20 @@ def _cm(t, name):
         return t.data_ptr(), max(1, t.shape[0])
     if t.stride(0) != 1 and t.shape[0] > 1:
         raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    return t.data_ptr(), max(t.stride(1), t.shape[0], 1)
+
+
+def _cm_host(t, name):
+    """(pointer, leading dimension) of a column-major CPU tensor (pinned for
+    overlapped copies)."""
+    if t is None:
+        return None, 0
+    if t.is_cuda:
+        raise ValueError(f"{name} must be a host (CPU) tensor")
+    if t.dim() == 2 and t.stride(0) != 1 and t.shape[0] > 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1)")
+    if t.dim() == 1:
+        return t.data_ptr(), max(1, t.shape[0])
     return t.data_ptr(), max(t.stride(1), t.shape[0], 1)
 
 
@@ -158,6 +173,24 @@ def pcp_l1filter_solve(plan: Plan, M, Lu, Lv, S=None, info=True,
     if raise_on_error and st not in (PCP_OK,):
         check(st, "pcp_l1filter_solve")
     return st, inf, rows, cols
+
+
+def pcp_l1filter_solve_host(plan: Plan, M, Lu, Lv, S=None, info=True,
+                            stream=None, raise_on_error=True):
+    """Algorithm 2 on a host M (column-major CPU tensor, pinned for overlap)
+    into host (Lu, Lv, S), copies overlapped with compute; returns
+    (status, info).  Without info, synchronise `stream` before reading."""
+    pM, ldm = _cm_host(M, "M")
+    pLu, _ = _cm_host(Lu, "Lu")
+    pLv, _ = _cm_host(Lv, "Lv")
+    pS, lds = _cm_host(S, "S")
+    inf = PCPInfo() if info else None
+    st = load().pcp_l1filter_solve_host(
+        plan.handle, pM, ldm, pLu, pLv, pS, lds if S is not None else plan.m,
+        C.byref(inf) if inf is not None else None, _stream(stream))
+    if raise_on_error and st not in (PCP_OK,):
+        check(st, "pcp_l1filter_solve_host")
+    return st, inf
 
 
 class _Problem:

@@ -113,6 +113,12 @@ static std::vector<int64_t> sorted_prefix(const std::vector<int64_t>& order,
 
 }  // namespace pcp
 
+// S-pass column chunks of a host-buffer solve (each chunk's S goes back to
+// the host while the next chunk is computed) and the events that order the
+// copy stream against the compute stream.
+constexpr int kHostChunks = 8;
+constexpr int kHostEvents = kHostChunks + 4;
+
 struct pcp_plan {
   pcp_params p;
   std::vector<int64_t> given_rows, given_cols;
@@ -136,6 +142,11 @@ struct pcp_plan {
   bool idx_uploaded = false;
   std::vector<int64_t> cur_rows, cur_cols;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // host-buffer solves (pcp_l1filter_solve_host), allocated on first use:
+  // device copies of M, S and the factors, a copy stream and its events
+  float *hd_M = nullptr, *hd_S = nullptr, *hd_Lu = nullptr, *hd_Lv = nullptr;
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t cev[kHostEvents] = {};
 };
 
 extern "C" const char* pcp_last_error(void) { return pcp::g_err; }
@@ -351,6 +362,13 @@ extern "C" void pcp_plan_destroy(pcp_plan* P) {
     if (ev) cudaEventDestroy(ev);
   if (P->h_idx) cudaFreeHost(P->h_idx);
   if (P->d_base) cudaFree(P->d_base);
+  for (auto& ev : P->cev)
+    if (ev) cudaEventDestroy(ev);
+  if (P->copy_st) cudaStreamDestroy(P->copy_st);
+  cudaFree(P->hd_M);
+  cudaFree(P->hd_S);
+  cudaFree(P->hd_Lu);
+  cudaFree(P->hd_Lv);
   delete P;
 }
 
@@ -406,11 +424,27 @@ static pcp_status upload_indices(pcp_plan* P, cudaStream_t st) {
   return PCP_OK;
 }
 
+// Host buffers of a pcp_l1filter_solve_host call.
+struct HostIO {
+  const float* hM;     // host M (column-major, ld ldm)
+  const float* gM;     // device-accessible address of hM, or null (pageable)
+  int64_t ldm;
+  float *hLu, *hLv;    // host factors (ld m / ld n)
+  float* hS;           // host S (ld lds) or null
+  int64_t lds;
+};
+
 static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
                              float* dLu, float* dLv, float* dS, int64_t lds,
                              int64_t* h_seed_rows_out,
                              int64_t* h_seed_cols_out, pcp_info* info,
-                             void* stream);
+                             void* stream, const HostIO* hio = nullptr);
+
+static pcp_status grow_loop(pcp_plan* P, const float* dM, int64_t ldm,
+                            float* dLu, float* dLv, float* dS, int64_t lds,
+                            int64_t* h_seed_rows_out,
+                            int64_t* h_seed_cols_out, pcp_info* info,
+                            void* stream, pcp_status st);
 
 extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
                                          int64_t ldm, float* dLu, float* dLv,
@@ -420,6 +454,15 @@ extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
                                          pcp_info* info, void* stream) {
   pcp_status st = solve_once(P, dM, ldm, dLu, dLv, dS, lds, h_seed_rows_out,
                              h_seed_cols_out, info, stream);
+  return grow_loop(P, dM, ldm, dLu, dLv, dS, lds, h_seed_rows_out,
+                   h_seed_cols_out, info, stream, st);
+}
+
+static pcp_status grow_loop(pcp_plan* P, const float* dM, int64_t ldm,
+                            float* dLu, float* dLv, float* dS, int64_t lds,
+                            int64_t* h_seed_rows_out,
+                            int64_t* h_seed_cols_out, pcp_info* info,
+                            void* stream, pcp_status st) {
   if (!P || !info || !P->p.grow_seed) return st;
   // Section 3.5: a seed whose rank r' fails Eq. rank_test grows to
   // (s_r r') x (s_c r') (prefixes of the same orders) and the solve repeats,
@@ -452,11 +495,68 @@ extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
   return st;
 }
 
+// Device buffers, copy stream and events of host-buffer solves.
+static pcp_status ensure_host_buffers(pcp_plan* P, bool want_S) {
+  const size_t mn = sizeof(float) * (size_t)P->m * (size_t)P->n;
+  if (!P->hd_M) {
+    PCP_CUDA(cudaMalloc(&P->hd_M, mn));
+    PCP_CUDA(cudaMalloc(&P->hd_Lu, sizeof(float) * (size_t)P->m * P->r));
+    PCP_CUDA(cudaMalloc(&P->hd_Lv, sizeof(float) * (size_t)P->n * P->r));
+    PCP_CUDA(cudaStreamCreateWithFlags(&P->copy_st, cudaStreamNonBlocking));
+    for (auto& ev : P->cev)
+      PCP_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  if (want_S && !P->hd_S) PCP_CUDA(cudaMalloc(&P->hd_S, mn));
+  return PCP_OK;
+}
+
+extern "C" pcp_status pcp_l1filter_solve_host(pcp_plan* P, const float* hM,
+                                              int64_t ldm, float* hLu,
+                                              float* hLv, float* hS,
+                                              int64_t lds, pcp_info* info,
+                                              void* stream) {
+  PCP_ARG(P && hM && hLu && hLv, "pcp_l1filter_solve_host: null pointer");
+  PCP_ARG(ldm >= P->m, "pcp_l1filter_solve_host: ldm < m");
+  PCP_ARG(!hS || lds >= P->m, "pcp_l1filter_solve_host: lds < m");
+  pcp_status s = ensure_host_buffers(P, hS != nullptr);
+  if (s != PCP_OK) return s;
+  // a page-locked M is read in place by the seed gather (the device reads
+  // host memory directly), so the seed need not wait for the whole copy
+  HostIO io{hM, nullptr, ldm, hLu, hLv, hS, lds};
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, hM) == cudaSuccess &&
+      pa.type == cudaMemoryTypeHost && pa.devicePointer)
+    io.gM = static_cast<const float*>(pa.devicePointer);
+  else
+    cudaGetLastError();  // pageable memory: clear the query's error
+  cudaStream_t st = (cudaStream_t)stream;
+  pcp_status r = solve_once(P, P->hd_M, P->m, P->hd_Lu, P->hd_Lv,
+                            hS ? P->hd_S : nullptr, P->m, nullptr, nullptr,
+                            info, stream, &io);
+  if (r == PCP_ERR_RANK_TEST && info && P->p.grow_seed) {
+    // Section 3.5 growth on the data already on the device, then the
+    // grown solve's outputs back to the host
+    r = grow_loop(P, P->hd_M, P->m, P->hd_Lu, P->hd_Lv,
+                  hS ? P->hd_S : nullptr, P->m, nullptr, nullptr, info,
+                  stream, r);
+    PCP_CUDA(cudaMemcpyAsync(hLu, P->hd_Lu, sizeof(float) * P->m * P->r,
+                             cudaMemcpyDeviceToHost, st));
+    PCP_CUDA(cudaMemcpyAsync(hLv, P->hd_Lv, sizeof(float) * P->n * P->r,
+                             cudaMemcpyDeviceToHost, st));
+    if (hS)
+      PCP_CUDA(cudaMemcpy2DAsync(hS, sizeof(float) * lds, P->hd_S,
+                                 sizeof(float) * P->m, sizeof(float) * P->m,
+                                 P->n, cudaMemcpyDeviceToHost, st));
+    PCP_CUDA(cudaStreamSynchronize(st));
+  }
+  return r;
+}
+
 static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
                              float* dLu, float* dLv, float* dS, int64_t lds,
                              int64_t* h_seed_rows_out,
                              int64_t* h_seed_cols_out, pcp_info* info,
-                             void* stream) {
+                             void* stream, const HostIO* hio) {
   PCP_ARG(P, "pcp_l1filter_solve: null plan");
   PCP_ARG(dM && dLu && dLv, "pcp_l1filter_solve: null pointer");
   PCP_ARG(ldm >= P->m, "pcp_l1filter_solve: ldm < m");
@@ -472,10 +572,27 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
   const bool timed = info != nullptr;
   if (timed) PCP_CUDA(cudaEventRecord(P->ev[0], st));
 
-  // stage 1: gather the seed (FP64) and count non-finite entries
+  // host buffers: M goes to the device on the copy stream (after whatever
+  // this stream still runs on the device copy), overlapping the seed
+  cudaEvent_t* cev = P->cev;
+  if (hio) {
+    PCP_CUDA(cudaEventRecord(cev[0], st));
+    PCP_CUDA(cudaStreamWaitEvent(P->copy_st, cev[0], 0));
+    PCP_CUDA(cudaMemcpy2DAsync(
+        const_cast<float*>(dM), sizeof(float) * ldm, hio->hM,
+        sizeof(float) * hio->ldm, sizeof(float) * P->m, P->n,
+        cudaMemcpyHostToDevice, P->copy_st));
+    PCP_CUDA(cudaEventRecord(cev[1], P->copy_st));
+    if (!hio->gM) PCP_CUDA(cudaStreamWaitEvent(st, cev[1], 0));
+  }
+  // stage 1: gather the seed (FP64) and count non-finite entries (from the
+  // page-locked host M itself when the device can read it)
   PCP_CUDA(cudaMemsetAsync(P->d_bad, 0, sizeof(int32_t), st));
-  s = pcp::gather_seed(dM, ldm, P->d_rows, P->mp, P->d_cols, P->np, P->d_Ms,
-                       P->d_bad, st);
+  s = (hio && hio->gM)
+          ? pcp::gather_seed(hio->gM, hio->ldm, P->d_rows, P->mp, P->d_cols,
+                             P->np, P->d_Ms, P->d_bad, st)
+          : pcp::gather_seed(dM, ldm, P->d_rows, P->mp, P->d_cols, P->np,
+                             P->d_Ms, P->d_bad, st);
   if (s != PCP_OK) return s;
   // stage 2: seed PCP (FP64)
   int* d_rank = nullptr;
@@ -491,6 +608,7 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
                            P->n, P->d_U32, P->d_V32, P->d_inv_sigma, st);
   if (s != PCP_OK) return s;
   if (timed) PCP_CUDA(cudaEventRecord(P->ev[1], st));
+  if (hio) PCP_CUDA(cudaStreamWaitEvent(st, cev[1], 0));  // all of M landed
   // stages 3 and 4: column and row filtering (Algorithm 1)
   const int64_t ncb = P->n - P->np, nrb = P->m - P->mp;
   s = pcp_l1_filter(dM, P->d_rows, P->mp, 1, P->d_cbar, (int32_t)ncb, ldm,
@@ -506,11 +624,42 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
                     q.lowp_iters, P->d_iters + ncb, st);
   if (s != PCP_OK) return s;
   if (timed) PCP_CUDA(cudaEventRecord(P->ev[2], st));
-  // stage 6: S = M - Lu Lv^T
-  if (dS) {
+  if (hio) {
+    // the factors go back while the S pass runs
+    PCP_CUDA(cudaEventRecord(cev[2], st));
+    PCP_CUDA(cudaStreamWaitEvent(P->copy_st, cev[2], 0));
+    PCP_CUDA(cudaMemcpyAsync(hio->hLu, dLu, sizeof(float) * P->m * P->r,
+                             cudaMemcpyDeviceToHost, P->copy_st));
+    PCP_CUDA(cudaMemcpyAsync(hio->hLv, dLv, sizeof(float) * P->n * P->r,
+                             cudaMemcpyDeviceToHost, P->copy_st));
+  }
+  // stage 6: S = M - Lu Lv^T (host buffers: in column chunks of a multiple
+  // of 64 columns, each chunk's S copied back while the next is computed)
+  if (dS && hio) {
+    const int64_t w = std::max<int64_t>(
+        64, (P->n + kHostChunks - 1) / kHostChunks / 64 * 64 + 64);
+    int c = 0;
+    for (int64_t j0 = 0; j0 < P->n; j0 += w, ++c) {
+      const int64_t nc = std::min(w, P->n - j0);
+      s = pcp_spass(dM + j0 * ldm, ldm, dLu, P->m, dLv + j0, P->n, P->r,
+                    dS + j0 * lds, lds, P->m, nc, st);
+      if (s != PCP_OK) return s;
+      PCP_CUDA(cudaEventRecord(cev[4 + c], st));
+      PCP_CUDA(cudaStreamWaitEvent(P->copy_st, cev[4 + c], 0));
+      PCP_CUDA(cudaMemcpy2DAsync(hio->hS + j0 * hio->lds,
+                                 sizeof(float) * hio->lds, dS + j0 * lds,
+                                 sizeof(float) * lds, sizeof(float) * P->m,
+                                 nc, cudaMemcpyDeviceToHost, P->copy_st));
+    }
+  } else if (dS) {
     s = pcp_spass(dM, ldm, dLu, P->m, dLv, P->n, P->r, dS, lds, P->m, P->n,
                   st);
     if (s != PCP_OK) return s;
+  }
+  if (hio) {
+    // this stream's later work (and its synchronisation) follows the copies
+    PCP_CUDA(cudaEventRecord(cev[3], P->copy_st));
+    PCP_CUDA(cudaStreamWaitEvent(st, cev[3], 0));
   }
   if (!timed) return PCP_OK;
   PCP_CUDA(cudaEventRecord(P->ev[3], st));
