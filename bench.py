@@ -50,6 +50,8 @@ FLUSH_BYTES = 256 << 20
 # kernel code on the same workload (profiles/ holds the summaries and the
 # commands); a kernel changed since its capture gets no entry.
 TRAFFIC = {
+    ("c2_5000_r20", "seed"): (
+        957696, "profiles/seed_alm_kernel_c2_5000_r20.md"),
     ("c2_5000_r20", "spass"): (
         158809600, "profiles/spass_tc_kernel_c2_5000_r20.md"),
     ("c3_20000_r50", "spass"): (
