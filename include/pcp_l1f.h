@@ -226,6 +226,15 @@ pcp_status pcp_l1filter_solve(pcp_plan* plan, const float* dM, int64_t ldm,
  * (with info, t_spass_ms includes the last copies of S).  Without info the
  * call returns before the copies finish: synchronise `stream` before
  * reading the outputs or reusing hM. */
+/* Asynchronous solves (info == NULL, either call above) run as a CUDA graph:
+ * the first call on a plan runs directly, the second with the same buffers
+ * (device pointers and leading dimensions, or host pointers) is captured
+ * into a graph of its launches and copies and later calls with the same
+ * buffers replay it on `stream`; other buffers are captured anew.  A solve
+ * that cannot be captured runs directly and graphs stay off for that plan.
+ * Returns the number of graph launches so far, or -1 when graphs are off. */
+int64_t pcp_plan_graph_launches(const pcp_plan* plan);
+
 pcp_status pcp_l1filter_solve_host(pcp_plan* plan, const float* hM,
                                    int64_t ldm, float* hLu, float* hLv,
                                    float* hS, int64_t lds, pcp_info* info,

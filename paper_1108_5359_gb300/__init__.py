@@ -23,6 +23,7 @@ __all__ = [
     "PCPError", "PCPInfo", "PCPParams", "PCP_FP32", "PCP_BF16_REFINED",
     "colmajor", "pcp_params_default", "pcp_l1filter_plan",
     "pcp_l1filter_solve", "pcp_l1filter_solve_host", "pcp_plan_destroy",
+    "pcp_plan_graph_launches",
     "pcp_gather_seed",
     "pcp_seed_workspace_bytes", "pcp_seed_pcp", "pcp_seed_pcp_static",
     "pcp_l1_filter",
@@ -173,6 +174,11 @@ def pcp_l1filter_solve(plan: Plan, M, Lu, Lv, S=None, info=True,
     if raise_on_error and st not in (PCP_OK,):
         check(st, "pcp_l1filter_solve")
     return st, inf, rows, cols
+
+
+def pcp_plan_graph_launches(plan: Plan) -> int:
+    """CUDA-graph replays of asynchronous solves on this plan (-1: off)."""
+    return int(load().pcp_plan_graph_launches(plan.handle))
 
 
 def pcp_l1filter_solve_host(plan: Plan, M, Lu, Lv, S=None, info=True,

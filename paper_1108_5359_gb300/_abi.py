@@ -135,6 +135,7 @@ PROTOTYPES = {
                                     _vp, _vp]),
     "pcp_spass": (_i32, [_vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _i64,
                          _i64, _i64, _vp]),
+    "pcp_plan_graph_launches": (_i64, [_vp]),
     "pcp_l1filter_solve_host": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64,
                                        _vp, _vp]),
     "pcp_spass_impl": (_i32, [_vp, _i64, _vp, _i64, _vp, _i64, _i32, _vp,

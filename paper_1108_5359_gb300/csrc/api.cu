@@ -147,6 +147,14 @@ struct pcp_plan {
   float *hd_M = nullptr, *hd_S = nullptr, *hd_Lu = nullptr, *hd_Lv = nullptr;
   cudaStream_t copy_st = nullptr;
   cudaEvent_t cev[kHostEvents] = {};
+  // asynchronous solves (info == NULL) replay a CUDA graph of the solve's
+  // launches and copies, captured on the second call with the same buffers
+  cudaStream_t cap_st = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uintptr_t> gkey;
+  int async_calls = 0;
+  int64_t graph_launches = 0;
+  bool graph_off = false;
 };
 
 extern "C" const char* pcp_last_error(void) { return pcp::g_err; }
@@ -365,6 +373,8 @@ extern "C" void pcp_plan_destroy(pcp_plan* P) {
   for (auto& ev : P->cev)
     if (ev) cudaEventDestroy(ev);
   if (P->copy_st) cudaStreamDestroy(P->copy_st);
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->cap_st) cudaStreamDestroy(P->cap_st);
   cudaFree(P->hd_M);
   cudaFree(P->hd_S);
   cudaFree(P->hd_Lu);
@@ -446,12 +456,84 @@ static pcp_status grow_loop(pcp_plan* P, const float* dM, int64_t ldm,
                             int64_t* h_seed_cols_out, pcp_info* info,
                             void* stream, pcp_status st);
 
+// Asynchronous solves through a CUDA graph: the first call runs directly
+// (it settles the filter autotuner and any first-use allocation), the
+// second with the same buffers is captured on the plan's capture stream and
+// instantiated, and later calls with the same buffers replay the graph on
+// the caller's stream.  A solve that cannot be captured (pageable host
+// memory, an index upload that has to synchronise) runs directly and turns
+// graphs off for the plan.
+template <typename Run>
+static pcp_status solve_async(pcp_plan* P, std::vector<uintptr_t> key,
+                              void* stream, Run run) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (P->graph_off || P->async_calls++ == 0) return run(st);
+  if (P->gexec && key == P->gkey) {
+    PCP_CUDA(cudaGraphLaunch(P->gexec, st));
+    ++P->graph_launches;
+    return PCP_OK;
+  }
+  if (!P->cap_st)
+    PCP_CUDA(cudaStreamCreateWithFlags(&P->cap_st, cudaStreamNonBlocking));
+  // the capture stream must not start before the caller's earlier work
+  // when the captured work is replayed: the graph is launched on `st`, so
+  // ordering is by the launch; nothing is enqueued on cap_st outside capture
+  if (cudaStreamBeginCapture(P->cap_st, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    P->graph_off = true;
+    return run(st);
+  }
+  pcp_status s = run(P->cap_st);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(P->cap_st, &g);
+  cudaGraphExec_t ex = nullptr;
+  const bool ok = s == PCP_OK && e == cudaSuccess && g &&
+                  cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    if (ex) cudaGraphExecDestroy(ex);
+    P->graph_off = true;
+    return run(st);
+  }
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  P->gexec = ex;
+  P->gkey = std::move(key);
+  PCP_CUDA(cudaGraphLaunch(P->gexec, st));
+  ++P->graph_launches;
+  return PCP_OK;
+}
+
+extern "C" int64_t pcp_plan_graph_launches(const pcp_plan* P) {
+  if (!P) return 0;
+  return P->graph_off ? -1 : P->graph_launches;
+}
+
 extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
                                          int64_t ldm, float* dLu, float* dLv,
                                          float* dS, int64_t lds,
                                          int64_t* h_seed_rows_out,
                                          int64_t* h_seed_cols_out,
                                          pcp_info* info, void* stream) {
+  if (P && !info) {
+    if (h_seed_rows_out || h_seed_cols_out) {
+      pcp_status s0 = upload_indices(P, (cudaStream_t)stream);
+      if (s0 != PCP_OK) return s0;
+      if (h_seed_rows_out)
+        std::copy(P->cur_rows.begin(), P->cur_rows.end(), h_seed_rows_out);
+      if (h_seed_cols_out)
+        std::copy(P->cur_cols.begin(), P->cur_cols.end(), h_seed_cols_out);
+    }
+    return solve_async(
+        P,
+        {(uintptr_t)dM, (uintptr_t)ldm, (uintptr_t)dLu, (uintptr_t)dLv,
+         (uintptr_t)dS, (uintptr_t)lds},
+        stream, [&](cudaStream_t s) {
+          return solve_once(P, dM, ldm, dLu, dLv, dS, lds, nullptr, nullptr,
+                            nullptr, s);
+        });
+  }
   pcp_status st = solve_once(P, dM, ldm, dLu, dLv, dS, lds, h_seed_rows_out,
                              h_seed_cols_out, info, stream);
   return grow_loop(P, dM, ldm, dLu, dLv, dS, lds, h_seed_rows_out,
@@ -530,6 +612,16 @@ extern "C" pcp_status pcp_l1filter_solve_host(pcp_plan* P, const float* hM,
   else
     cudaGetLastError();  // pageable memory: clear the query's error
   cudaStream_t st = (cudaStream_t)stream;
+  if (!info)
+    return solve_async(
+        P,
+        {1, (uintptr_t)hM, (uintptr_t)ldm, (uintptr_t)hLu, (uintptr_t)hLv,
+         (uintptr_t)hS, (uintptr_t)lds, (uintptr_t)io.gM},
+        stream, [&](cudaStream_t s) {
+          return solve_once(P, P->hd_M, P->m, P->hd_Lu, P->hd_Lv,
+                            hS ? P->hd_S : nullptr, P->m, nullptr, nullptr,
+                            nullptr, s, &io);
+        });
   pcp_status r = solve_once(P, P->hd_M, P->m, P->hd_Lu, P->hd_Lv,
                             hS ? P->hd_S : nullptr, P->m, nullptr, nullptr,
                             info, stream, &io);

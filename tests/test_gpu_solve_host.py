@@ -115,3 +115,45 @@ def test_host_solve_grows_the_seed():
     L = hLu.numpy().astype(np.float64) @ hLv.numpy().astype(np.float64).T
     assert relerr(L, L0) < 1e-5
     assert relerr(hS.numpy().astype(np.float64), S0) < 1e-5
+
+
+def test_async_solves_replay_a_graph_with_the_same_results():
+    # without info the second call with the same buffers is captured into a
+    # CUDA graph and later calls replay it; new buffers are captured anew
+    import torch
+    import paper_1108_5359_gb300 as pk
+    build_and_load()
+    P = synth.make_config("c1_500_r5", seed=6, m=900, n=700, r=6)
+    M32 = P.M.astype(np.float32)
+    Lu_d, Lv_d, S_d = _device_solve(P, M32)
+    plan = pk.Plan(pk.pcp_params_default(P.m, P.n, P.r), P.rows, P.cols)
+    dM = to_dev_cm(M32)
+    for bufset in range(2):
+        Lu, Lv = pk.colmajor(P.m, P.r), pk.colmajor(P.n, P.r)
+        S = pk.colmajor(P.m, P.n)
+        for _ in range(4):
+            Lu.fill_(float("nan"))
+            S.fill_(float("nan"))
+            st, inf, _, _ = pk.pcp_l1filter_solve(plan, dM, Lu, Lv, S,
+                                                  info=False)
+            assert st == 0 and inf is None
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(to_host(Lu), Lu_d)
+            np.testing.assert_array_equal(to_host(Lv), Lv_d)
+            np.testing.assert_array_equal(to_host(S), S_d)
+    # calls 2..4 of the first buffer set and 1..4 of the second replayed
+    assert pk.pcp_plan_graph_launches(plan) == 7
+    # host buffers, asynchronous, replayed
+    hM = _host_cm(M32)
+    hLu, hLv = _host_cm(np.zeros((P.m, P.r))), _host_cm(np.zeros((P.n, P.r)))
+    hS = _host_cm(np.zeros((P.m, P.n)))
+    for _ in range(4):
+        hS.fill_(float("nan"))
+        st, _ = pk.pcp_l1filter_solve_host(plan, hM, hLu, hLv, hS, info=False)
+        assert st == 0
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(hLu.numpy(), Lu_d)
+        np.testing.assert_array_equal(hLv.numpy(), Lv_d)
+        assert relerr(hS.numpy().astype(np.float64), S_d) < 1e-6
+    assert pk.pcp_plan_graph_launches(plan) == 11
+    plan.close()
