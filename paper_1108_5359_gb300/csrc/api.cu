@@ -150,6 +150,10 @@ struct pcp_plan {
   // asynchronous solves (info == NULL) replay a CUDA graph of the solve's
   // launches and copies, captured on the second call with the same buffers
   cudaStream_t cap_st = nullptr;
+  // the row filter runs on a second stream beside the column filter (the
+  // two launches are independent; together they fill the last wave)
+  cudaStream_t side_st = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<uintptr_t> gkey;
   int async_calls = 0;
@@ -359,6 +363,15 @@ extern "C" pcp_status pcp_l1filter_plan(const pcp_params* params,
       return pcp::cuda_fail(e, "cudaEventCreate", __FILE__, __LINE__);
     }
   }
+  if ((e = cudaStreamCreateWithFlags(&P->side_st, cudaStreamNonBlocking)) !=
+          cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&P->fork_ev, cudaEventDisableTiming)) !=
+          cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&P->join_ev, cudaEventDisableTiming)) !=
+          cudaSuccess) {
+    pcp_plan_destroy(P);
+    return pcp::cuda_fail(e, "plan streams", __FILE__, __LINE__);
+  }
   *out = P;
   return PCP_OK;
 }
@@ -375,6 +388,9 @@ extern "C" void pcp_plan_destroy(pcp_plan* P) {
   if (P->copy_st) cudaStreamDestroy(P->copy_st);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->cap_st) cudaStreamDestroy(P->cap_st);
+  if (P->side_st) cudaStreamDestroy(P->side_st);
+  if (P->fork_ev) cudaEventDestroy(P->fork_ev);
+  if (P->join_ev) cudaEventDestroy(P->join_ev);
   cudaFree(P->hd_M);
   cudaFree(P->hd_S);
   cudaFree(P->hd_Lu);
@@ -701,8 +717,11 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
   if (s != PCP_OK) return s;
   if (timed) PCP_CUDA(cudaEventRecord(P->ev[1], st));
   if (hio) PCP_CUDA(cudaStreamWaitEvent(st, cev[1], 0));  // all of M landed
-  // stages 3 and 4: column and row filtering (Algorithm 1)
+  // stages 3 and 4: column and row filtering (Algorithm 1), the row filter
+  // on the plan's second stream so that both launches share the GPU
   const int64_t ncb = P->n - P->np, nrb = P->m - P->mp;
+  PCP_CUDA(cudaEventRecord(P->fork_ev, st));
+  PCP_CUDA(cudaStreamWaitEvent(P->side_st, P->fork_ev, 0));
   s = pcp_l1_filter(dM, P->d_rows, P->mp, 1, P->d_cbar, (int32_t)ncb, ldm,
                     P->d_U32, P->mp, P->r, d_rank, nullptr, dLv, P->n,
                     q.filter_tol, q.filter_rho, q.beta0_scale,
@@ -713,8 +732,10 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
                     P->d_V32, P->np, P->r, d_rank, P->d_inv_sigma, dLu, P->m,
                     q.filter_tol, q.filter_rho, q.beta0_scale,
                     q.beta_bar_ratio, q.filter_max_iter, q.precision,
-                    q.lowp_iters, P->d_iters + ncb, st);
+                    q.lowp_iters, P->d_iters + ncb, P->side_st);
   if (s != PCP_OK) return s;
+  PCP_CUDA(cudaEventRecord(P->join_ev, P->side_st));
+  PCP_CUDA(cudaStreamWaitEvent(st, P->join_ev, 0));
   if (timed) PCP_CUDA(cudaEventRecord(P->ev[2], st));
   if (hio) {
     // the factors go back while the S pass runs
