@@ -13,16 +13,19 @@
 // range of tiles in row-block-major order, processed by a warp-specialised
 // pipeline whose stages hand over through mbarriers:
 //   * warp 0 (one thread): TMA loads of M tiles into an NS-stage ring;
-//   * warps 2-3: operand producers: the 128 x K split Lu rows of the current
-//     row block (A, rewritten when the row block changes, after the MMAs of
-//     the previous tile are done) and the 64 x K split Lv rows of each tile
-//     (B, double-buffered);
+//   * warps 2-3 and 8-9: operand producers: the 128 x K split Lu rows of
+//     the current row block (A, rewritten when the row block changes, after
+//     the MMAs of the previous tile are done) and the 64 x K split Lv rows
+//     of each tile (B, double-buffered; the next tile's loads are issued
+//     before the wait for a free buffer);
 //   * warp 1 (one thread; the warp owns the TMEM allocation): 3 K/8
 //     tcgen05.mma per tile into one of two 64-column accumulators, committed
 //     to barriers that free the B buffer and hand the accumulator on;
 //   * warps 4-7: epilogue: tcgen05.ld of the accumulator (warp 4 + q reads
 //     lanes 32 q ..), S = M - L in place in the stage, one thread issues the
 //     TMA store and frees the stage once the store has read it.
+// M loads and S stores carry an L2 evict-first policy so that the factor
+// rows, which every CTA reads, stay in L2.
 // Operands use the no-swizzle K-major layout: a core matrix is 8 rows x 16
 // bytes stored contiguously; the 8-row groups of a k-group are adjacent
 // (stride 128 B) and k-groups follow each other (stride rows x 16 B), which
