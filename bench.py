@@ -107,6 +107,28 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(seed, rank):
+    """Each rank solves its own instance (weak scaling, no data exchange)."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x, device=None):
+    """The slowest rank's time (every rank gets it); x itself at N=1."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or \
+            dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws, entries_per_rank, t_ms):
+    """Whole-job throughput: entries all ranks recovered / slowest rank."""
+    return ws * entries_per_rank / (t_ms * 1e-3)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -317,7 +339,7 @@ def run_ours(args):
     pk.load()
 
     large = args.workload == "large"
-    pseed = args.seed + 1000 * rank
+    pseed = rank_seed(args.seed, rank)
     P, M32 = make_problem(pseed, args.small, large, args.size)
     m, n, r = P.m, P.n, P.r
     mn = m * n
@@ -367,12 +389,8 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    t_step = statistics.mean(step_ms)
-    if ws > 1:
-        tt = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
-    value = ws * mn / (t_step * 1e-3)
+    t_step = max_over_ranks(statistics.mean(step_ms), dev)
+    value = job_value(ws, mn, t_step)
     last_info = info.as_dict()
 
     # parity of the last solve: exact recovery of the generated L0, S0
@@ -407,12 +425,8 @@ def run_ours(args):
             e1.synchronize()
             if it >= max(3, args.warmup):
                 e_ms.append(e0.elapsed_time(e1))
-        te = statistics.mean(e_ms)
-        if ws > 1:
-            tt = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": ws * mn / (te * 1e-3), "unit": "entries/s",
+        te = max_over_ranks(statistics.mean(e_ms), dev)
+        e2e = {"value": job_value(ws, mn, te), "unit": "entries/s",
                "ms_per_step": te, "h2d_bytes_per_step": 4 * mn,
                "d2h_bytes_per_step": 4 * mn + 4 * r * (m + n)}
 
