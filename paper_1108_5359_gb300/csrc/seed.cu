@@ -869,7 +869,7 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
           }
           __syncthreads();
           const int ns = s_nsub, nsp = (ns + 1) & ~1;
-          cluster = ns <= 24 && 2 * ns <= k && 3 * nsp * nsp <= kmax * kmax;
+          cluster = ns <= 32 && 2 * ns <= k && 3 * nsp * nsp <= kmax * kmax;
         }
         if (fast || cluster) {
           for (int idx = tid; idx < k * k; idx += kSeedThreads) {
