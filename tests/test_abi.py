@@ -99,3 +99,36 @@ def test_batch_and_serve_validate_without_gpu(lib):
     assert lib.pcp_serve_destroy(None) == _abi.PCP_OK
     assert lib.pcp_serve_poll(None, 1, None) == _abi.PCP_ERR_ARG
     assert lib.pcp_serve_stop(None) == _abi.PCP_ERR_ARG
+
+
+def test_new_entry_points_validate_without_gpu(lib):
+    from paper_1108_5359_gb300 import _abi
+    # S-pass kernel choice: unknown choice and out-of-range rank refused
+    # before any device work; an empty matrix is a no-op
+    st = lib.pcp_spass_impl(None, 1, None, 1, None, 1, 4, None, 1, 1, 1, 7,
+                            None)
+    assert st == _abi.PCP_ERR_ARG
+    st = lib.pcp_spass_impl(None, 1, None, 1, None, 1, 65, None, 1, 1, 1, 0,
+                            None)
+    assert st == _abi.PCP_ERR_ARG
+    st = lib.pcp_spass_impl(None, 1, None, 1, None, 1, 4, None, 1, 0, 5, 2,
+                            None)
+    assert st == _abi.PCP_OK
+    # host-buffer solve: null plan / buffers refused
+    st = lib.pcp_l1filter_solve_host(None, None, 1, None, None, None, 1,
+                                     None, None)
+    assert st == _abi.PCP_ERR_ARG
+    assert lib.pcp_plan_graph_launches(None) == 0
+
+
+def test_precision_forms_of_algorithm_1(lib):
+    from paper_1108_5359_gb300 import _abi
+    # every built precision passes validation (N = 0: no launch); the
+    # reserved FP64 form reports PCP_ERR_UNSUPPORTED
+    for prec, want in [(0, _abi.PCP_OK), (1, _abi.PCP_OK), (2, _abi.PCP_OK),
+                       (3, _abi.PCP_ERR_UNSUPPORTED), (4, _abi.PCP_OK),
+                       (5, _abi.PCP_OK), (6, _abi.PCP_ERR_ARG)]:
+        st = lib.pcp_l1_filter(None, None, 16, 1, None, 0, 1, None, 16, 4,
+                               None, None, None, 1, 1e-6, 1.5, 1.0, 1e10, 10,
+                               prec, 4, None, None)
+        assert st == want, (prec, st)
