@@ -51,7 +51,7 @@ FLUSH_BYTES = 256 << 20
 # commands); a kernel changed since its capture gets no entry.
 TRAFFIC = {
     ("c2_5000_r20", "seed"): (
-        957696, "profiles/seed_alm_kernel_c2_5000_r20.md"),
+        958720, "profiles/seed_alm_kernel_c2_5000_r20.md"),
     ("c2_5000_r20", "spass"): (
         158809600, "profiles/spass_tc_kernel_c2_5000_r20.md"),
     ("c3_20000_r50", "spass"): (
