@@ -212,8 +212,8 @@ pcp_status pcp_l1filter_solve(pcp_plan* plan, const float* dM, int64_t ldm,
                               int64_t* h_seed_cols_out, pcp_info* info,
                               void* stream);
 
-/* pcp_l1filter_solve on host buffers, with the copies overlapped with the
- * compute.  hM (m x n, ldm >= m) is host memory; page-locked memory
+/* pcp_l1filter_solve (Algorithm 2) on host buffers, with the copies
+ * overlapped with the compute.  hM (m x n, ldm >= m) is host memory; page-locked memory
  * (cudaHostAlloc / cudaHostRegister) is read in place by the seed gather so
  * the seed starts while M is still being copied, and the copies run
  * asynchronously; pageable memory works with the copies serialised.
@@ -226,6 +226,11 @@ pcp_status pcp_l1filter_solve(pcp_plan* plan, const float* dM, int64_t ldm,
  * (with info, t_spass_ms includes the last copies of S).  Without info the
  * call returns before the copies finish: synchronise `stream` before
  * reading the outputs or reusing hM. */
+pcp_status pcp_l1filter_solve_host(pcp_plan* plan, const float* hM,
+                                   int64_t ldm, float* hLu, float* hLv,
+                                   float* hS, int64_t lds, pcp_info* info,
+                                   void* stream);
+
 /* Asynchronous solves (info == NULL, either call above) run as a CUDA graph:
  * the first call on a plan runs directly, the second with the same buffers
  * (device pointers and leading dimensions, or host pointers) is captured
@@ -234,11 +239,6 @@ pcp_status pcp_l1filter_solve(pcp_plan* plan, const float* dM, int64_t ldm,
  * that cannot be captured runs directly and graphs stay off for that plan.
  * Returns the number of graph launches so far, or -1 when graphs are off. */
 int64_t pcp_plan_graph_launches(const pcp_plan* plan);
-
-pcp_status pcp_l1filter_solve_host(pcp_plan* plan, const float* hM,
-                                   int64_t ldm, float* hLu, float* hLv,
-                                   float* hS, int64_t lds, pcp_info* info,
-                                   void* stream);
 
 void pcp_plan_destroy(pcp_plan* plan);
 
