@@ -595,15 +595,18 @@ static pcp_status grow_loop(pcp_plan* P, const float* dM, int64_t ldm,
 
 // Device buffers, copy stream and events of host-buffer solves.
 static pcp_status ensure_host_buffers(pcp_plan* P, bool want_S) {
+  // each resource on its own, so a call after a failed allocation retries
+  // only what is missing
   const size_t mn = sizeof(float) * (size_t)P->m * (size_t)P->n;
-  if (!P->hd_M) {
-    PCP_CUDA(cudaMalloc(&P->hd_M, mn));
+  if (!P->hd_M) PCP_CUDA(cudaMalloc(&P->hd_M, mn));
+  if (!P->hd_Lu)
     PCP_CUDA(cudaMalloc(&P->hd_Lu, sizeof(float) * (size_t)P->m * P->r));
+  if (!P->hd_Lv)
     PCP_CUDA(cudaMalloc(&P->hd_Lv, sizeof(float) * (size_t)P->n * P->r));
+  if (!P->copy_st)
     PCP_CUDA(cudaStreamCreateWithFlags(&P->copy_st, cudaStreamNonBlocking));
-    for (auto& ev : P->cev)
-      PCP_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  }
+  for (auto& ev : P->cev)
+    if (!ev) PCP_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   if (want_S && !P->hd_S) PCP_CUDA(cudaMalloc(&P->hd_S, mn));
   return PCP_OK;
 }
