@@ -15,12 +15,14 @@ import ctypes as C
 
 from . import _abi
 from ._abi import (PCPError, PCPInfo, PCPParams, PCPProblem,
-                   PCP_BF16_REFINED, PCP_ERR_BUSY, PCP_FP32, PCP_OK,
+                   PCP_BF16_REFINED, PCP_ERR_BUSY, PCP_FP32, PCP_FP32_SIMT,
+                   PCP_FP32_TENSOR, PCP_OK, PCP_TF32_REFINED,
                    PCP_SPASS_AUTO, PCP_SPASS_SIMT, PCP_SPASS_TENSOR, check,
                    load)
 
 __all__ = [
     "PCPError", "PCPInfo", "PCPParams", "PCP_FP32", "PCP_BF16_REFINED",
+    "PCP_TF32_REFINED", "PCP_FP32_TENSOR", "PCP_FP32_SIMT",
     "colmajor", "pcp_params_default", "pcp_l1filter_plan",
     "pcp_l1filter_solve", "pcp_l1filter_solve_host", "pcp_plan_destroy",
     "pcp_plan_graph_launches",

@@ -121,14 +121,14 @@ __device__ __forceinline__ void tc_prep(TcFrag& f, const float (&a)[4]) {
   if (kMode == kOneBf16) {
     f.h[0] = pack_bf16(a[0], a[2]);
     f.h[1] = pack_bf16(a[1], a[3]);
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (kMode == kSplitTf32)
-      split_tf32(a[q], f.h[q], f.l[q]);
-    else
-      f.h[q] = tf32_rna(a[q]);
+    for (int q = 0; q < 4; ++q) {
+      if (kMode == kSplitTf32)
+        split_tf32(a[q], f.h[q], f.l[q]);
+      else
+        f.h[q] = tf32_rna(a[q]);
+    }
   }
 }
 
