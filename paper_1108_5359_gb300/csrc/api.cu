@@ -476,9 +476,9 @@ static pcp_status grow_loop(pcp_plan* P, const float* dM, int64_t ldm,
 // (it settles the filter autotuner and any first-use allocation), the
 // second with the same buffers is captured on the plan's capture stream and
 // instantiated, and later calls with the same buffers replay the graph on
-// the caller's stream.  A solve that cannot be captured (pageable host
-// memory, an index upload that has to synchronise) runs directly and turns
-// graphs off for the plan.
+// the caller's stream.  A solve that cannot be captured (an index upload
+// that has to synchronise, or anything the driver refuses to capture) runs
+// directly and turns graphs off for the plan.
 template <typename Run>
 static pcp_status solve_async(pcp_plan* P, std::vector<uintptr_t> key,
                               void* stream, Run run) {

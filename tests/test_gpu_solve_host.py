@@ -157,3 +157,29 @@ def test_async_solves_replay_a_graph_with_the_same_results():
         assert relerr(hS.numpy().astype(np.float64), S_d) < 1e-6
     assert pk.pcp_plan_graph_launches(plan) == 11
     plan.close()
+
+
+def test_pageable_host_buffers_give_the_same_results():
+    # pageable memory: the seed cannot read M in place and the copies are
+    # synchronous for the host; whether the driver captures them into the
+    # graph (replays) or not (graphs off, -1), the results are the same
+    import torch
+    import paper_1108_5359_gb300 as pk
+    build_and_load()
+    P = synth.make_config("c1_500_r5", seed=6, m=700, n=520, r=6)
+    M32 = P.M.astype(np.float32)
+    Lu_d, Lv_d, S_d = _device_solve(P, M32)
+    plan = pk.Plan(pk.pcp_params_default(P.m, P.n, P.r), P.rows, P.cols)
+    hM = _host_cm(M32, pin=False)
+    hLu = _host_cm(np.zeros((P.m, P.r)), pin=False)
+    hLv = _host_cm(np.zeros((P.n, P.r)), pin=False)
+    hS = _host_cm(np.zeros((P.m, P.n)), pin=False)
+    for _ in range(3):
+        st, _ = pk.pcp_l1filter_solve_host(plan, hM, hLu, hLv, hS, info=False)
+        assert st == 0
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(hLu.numpy(), Lu_d)
+        np.testing.assert_array_equal(hLv.numpy(), Lv_d)
+        assert relerr(hS.numpy().astype(np.float64), S_d) < 1e-6
+    assert pk.pcp_plan_graph_launches(plan) in (-1, 2)
+    plan.close()
