@@ -98,7 +98,8 @@ typedef struct pcp_params {
   double rank_cut;          /* singular values of L^s below rank_cut * the
                                largest are dropped, default 1e-6 (the seed is
                                resolved only to ~1e-7 of its norm) */
-  double filter_tol;        /* epsilon of Algorithm 1, default 3e-7 */
+  double filter_tol;        /* epsilon of Algorithm 1's stop test (see
+                               pcp_l1_filter), default 3e-6 */
   double filter_rho;        /* rho of Algorithm 1, default 1.5 */
   double beta0_scale;       /* beta_0 = beta0_scale/||x||_inf, default 1 */
   double beta_bar_ratio;    /* beta_bar = ratio * beta_0, default 1e10 */
@@ -408,6 +409,10 @@ int32_t pcp_plan_seed_trace(const pcp_plan* plan, uint64_t* h_out,
  * precision: PCP_FP32 / PCP_FP32_TENSOR (split TF32), PCP_TF32_REFINED
  * (lowp_iters one-pass TF32 iterations, then split TF32 until eps) or
  * PCP_FP32_SIMT; the stop test is only taken on FP32-accurate iterations.
+ * Stop test (FP32 reading of Algorithm 1's): a problem stops when
+ * ||x - A z - e||_inf < eps * max(||x - e||_inf, 1e-3 ||x||_inf); the paper
+ * divides by ||x||_inf, which lets the fit of x - e be as loose as
+ * eps times the largest outlier.
  * Limits: p <= 512, r <= 64 (PCP_FP32_SIMT: p <= 256, r <= 32). */
 pcp_status pcp_l1_filter(const float* dM, const int32_t* d_pidx, int32_t p,
                          int64_t sp, const int32_t* d_qidx, int32_t N,

@@ -187,7 +187,7 @@ extern "C" pcp_status pcp_params_default(pcp_params* p, int64_t m, int64_t n,
   p->seed_mu_scale = 1.25;
   p->seed_mu_max_ratio = 1e7;
   p->rank_cut = 1e-6;
-  p->filter_tol = 3e-7;
+  p->filter_tol = 3e-6;
   p->filter_rho = 1.5;
   p->beta0_scale = 1.0;
   p->beta_bar_ratio = 1e10;

@@ -61,6 +61,11 @@ __device__ __forceinline__ float shrink(float x, float eta) {
 __device__ __forceinline__ double shrink(double x, double eta) {
   return copysign(fmax(fabs(x) - eta, 0.0), x);
 }
+// The part of x that the shrinkage removes: x - S_eta(x), i.e. x clipped to
+// [-eta, eta].
+__device__ __forceinline__ float clip(float x, float eta) {
+  return fminf(fmaxf(x, -eta), eta);
+}
 
 // Largest number of CTAs the library launches per device in one
 // cooperative grid; bounds per-block scratch arrays.

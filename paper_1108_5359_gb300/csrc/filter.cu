@@ -7,14 +7,25 @@
 //   z_{k+1} = A^T (x - e_{k+1} + y_k/beta_k)
 //   y_{k+1} = y_k + beta_k (x - A z_{k+1} - e_{k+1}),
 //   beta_{k+1} = min(rho beta_k, beta_bar)
-// stopping when ||x - A z_k - e_k||_inf / ||x||_inf < eps.  Each problem runs
-// its own instance (own beta_0 = beta0_scale/||x||_inf and stop test); the
-// problems are independent (Section 3.2), which is the grid decomposition.
+// stopping when ||x - A z_k - e_k||_inf is below eps times ||x - e_k||_inf
+// (floored at kStopNormFloor ||x||_inf; the paper divides by ||x||_inf).
+// Each problem runs its own instance (own beta_0 = beta0_scale/||x||_inf and
+// stop test); the problems are independent (Section 3.2), which is the grid
+// decomposition.
+//
+// FP32 form of the same iteration: the state holds d = x - e instead of e.
+// With v = x - A z_k + y_k/beta_k and c = v - S_{1/beta_k}(v) (v clipped to
+// +-1/beta_k), e_{k+1} = v - c gives
+//   d_{k+1} = A z_k - y_k/beta_k + c,   x - e_{k+1} + y_k/beta_k = A z_k + c,
+//   residual x - A z_{k+1} - e_{k+1} = d_{k+1} - A z_{k+1},
+// so no step subtracts two copies of a large outlier: x enters only through
+// v, which is clipped.  (With e stored, an outlier of size |x_i| leaves an
+// FP32 rounding of ~|x_i| 2^-24 in z and in the residual.)
 //
 // GB300 mapping (FP32 SIMT form):
 //   * one CTA = 8 warps = 32 problems; lane l of every warp works on problem
 //     l, warp w owns the entries t = w, w+8, w+16, ... of that problem;
-//   * x, y, e of the owned entries live in registers for the whole solve,
+//   * x, y, d of the owned entries live in registers for the whole solve,
 //     A (p x r) is staged once into shared memory (row-major, zero padded to
 //     RMAX columns) and read as warp-broadcast float4;
 //   * one pass over the owned rows per iteration fuses A z (for the
@@ -63,6 +74,7 @@ __device__ __forceinline__ void adm_f32_tile(const FilterArgs& a,
   float* red = As + kWarps * SPT * RMAX;            // [kWarps][RMAX][32]
   float* zsh = red + kWarps * RMAX * 32;            // [RMAX][32]
   float* mxs = zsh + RMAX * 32;                     // [kWarps][32]
+  float* mds = mxs + kWarps * 32;                   // [kWarps][32]
 
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
@@ -79,7 +91,7 @@ __device__ __forceinline__ void adm_f32_tile(const FilterArgs& a,
   }
 
   // Load the owned entries of x_j.
-  float x[SPT], y[SPT], e[SPT];
+  float x[SPT], y[SPT], d[SPT];  // d = x - e
   const int64_t qoff = valid ? (int64_t)a.qidx[j] * a.sq : 0;
   float xm = 0.0f;
 #pragma unroll
@@ -102,8 +114,8 @@ __device__ __forceinline__ void adm_f32_tile(const FilterArgs& a,
   float beta = done ? 1.0f : a.beta0_scale * inv_xinf;
   const float beta_bar = beta * a.beta_bar_ratio;
 
-  // Iteration 1, step 1 with z_0 = 0, y_0 = 0: e_1 = S_{1/beta_0}(x);
-  // accumulate the partial products of z_1 = A^T (x - e_1).
+  // Iteration 1, step 1 with z_0 = 0, y_0 = 0: e_1 = S_{1/beta_0}(x), so
+  // d_1 = x - e_1 = clip(x, 1/beta_0); partial products of z_1 = A^T d_1.
   float acc[RMAX];
 #pragma unroll
   for (int k = 0; k < RMAX; ++k) acc[k] = 0.0f;
@@ -113,14 +125,14 @@ __device__ __forceinline__ void adm_f32_tile(const FilterArgs& a,
     for (int s = 0; s < SPT; ++s) {
       const int t = w + kWarps * s;
       if (t < p) {
-        e[s] = shrink(x[s], ib);
-        const float v = x[s] - e[s];
+        d[s] = clip(x[s], ib);
+        const float v = d[s];
         float ar[RMAX];
         load_arow<RMAX>(As, t, ar);
 #pragma unroll
         for (int k = 0; k < RMAX; ++k) acc[k] = fmaf(ar[k], v, acc[k]);
       } else {
-        e[s] = 0.0f;
+        d[s] = 0.0f;
       }
     }
   }
@@ -152,7 +164,7 @@ __device__ __forceinline__ void adm_f32_tile(const FilterArgs& a,
     // step 1 and the A^T partial products of the next iteration.
     const float bn = fminf(a.rho * beta, beta_bar);
     const float ibn = 1.0f / bn;
-    float rmax = 0.0f;
+    float rmax = 0.0f, dmax = 0.0f;
 #pragma unroll
     for (int k = 0; k < RMAX; ++k) acc[k] = 0.0f;
 #pragma unroll
@@ -164,23 +176,30 @@ __device__ __forceinline__ void adm_f32_tile(const FilterArgs& a,
         float az = 0.0f;
 #pragma unroll
         for (int k = 0; k < RMAX; ++k) az = fmaf(ar[k], z[k], az);
-        const float res = x[s] - az - e[s];
+        const float res = d[s] - az;
         rmax = fmaxf(rmax, fabsf(res));
+        dmax = fmaxf(dmax, fabsf(d[s]));
         y[s] = fmaf(beta, res, y[s]);
-        const float u = x[s] - az + y[s] * ibn;
-        e[s] = shrink(u, ibn);
-        const float v = x[s] - e[s] + y[s] * ibn;
+        const float yb = y[s] * ibn;
+        const float c = clip(x[s] - az + yb, ibn);
+        d[s] = az - yb + c;
+        const float v = az + c;
 #pragma unroll
         for (int k = 0; k < RMAX; ++k) acc[k] = fmaf(ar[k], v, acc[k]);
       }
     }
     beta = bn;
     mxs[w * 32 + lane] = rmax;
+    mds[w * 32 + lane] = dmax;
     __syncthreads();
-    float rm = 0.0f;
+    float rm = 0.0f, dm = 0.0f;
 #pragma unroll
-    for (int q = 0; q < kWarps; ++q) rm = fmaxf(rm, mxs[q * 32 + lane]);
-    const bool conv_now = !done && (rm * inv_xinf < a.eps);
+    for (int q = 0; q < kWarps; ++q) {
+      rm = fmaxf(rm, mxs[q * 32 + lane]);
+      dm = fmaxf(dm, mds[q * 32 + lane]);
+    }
+    const bool conv_now =
+        !done && (rm < a.eps * fmaxf(dm, kStopNormFloor * xinf));
     const bool out_now = conv_now || (!done && iter >= a.max_iter);
     if (out_now && w == 0) {
       const int64_t row = a.qidx[j];
@@ -217,7 +236,7 @@ template <int SPT, int RMAX>
 size_t adm_smem_bytes() {
   return sizeof(float) * ((size_t)kWarps * SPT * RMAX +
                           (size_t)kWarps * RMAX * 32 + (size_t)RMAX * 32 +
-                          (size_t)kWarps * 32);
+                          (size_t)2 * kWarps * 32);
 }
 
 template <int SPT, int RMAX>

@@ -2,8 +2,10 @@
 //
 // The same ADM steps as filter.cu (per problem: e = S_{1/beta}(x - A z +
 // y/beta), z = A^T (x - e + y/beta), y += beta (x - A z - e), beta grows by
-// rho up to beta_bar, stop when ||x - A z - e||_inf < eps ||x||_inf), with
-// the two products of every iteration on the tensor cores:
+// rho up to beta_bar, stop when ||x - A z - e||_inf < eps max(||x - e||_inf,
+// kStopNormFloor ||x||_inf)) in the same FP32 form (state d = x - e, so
+// that no step subtracts two copies of an outlier), with the two products
+// of every iteration on the tensor cores:
 //
 //   w^T (16 x p) = z^T (16 x r) A^T (r x p)     (A z for 16 problems)
 //   z^T (16 x r) = u^T (16 x p) A (p x r)       (A^T u, u = x - e + y/beta)
@@ -11,7 +13,7 @@
 // as mma.sync m16n8k8 TF32 with FP32 accumulation (problems are the M
 // dimension).  The accumulator fragment of the first product holds, per
 // thread, entries 2t and 2t+1 of problems g and g+8 (g = lane/4,
-// t = lane%4); x, y, e live in registers in exactly that layout, so the
+// t = lane%4); x, y, d live in registers in exactly that layout, so the
 // elementwise ADM step needs no data movement, and the same four values
 // are the A-operand fragment of the second product once its k index is
 // permuted (k slot t <-> entry 2t, slot t+4 <-> entry 2t+1; the B operand
@@ -152,10 +154,6 @@ __device__ __forceinline__ void mma_pre(float (&d)[4], float (&dl)[4],
   }
 }
 
-__device__ __forceinline__ float shrinkf(float v, float tau) {
-  return copysignf(fmaxf(fabsf(v) - tau, 0.0f), v);
-}
-
 // Row pitch (floats) of A and of the z buffers in shared memory: >= 8 RB
 // and = 8 mod 32, so the 64-bit fragment loads of the A z product are
 // bank-conflict free (the A^T u product's 32-bit loads see a 2-way
@@ -172,7 +170,8 @@ constexpr size_t tc_smem_bytes() {
           (size_t)kTcWarps * kTcProblems * tc_pitch<RB>() +     // z partials
           (size_t)2 * kTcProblems * tc_pitch<RB>() +            // z (x2)
           (size_t)kTcWarps * kTcProblems +                      // max |res|
-          (size_t)kTcWarps * kTcProblems);                      // max |x|
+          (size_t)kTcWarps * kTcProblems +                      // max |x|
+          (size_t)kTcWarps * kTcProblems);                      // max |d|
 }
 
 // One CTA: 16 problems (tile) of one set, 8 warps x NT tiles of 8 entries.
@@ -187,6 +186,7 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
   float* zs = zred + kTcWarps * kTcProblems * RP;    // [2][16][RP]
   float* rmx = zs + 2 * kTcProblems * RP;            // [W][16]
   float* xmx = rmx + kTcWarps * kTcProblems;         // [W][16]
+  float* dmx = xmx + kTcWarps * kTcProblems;         // [W][16]
   __shared__ int s_done[kTcProblems];
   __shared__ int s_new[kTcProblems];
   __shared__ int s_all;
@@ -209,7 +209,7 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
   // x for (problems g, g+8) x (entries 2t, 2t+1) of each of my NT tiles;
   // fragment order: [0] = (g, 2t), [1] = (g, 2t+1), [2] = (g+8, 2t),
   // [3] = (g+8, 2t+1).
-  float x[NT][4], y[NT][4], e[NT][4];
+  float x[NT][4], y[NT][4], d[NT][4];  // d = x - e
   const int jA = j0 + g, jB = j0 + g + 8;
   const bool vA = jA < a.N, vB = jB < a.N;
   const int64_t qA = vA ? (int64_t)a.qidx[jA] * a.sq : 0;
@@ -284,9 +284,9 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const float ib = q < 2 ? ibA : ibB;
-        e[i][q] = shrinkf(x[i][q], ib);
+        d[i][q] = clip(x[i][q], ib);  // x - S_{1/beta_0}(x)
         y[i][q] = 0.0f;
-        u[q] = x[i][q] - e[i][q];
+        u[q] = d[i][q];
       }
       const int n0 = (w * NT + i) * 8;
       const float af[4] = {u[0], u[2], u[1], u[3]};
@@ -307,6 +307,7 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
   int cur = 0;
   int it = 1;  // index of the z whose partial products are in zacc
   float rmA = 0.0f, rmB = 0.0f;  // residual max of the last pass
+  float dmA = 0.0f, dmB = 0.0f;  // max |x - e| of the last pass
   bool last_split = false;       // the last pass used split products
   while (true) {
     // ---- publish partials of z_it and the last pass's residual max -----
@@ -323,26 +324,32 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
       rmA = fmaxf(rmA, __shfl_xor_sync(0xffffffffu, rmA, 2));
       rmB = fmaxf(rmB, __shfl_xor_sync(0xffffffffu, rmB, 1));
       rmB = fmaxf(rmB, __shfl_xor_sync(0xffffffffu, rmB, 2));
+      dmA = fmaxf(dmA, __shfl_xor_sync(0xffffffffu, dmA, 1));
+      dmA = fmaxf(dmA, __shfl_xor_sync(0xffffffffu, dmA, 2));
+      dmB = fmaxf(dmB, __shfl_xor_sync(0xffffffffu, dmB, 1));
+      dmB = fmaxf(dmB, __shfl_xor_sync(0xffffffffu, dmB, 2));
       if (t == 0) {
         rmx[w * kTcProblems + g] = rmA;
         rmx[w * kTcProblems + g + 8] = rmB;
+        dmx[w * kTcProblems + g] = dmA;
+        dmx[w * kTcProblems + g + 8] = dmB;
       }
     }
     __syncthreads();  // (A)
     // ---- stop test for z_{it-1} (in zs[cur]) ------------------------------
     if (tid < kTcProblems) {
       int nw = 0;
-      const int d = s_done[tid];
+      const int sd = s_done[tid];
       if (it == 1) {
-        if (d == 2) nw = 1;  // zero problem: z = 0 now
-      } else if (d == 0) {
-        float rm = 0.0f;
-        for (int q = 0; q < kTcWarps; ++q)
+        if (sd == 2) nw = 1;  // zero problem: z = 0 now
+      } else if (sd == 0) {
+        float rm = 0.0f, xm = 0.0f, dm = 0.0f;
+        for (int q = 0; q < kTcWarps; ++q) {
           rm = fmaxf(rm, rmx[q * kTcProblems + tid]);
-        float xm = 0.0f;
-        for (int q = 0; q < kTcWarps; ++q)
           xm = fmaxf(xm, xmx[q * kTcProblems + tid]);
-        if (last_split && rm < a.eps * xm)
+          dm = fmaxf(dm, dmx[q * kTcProblems + tid]);
+        }
+        if (last_split && rm < a.eps * fmaxf(dm, kStopNormFloor * xm))
           nw = 1;
         else if (it - 1 >= a.max_iter)
           nw = 2;
@@ -408,8 +415,7 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
     const float bnA = fminf(a.rho * betaA, bbarA);
     const float bnB = fminf(a.rho * betaB, bbarB);
     const float ibnA = 1.0f / bnA, ibnB = 1.0f / bnB;
-    rmA = 0.0f;
-    rmB = 0.0f;
+    rmA = rmB = dmA = dmB = 0.0f;
 #pragma unroll
     for (int rb = 0; rb < RB; ++rb)
 #pragma unroll
@@ -460,14 +466,19 @@ __device__ __forceinline__ void adm_tc_tile(const FilterArgs& a,
       for (int q = 0; q < 4; ++q) {
         const float beta = q < 2 ? betaA : betaB;
         const float ibn = q < 2 ? ibnA : ibnB;
-        const float res = x[i][q] - wz[q] - e[i][q];
-        if (q < 2)
+        const float res = d[i][q] - wz[q];
+        if (q < 2) {
           rmA = fmaxf(rmA, fabsf(res));
-        else
+          dmA = fmaxf(dmA, fabsf(d[i][q]));
+        } else {
           rmB = fmaxf(rmB, fabsf(res));
+          dmB = fmaxf(dmB, fabsf(d[i][q]));
+        }
         y[i][q] = fmaf(beta, res, y[i][q]);
-        e[i][q] = shrinkf(x[i][q] - wz[q] + y[i][q] * ibn, ibn);
-        u[q] = x[i][q] - e[i][q] + y[i][q] * ibn;
+        const float yb = y[i][q] * ibn;
+        const float c = clip(x[i][q] - wz[q] + yb, ibn);
+        d[i][q] = wz[q] - yb + c;
+        u[q] = wz[q] + c;
       }
       const float af[4] = {u[0], u[2], u[1], u[3]};
       if (kPreZ) {

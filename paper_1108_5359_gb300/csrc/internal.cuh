@@ -51,6 +51,13 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
 SeedCtl* seed_ctl_ptr_cta(void* d_work, int mp, int np, int kmax);
 int* seed_rank_ptr_cta(void* d_work, int mp, int np, int kmax);
 
+// Algorithm 1's stop test in FP32: ||x - A z - e||_inf < eps * max(||x -
+// e||_inf, kStopNormFloor ||x||_inf).  The paper divides by ||x||_inf; with
+// outliers far above the low-rank part that bound is loose on the part that
+// matters (the fit of x - e), so the FP32 kernels measure the residual
+// against x - e, floored for problems whose low-rank part is (near) zero.
+constexpr float kStopNormFloor = 1e-3f;
+
 // Device arguments of one set of Algorithm 1 problems (see pcp_l1_filter).
 // lowp_iters: tensor-core kernel only, iterations with one-pass TF32
 // products before the split (FP32-accurate) products; 0 = split throughout.

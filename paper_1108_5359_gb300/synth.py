@@ -35,6 +35,7 @@ __all__ = [
     "uneven_instances",
     "video_like",
     "checkerboard",
+    "sparse_magnitude",
 ]
 
 
@@ -280,11 +281,14 @@ def video_like(n_frames, height=240, width=320, r=None, seed=0,
                    name="video_like")
 
 
-def checkerboard(m, square=None, density=0.10, seed=0):
+def checkerboard(m, square=None, density=0.10, seed=0, seed_size=60):
     """Rank-2 checkerboard corrupted by impulsive noise (Section 4.1.2 shape).
 
-    Entries are 0/1 squares; 10% of entries (uniform support) are replaced by
-    the opposite colour (impulsive noise), i.e. S0 = flipped - L0.
+    Entries are 0/1 squares (``square`` pixels wide, default m // 8); 10% of
+    entries (uniform support) are replaced by the opposite colour (impulsive
+    noise), i.e. S0 = flipped - L0.  The section gives no seed size: at this
+    corruption a 20 x 20 seed (10 r) does not recover the seed's own low-rank
+    part, a 60 x 60 one (30 r) does, so ``seed_size`` defaults to 60.
     """
     rng = _rng((seed, 0xC4EC))
     if square is None:
@@ -295,6 +299,21 @@ def checkerboard(m, square=None, density=0.10, seed=0):
     S0 = np.zeros((m, m), order="F")
     S0[mask] = 1.0 - 2.0 * L0[mask]
     M = np.asfortranarray(L0 + S0)
-    rows, cols = seed_indices(m, m, 20, 20, seed=seed)
+    rows, cols = seed_indices(m, m, seed_size, seed_size, seed=seed)
     return Problem(M=M, L0=L0, S0=S0, r=2, rows=rows, cols=cols,
                    name="checkerboard")
+
+
+def sparse_magnitude(sigma, m=1000, seed=0, s=10):
+    """M = L0 + sigma S0 with the Section 4.1 generator (Section 4.1.2 sweep).
+
+    m x m, r = 0.01 m, support ratio 0.01, S0's values U[-500, 500] before the
+    scale sigma (the sweep runs sigma from 1 to 10); the seed is (s r)^2.
+    """
+    r = max(1, int(round(0.01 * m)))
+    M, L0, S0 = lowrank_plus_sparse(m, m, r, 0.01, -500.0, 500.0, seed=seed)
+    S0 = np.asfortranarray(sigma * S0)
+    M = np.asfortranarray(L0 + S0)
+    rows, cols = seed_indices(m, m, s * r, s * r, seed=seed)
+    return Problem(M=M, L0=L0, S0=S0, r=r, rows=rows, cols=cols,
+                   name=f"sparse_magnitude_{sigma:g}")

@@ -57,8 +57,9 @@ def test_tc_zero_and_clean_columns(precision):
     mask = np.ones(N, bool)
     mask[[3, 17]] = False
     # uncorrupted columns: the least-squares z_1 is exact up to the split
-    # products' rounding (~2^-21), so the stop test (3e-7 of ||x||_inf) is
-    # met on the first split-product iteration or the one after
+    # products' rounding (~2^-21), so the stop test (3e-7 of ||x - e||_inf,
+    # here ||x||_inf) is met on the first split-product iteration or the
+    # one after
     # (after one-pass TF32 iterations, whose rounding leaves small nonzero
     # e entries, the refinement takes a few iterations more)
     first, extra = {PCP_FP32_TENSOR: (1, 2), PCP_TF32_REFINED: (5, 4),
