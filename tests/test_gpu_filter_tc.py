@@ -102,3 +102,32 @@ def test_tc_deterministic_and_matches_simt():
     assert np.array_equal(zd, z1) or np.array_equal(zd, zs)
     zd2, _ = _run(A, X, "row", precision=0)
     np.testing.assert_array_equal(zd2, zd)
+
+
+@pytest.mark.parametrize("precision", [PCP_BF16_REFINED, PCP_TF32_REFINED])
+def test_error_before_and_after_refinement(precision, capsys):
+    # the error of A z against the FP64 oracle after the lowp_iters one-pass
+    # iterations alone (max_iter = lowp_iters stops the kernel there), beside
+    # the FP32-accurate form stopped after as many iterations (the ADM's own
+    # progress at that count) and the refined result at the FP32 stop test;
+    # shapes of the 5000^2 r20 column filter (p = 200, r = 20, 10% outliers
+    # of up to 100 against entries of a few units)
+    A, X = _problem(31, 200, 20, 480, dens=0.1, mag=100.0)
+    ref = l1filter.adm_l1(X, A)
+
+    def err(Z):
+        return relerr(A @ Z, A @ ref.Z)
+
+    lowp = 12
+    Zb, itb = _run(A, X, "col", precision=precision, lowp_iters=lowp,
+                   max_iter=lowp)
+    Zf, _ = _run(A, X, "col", precision=PCP_FP32_TENSOR, max_iter=lowp)
+    Zr, itr = _run(A, X, "col", precision=precision, lowp_iters=lowp)
+    eb, ef, er = err(Zb), err(Zf), err(Zr)
+    with capsys.disabled():
+        print(f"\nprecision {precision}: before refinement {eb:.3e} "
+              f"(FP32 form at {lowp} iterations {ef:.3e}), after {er:.3e}, "
+              f"iterations max {int(np.abs(itr).max())}")
+    assert (itb == -lowp).all()        # stopped by max_iter, unrefined
+    assert er < TOL and (itr > 0).all()
+    assert eb > 100 * er
