@@ -127,3 +127,32 @@ def test_lp_and_bruteforce_agree():
             zb, vb = lp.l1_regression_bruteforce(X[:, j], A)
             zl, vl = lp.l1_regression_lp(X[:, j], A)
             assert abs(vb - vl) <= 1e-8 * max(1.0, vb)
+
+
+def test_adm_nonunique_minimiser_reaches_the_optimal_objective():
+    # degenerate l1 regressions whose minimisers form a segment: z is not
+    # unique, so the ADM's answer is checked by its objective (against the
+    # closed form and the LP) and by membership of the optimal set
+    a1 = np.array([1, 1, 1, 1, 0, 0, 0, 0]) / 2.0
+    a2 = np.array([0, 0, 0, 0, 1, 1, 1, 1]) / 2.0
+    A = np.stack([a1, a2], axis=1)                   # orthonormal columns
+    x = np.array([0.0, 0.0, 1.0, 1.0, 0.0, 1.0, 2.0, 3.0])
+    # separable: sum |x_i - z1/2| over {0, 0, 1, 1} is 2 for z1/2 in [0, 1];
+    # over {0, 1, 2, 3} it is 4 for z2/2 in [1, 2] (any median)
+    res = l1filter.adm_l1(x[:, None], A)
+    assert res.converged.all()
+    z = res.Z[:, 0]
+    va = np.abs(x - A @ z).sum()
+    _, vl = lp.l1_regression_lp(x, A)
+    assert abs(va - 6.0) <= 1e-9 * 6.0 and abs(vl - 6.0) <= 1e-9 * 6.0
+    tol = 1e-8
+    assert -tol <= z[0] / 2 <= 1 + tol and 1 - tol <= z[1] / 2 <= 2 + tol
+    gmax, eqres = lp.kkt_certificate(x, A, z)
+    assert gmax <= 1 + 1e-6 and eqres <= 1e-6
+    # one column of a single basis vector: any z/2 in [0, 1] is optimal
+    A1 = np.full((4, 1), 0.5)
+    x1 = np.array([0.0, 0.0, 1.0, 1.0])
+    r1 = l1filter.adm_l1(x1[:, None], A1)
+    z1 = r1.Z[0, 0]
+    assert abs(np.abs(x1 - A1[:, 0] * z1).sum() - 2.0) <= 1e-9 * 2.0
+    assert -tol <= z1 / 2 <= 1 + tol
