@@ -12,7 +12,6 @@ factors only, the asynchronous form (no info), and seed growth (Section
 import numpy as np
 import pytest
 
-from oracle import l1filter
 from paper_1108_5359_gb300 import synth
 from tests.gpuhelp import build_and_load, relerr, to_dev_cm, to_host
 

@@ -17,7 +17,7 @@ import pytest
 from oracle import l1filter, pcp
 from paper_1108_5359_gb300 import synth
 from tests.gpuhelp import build_and_load, relerr
-from tests.test_gpu_solve import _check, _gpu_solve
+from tests.test_gpu_solve import _gpu_solve
 
 pytestmark = pytest.mark.gpu
 

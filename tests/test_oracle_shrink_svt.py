@@ -5,7 +5,6 @@ Section 2).  Checked against closed forms and the optimality conditions of the
 two proximal problems, never against the oracle's own formula.
 """
 import numpy as np
-import pytest
 
 from oracle import pcp
 
