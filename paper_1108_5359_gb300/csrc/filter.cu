@@ -36,6 +36,7 @@
 //     converged writes its z and is frozen (its lanes keep computing but
 //     never write again) so every problem stops exactly at its own test.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <cstring>
 #include <vector>
@@ -242,13 +243,15 @@ size_t adm_smem_bytes() {
 template <int SPT, int RMAX>
 cudaError_t launch_adm(const FilterArgs& a, cudaStream_t st) {
   const size_t smem = adm_smem_bytes<SPT, RMAX>();
-  static bool configured = false;  // per process; attribute is per function
-  if (!configured) {
+  // per process (the attribute is per function); host threads may race to
+  // set it, which is harmless: every setter writes the same value
+  static std::atomic<bool> configured{false};
+  if (!configured.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(
         adm_f32_kernel<SPT, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured.store(true, std::memory_order_release);
   }
   const int grid = (a.N + 31) / 32;
   adm_f32_kernel<SPT, RMAX><<<grid, kThreads, smem, st>>>(a);
@@ -274,13 +277,13 @@ template <int SPT, int RMAX>
 cudaError_t launch_adm_batched(const FilterArgs* d_sets, const int32_t* d_tiles,
                                int ntiles, cudaStream_t st) {
   const size_t smem = adm_smem_bytes<SPT, RMAX>();
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<bool> configured{false};
+  if (!configured.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(
         adm_f32_batched_kernel<SPT, RMAX>,
         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured.store(true, std::memory_order_release);
   }
   adm_f32_batched_kernel<SPT, RMAX><<<ntiles, kThreads, smem, st>>>(d_sets,
                                                                     d_tiles);

@@ -30,6 +30,7 @@
 // split-product iterations.  lowp_iters = 0 gives the FP32-accurate form
 // throughout.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -561,8 +562,8 @@ template <int RB, int NT>
 cudaError_t launch_tc(const FilterArgs* a, const FilterArgs* d_sets,
                       const int32_t* d_tiles, int ntiles, cudaStream_t st) {
   constexpr size_t smem = tc_smem_bytes<RB, NT>();
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<bool> configured{false};  // same value from any thread
+  if (!configured.load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(
         adm_tc_kernel<RB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)smem);
@@ -571,7 +572,7 @@ cudaError_t launch_tc(const FilterArgs* a, const FilterArgs* d_sets,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured.store(true, std::memory_order_release);
   }
   if (a) {
     const int grid = (a->N + kTcProblems - 1) / kTcProblems;

@@ -39,6 +39,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -573,24 +574,28 @@ bool make_map(CUtensorMap* map, const float* base, int64_t ld, int64_t m,
 template <int K>
 pcp_status launch_k(const CUtensorMap& mm, const CUtensorMap& ms,
                     const SpassTcArgs& a0, cudaStream_t st) {
-  static int optin = 0;
+  // the opt-in limit and the attribute are per process; host threads that
+  // race here query or set the same values
+  static std::atomic<int> optin_cache{0};
+  int optin = optin_cache.load(std::memory_order_acquire);
   if (!optin) {
     int dev = 0;
     PCP_CUDA(cudaGetDevice(&dev));
     PCP_CUDA(cudaDeviceGetAttribute(
         &optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    optin_cache.store(optin, std::memory_order_release);
   }
   SpassTcArgs a = a0;
   const size_t fixed = tc_smem_bytes(K, 0);
   a.ns = (int)std::min<size_t>(kMaxStages, ((size_t)optin - fixed) / kTileBytes);
   if (a.ns < 3) return PCP_ERR_UNSUPPORTED;
   const size_t smem = tc_smem_bytes(K, a.ns);
-  static size_t smem_set = 0;
-  if (smem_set != smem) {
+  static std::atomic<size_t> smem_set{0};
+  if (smem_set.load(std::memory_order_acquire) != smem) {
     PCP_CUDA(cudaFuncSetAttribute(spass_tc_kernel<K>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-    smem_set = smem;
+    smem_set.store(smem, std::memory_order_release);
   }
   const int grid =
       (int)std::max<int64_t>(1, std::min<int64_t>(a.ntiles, device_sm_count()));
