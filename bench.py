@@ -3,7 +3,7 @@
 
 One step = one whole solve of Algorithm 2 on a resident 5000 x 5000 FP32
 matrix of rank 20 with 10% corruption in [-100, 100] (seed 200 x 200):
-seed gather + FP64 seed PCP + column/row l1 filtering + factor assembly +
+seed gather + seed PCP + column/row l1 filtering + factor assembly +
 S = M - L.  Prints ONE JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -13,9 +13,16 @@ value        entries (m*n) recovered per second, device-resident input, L2
 e2e          the same metric through the public API from pinned host
              memory: H2D of M, the solve, D2H of Lu, Lv and S per step;
 roofline     the dominant kernel of the step against MEASURED_PEAKS.json;
-cpu_baseline the FP64 oracle on the host cores (rank 0, N=1 only), one full
-             solve of the same workload;
---impl reference  times that oracle as the reference arm.
+cpu_baseline the FP64 oracle on the host cores (rank 0, N=1 only): the
+             median of three full solves of the same workload;
+gpu_launches the library's own kernel launches in the timed steps, as the
+             library counts them (pcp_info.launches);
+large        (N=1) the same record for the 20000 x 20000 rank-50 solve in
+             the BF16 + refinement form, its CPU baseline a stated sample;
+batch        (N=1) 64 uneven instances through pcp_l1filter_batch against
+             one pcp_l1filter_solve per instance, p50 / p99;
+--impl reference  the oracle as the reference arm: one full FP64 oracle
+             solve per step, nothing sampled or scaled.
 Multi-GPU: independent replicas (each rank solves its own instance; weak
 scaling, no collective on the data path), max time over ranks.
 """
@@ -50,11 +57,9 @@ FLUSH_BYTES = 256 << 20
 # kernel code on the same workload (profiles/ holds the summaries and the
 # commands); a kernel changed since its capture gets no entry.
 TRAFFIC = {
-    ("c2_5000_r20", "seed"): (
-        958720, "profiles/seed_alm_kernel_c2_5000_r20.md"),
-    ("c2_5000_r20", "spass"): (
+    ("c2_5000_r20", "spass", "spass_tc_kernel"): (
         158809600, "profiles/spass_tc_kernel_c2_5000_r20.md"),
-    ("c3_20000_r50", "spass"): (
+    ("c3_20000_r50", "spass", "spass_tc_kernel"): (
         2895202000, "profiles/spass_tc_kernel_c2_5000_r20.md: 8000^2 capture "
         "(463.2 MB) scaled by the entry count (x 6.25)"),
 }
@@ -70,6 +75,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the extra records of the default line (the "
+                         "20000^2 solve and the batched form)")
     ap.add_argument("--small", action="store_true",
                     help="500x500 rank-5 workload (profiling / smoke)")
     ap.add_argument("--workload", choices=["single", "large", "batch",
@@ -252,58 +260,70 @@ def relerr(a, b):
 # oracle timing (cpu_baseline and the reference arm)
 # -------------------------------------------------------------------------
 
-def oracle_solve(P, M32, frac=1.0):
-    """FP64 oracle on the workload; frac < 1 filters a sample of the column
-    and row problems and forms that fraction of S, and scales the time."""
-    from oracle import l1filter, pcp
+def oracle_solve(P, M32):
+    """One full FP64 oracle solve (Algorithm 2) of the workload; returns
+    (seconds, result)."""
+    from oracle import l1filter
     M = M32.astype(np.float64)
     t0 = time.perf_counter()
-    if frac >= 1.0:
-        res = l1filter.l1_filter_pcp(M, P.rows, P.cols, r=P.r)
-        t = time.perf_counter() - t0
-        return t, res
-    mp = P.rows.size
-    Ms = M[np.ix_(P.rows, P.cols)]
-    seed = pcp.inexact_alm_pcp(Ms, 1.0 / math.sqrt(mp))
+    res = l1filter.l1_filter_pcp(M, P.rows, P.cols, r=P.r)
+    return time.perf_counter() - t0, res
+
+
+def oracle_sample(P, M32, frac):
+    """A bounded sample of the oracle on a workload too large to solve in
+    full within the bench: the FP64 seed PCP in full, Algorithm 1 on the
+    first frac of the column and row problems, and frac of the S pass.
+    Returns (seconds of the seed, seconds of the sampled rest); the caller
+    scales the rest to the whole workload and says so."""
+    from oracle import l1filter, pcp
+    M = M32  # FP32 storage, promoted per block below
+    t0 = time.perf_counter()
+    Ms = M[np.ix_(P.rows, P.cols)].astype(np.float64)
+    seed = pcp.inexact_alm_pcp(Ms, 1.0 / math.sqrt(max(Ms.shape)))
     t_seed = time.perf_counter() - t0
     U, V = seed.U[:, :P.r], seed.V[:, :P.r]
     rbar = np.setdiff1d(np.arange(P.m), P.rows)
     cbar = np.setdiff1d(np.arange(P.n), P.cols)
     nc = max(1, int(frac * cbar.size))
     nr = max(1, int(frac * rbar.size))
-    t1 = time.perf_counter()
-    col = l1filter.adm_l1(M[np.ix_(P.rows, cbar[:nc])], U)
-    row = l1filter.adm_l1(M[np.ix_(rbar[:nr], P.cols)].T, V)
     ns = max(1, int(frac * P.n))
+    t1 = time.perf_counter()
+    col = l1filter.adm_l1(M[np.ix_(P.rows, cbar[:nc])].astype(np.float64), U)
+    row = l1filter.adm_l1(M[np.ix_(rbar[:nr], P.cols)].T.astype(np.float64),
+                          V)
     Lu = np.zeros((P.m, P.r))
     Lv = np.zeros((ns, P.r))
-    _ = M[:, :ns] - Lu @ Lv.T
+    _ = M[:, :ns].astype(np.float64) - Lu @ Lv.T
     t_rest = time.perf_counter() - t1
     del col, row
-    return t_seed + t_rest / frac, None
+    return t_seed, t_rest
 
 
 def run_reference(args):
+    """The oracle as the reference arm: one FULL FP64 oracle solve of the
+    bench's workload per step (no sampling, no scaling), on the host cores,
+    rank 0 only."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     large = args.workload == "large"
     P, M32 = make_problem(args.seed, args.small, large, args.size)
     mn = P.m * P.n
-    frac = 1.0 if args.small else (0.01 if large else 0.1)
     cores = os.cpu_count()
     for _ in range(args.warmup):
-        oracle_solve(P, M32, frac)
+        oracle_solve(P, M32)
     times = []
+    wall0 = time.perf_counter()
     for _ in range(args.steps):
-        t, _ = oracle_solve(P, M32, frac)
+        t, _ = oracle_solve(P, M32)
         times.append(t)
+    wall = time.perf_counter() - wall0
     t_mean = statistics.mean(times)
     value = mn / t_mean
-    sample = (f"full oracle solve per step" if frac >= 1 else
-              f"per step: full FP64 seed PCP + Algorithm 1 on {frac:.0%} of "
-              f"the column and row problems + {frac:.0%} of the S pass, "
-              f"non-seed time scaled by 1/{frac:g}")
+    sample = ("one full FP64 oracle solve of the workload per step (numpy, "
+              f"BLAS threads = host cores); {args.steps} steps after "
+              f"{args.warmup} warm-up steps")
     out = {
         "impl": "reference", "metric": METRIC, "value": value,
         "unit": "entries/s", "n_gpus": args.gpus, "steps": args.steps,
@@ -313,6 +333,7 @@ def run_reference(args):
         "config": {"workload": workload_name(args)[0],
                    "desc": workload_name(args)[1],
                    "parallelism": "host cores"},
+        "wall_s_timed_loop": wall,
         "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0,
@@ -325,41 +346,34 @@ def run_reference(args):
 # our arm
 # -------------------------------------------------------------------------
 
-def run_ours(args):
-    import torch
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else
-                                "gloo")
-    torch.cuda.set_device(local)
-    import paper_1108_5359_gb300 as pk
-    from paper_1108_5359_gb300 import build as pkbuild
-    pkbuild.build()
-    pk.load()
+SEED_DTYPE = ("f64 ALM state, Ritz values and final skinny SVD (U^s, V^s "
+              "orthonormal to FP64 rounding); FP32 k x k Cholesky / Jacobi "
+              "inside the ALM; FP32 tall and rank-k products while the ALM "
+              "residual is above 1e-4")
 
-    large = args.workload == "large"
-    pseed = rank_seed(args.seed, rank)
-    P, M32 = make_problem(pseed, args.small, large, args.size)
+
+def measure_single(pk, torch, dev, P, M32, wl, precision, steps, warmup,
+                   ws=1, pseed=0, want_e2e=True, cpu_mode=None, local=0):
+    """Time `steps` whole solves of one resident instance (after `warmup`),
+    then the same through the host-buffer API; returns the record."""
     m, n, r = P.m, P.n, P.r
     mn = m * n
-    dev = torch.device("cuda", local)
     dM = pk.colmajor(m, n, device=dev)
     dM.copy_(torch.from_numpy(M32))
     Lu = pk.colmajor(m, r, device=dev)
     Lv = pk.colmajor(n, r, device=dev)
     S = pk.colmajor(m, n, device=dev)
     params = pk.pcp_params_default(m, n, r)
-    params.precision = PRECISIONS[args.precision]
+    params.precision = PRECISIONS[precision]
     plan = pk.Plan(params, P.rows, P.cols)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(info=True):
-        return pk.pcp_l1filter_solve(plan, dM, Lu, Lv, S, info=info,
+    def step():
+        return pk.pcp_l1filter_solve(plan, dM, Lu, Lv, S, info=True,
                                      stream=stream, raise_on_error=False)
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         flush.zero_()
         st, info, _, _ = step()
     torch.cuda.synchronize()
@@ -371,10 +385,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler.start()
     step_ms, stage = [], {"seed": [], "filter": [], "spass": []}
+    launches = 0
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     wall0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         ev0.record(stream)
         st, info, _, _ = step()
@@ -384,16 +399,17 @@ def run_ours(args):
         stage["seed"].append(info.t_seed_ms)
         stage["filter"].append(info.t_filter_ms)
         stage["spass"].append(info.t_spass_ms)
+        launches += info.launches
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if ws > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
     t_step = max_over_ranks(statistics.mean(step_ms), dev)
-    value = job_value(ws, mn, t_step)
     last_info = info.as_dict()
 
     # parity of the last solve: exact recovery of the generated L0, S0
+    Lrec = Sh = None
     if P.L0 is not None:
         Lh = Lu.double().cpu().numpy()
         Vh = Lv.double().cpu().numpy()
@@ -409,13 +425,14 @@ def run_ours(args):
     # M from pinned host memory, Lu, Lv and S back to pinned host memory,
     # all copies inside the timed span
     e2e = None
-    if not args.no_e2e:
+    if want_e2e:
+        del S
         hM = torch.from_numpy(np.ascontiguousarray(M32.T)).pin_memory().t()
         hLu = torch.empty((r, m), dtype=torch.float32).pin_memory().t()
         hLv = torch.empty((r, n), dtype=torch.float32).pin_memory().t()
         hS = torch.empty((n, m), dtype=torch.float32).pin_memory().t()
         e_ms = []
-        for it in range(max(3, args.warmup) + args.steps):
+        for it in range(max(3, warmup) + steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -423,21 +440,36 @@ def run_ours(args):
                                        stream=stream)
             e1.record(stream)
             e1.synchronize()
-            if it >= max(3, args.warmup):
+            if it >= max(3, warmup):
                 e_ms.append(e0.elapsed_time(e1))
         te = max_over_ranks(statistics.mean(e_ms), dev)
         e2e = {"value": job_value(ws, mn, te), "unit": "entries/s",
                "ms_per_step": te, "h2d_bytes_per_step": 4 * mn,
                "d2h_bytes_per_step": 4 * mn + 4 * r * (m + n)}
+        del hM, hS
+    plan.close()
+    del dM, flush
+    torch.cuda.empty_cache()
+    return dict(P=P, M32=M32, wl=wl, precision=precision, steps=steps,
+                warmup=max(3, warmup), t_step=t_step, step_ms=step_ms,
+                stage=stage, launches=launches, wall=wall, clocks=clocks,
+                info=last_info, parity=parity, e2e=e2e, Lrec=Lrec, Sh=Sh,
+                ws=ws, cpu_mode=cpu_mode)
 
-    # roofline of the dominant kernel
+
+def report(pk, rec, rank=0):
+    """Stages, roofline of the dominant kernel, CPU baseline and parity
+    against the oracle for one measure_single() record."""
+    P, M32, info = rec["P"], rec["M32"], rec["info"]
+    m, n, r = P.m, P.n, P.r
+    mn = m * n
+    ws = rec["ws"]
     pk_d, pk_src = peaks()
-    mean = {k: statistics.mean(v) for k, v in stage.items()}
-    mp = P.rows.size
-    np_ = P.cols.size
+    mean = {k: statistics.mean(v) for k, v in rec["stage"].items()}
+    mp, np_ = P.rows.size, P.cols.size
     spass_bytes = 8 * mn + 4 * r * (m + n)
-    kiter = last_info["filter_iters_max"]
-    kmean = last_info.get("filter_iters_mean") or kiter
+    kiter = info["filter_iters_max"]
+    kmean = info.get("filter_iters_mean") or kiter
     # algorithmic flops of Algorithm 1: 4 p r per problem-iteration (A z and
     # A^T u), summed over problems at their own iteration counts
     filt_flops = 4.0 * r * ((n - np_) * mp + (m - mp) * np_) * kmean
@@ -447,102 +479,169 @@ def run_ours(args):
     # tf32 / bf16 ratio (1.1 / 2.25 PFLOP/s)
     tf32_peak = pk_d["bf16_tflops"] * 1.1 / 2.25
     k_seed = r + max(6, r // 4)
-    seed_flops = (last_info["seed_iters"] + 3) * (
+    seed_flops = (info["seed_iters"] + 3) * (
         6.0 * mp * np_ * k_seed + 4.0 * (mp + np_) * k_seed ** 2)
-    tc = args.precision != "fp32simt"
+    prec = PRECISIONS[rec["precision"]]
+    fk = pk.pcp_l1_filter_kernel(mp, r, prec)
+    tc = fk == pk._abi.PCP_KERNEL_TENSOR
+    team = info.get("seed_team", 0)
+    seed_kernel = "seed_alm_cluster_kernel" if team > 0 else "seed_alm_kernel"
     stages = {
         "spass": {"bound": "hbm", "ms": mean["spass"],
                   "achieved": spass_bytes / (mean["spass"] * 1e-3) / 1e9,
                   "peak": pk_d["hbm_gbs"], "unit": "GB/s",
-                  "algorithmic_bytes": spass_bytes},
+                  "algorithmic_bytes": spass_bytes,
+                  "kernel": "spass_tc_kernel"},
         "filter": {"bound": "tensor" if tc else "alu", "ms": mean["filter"],
                    "achieved": filt_flops / (mean["filter"] * 1e-3) / 1e12,
                    "peak": tf32_peak if tc else fp32_peak, "unit": "TFLOP/s",
                    "iters_mean": kmean, "iters_max": kiter,
+                   "kernel": pk._abi.KERNEL_NAMES[fk],
                    "note": ("algorithmic flops 4 p r per problem-iteration "
                             "at each problem's own count; " +
                             ("TF32 tensor peak (measured bf16 x 1.1/2.25); "
                              "split-TF32 executes 3 passes per product"
                              if tc else "FP32 FMA peak derived"))},
         "seed": {"bound": "alu", "ms": mean["seed"], "unit": "TFLOP/s",
-                 "peak": fp64_peak,
+                 "peak": fp64_peak, "kernel": seed_kernel,
+                 "team": (f"cluster of {team} CTAs" if team > 0 else
+                          f"cooperative grid of {-team} CTAs"),
                  "achieved": seed_flops / (mean["seed"] * 1e-3) / 1e12,
-                 "note": "FP64; 6 m'n'k + 4 (m'+n') k^2 flops per ALM "
-                         "iteration (k = r + max(6, r/4)), seed iterations "
-                         "+ 3 prologue passes"},
+                 "note": "6 m'n'k + 4 (m'+n') k^2 flops per ALM iteration "
+                         "(k = r + max(6, r/4)), seed iterations + 3 "
+                         "prologue passes, against the FP64 peak (part of "
+                         "the work runs in FP32)"},
     }
-    for v in stages.values():
-        v["frac"] = v["achieved"] / v["peak"]
-    dom = max(stages, key=lambda k: stages[k]["ms"])
-    d = stages[dom]
-    wl_name = workload_name(args)[0]
-    kernel = {"spass": "spass_tc_kernel",
-              "filter": ("adm_f32_kernel" if args.precision == "fp32simt"
-                         else "adm_tc_kernel"),
-              "seed": "seed_alm_kernel"}
     for k, v in stages.items():
-        v["kernel"] = kernel[k]
-        t = TRAFFIC.get((wl_name, k))
+        v["frac"] = v["achieved"] / v["peak"]
+        t = TRAFFIC.get((rec["wl"], k, v["kernel"]))
         v["traffic"] = t[0] if t else None
         if t:
             v["traffic_source"] = t[1]
-    roofline = {"kernel": kernel[dom],
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    d = stages[dom]
+    roofline = {"kernel": d["kernel"], "stage": dom,
                 "bound": d["bound"], "achieved": d["achieved"],
                 "peak": d["peak"], "unit": d["unit"], "frac": d["frac"],
                 "traffic": d["traffic"],
                 "peak_source": (pk_src + " hbm_gbs" if d["bound"] == "hbm"
                                 else (pk_src + " bf16_tflops x 1.1/2.25"
                                       if d["bound"] == "tensor" else
-                                      "derived: 152 SMs x FP64 FMA/clk x 2 "
-                                      "x 2.07 GHz"))}
-
+                                      "derived: 152 SMs x FMA/clk x 2 x "
+                                      "2.07 GHz (FP64: 2 FMA/clk/SM, FP32: "
+                                      "128)"))}
+    parity = dict(rec["parity"])
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        frac = 0.01 if large else 1.0
-        t_or, ref = oracle_solve(P, M32, frac)
-        cpu = {"value": mn / t_or, "unit": "entries/s",
-               "cores": os.cpu_count(), "kind": "oracle",
-               "sample": ("one full FP64 oracle solve of the same workload "
-                          "(numpy, BLAS threads = host cores)" if frac >= 1
-                          else "full FP64 seed PCP + Algorithm 1 on 1% of "
-                          "the column and row problems + 1% of the S pass, "
-                          "non-seed time scaled by 100")}
-        if ref is not None:
-            parity["relerr_L_vs_oracle"] = relerr(Lrec, ref.L)
-            parity["relerr_S_vs_oracle"] = relerr(Sh, ref.S)
+    mode = rec["cpu_mode"]
+    if rank == 0 and ws == 1 and mode:
+        cores = os.cpu_count()
+        if mode == "full":
+            # median of three full FP64 oracle solves
+            ts, ref = [], None
+            for _ in range(3):
+                t, ref = oracle_solve(P, M32)
+                ts.append(t)
+            t_or = statistics.median(ts)
+            cpu = {"value": mn / t_or, "unit": "entries/s", "cores": cores,
+                   "kind": "oracle", "seconds": ts,
+                   "sample": "median of 3 full FP64 oracle solves of the "
+                             "same workload (numpy, BLAS threads = host "
+                             "cores)"}
+            if rec["Lrec"] is not None:
+                parity["relerr_L_vs_oracle"] = relerr(rec["Lrec"], ref.L)
+                parity["relerr_S_vs_oracle"] = relerr(rec["Sh"], ref.S)
+        else:
+            frac = mode
+            t_seed, t_rest = oracle_sample(P, M32, frac)
+            t_or = t_seed + t_rest / frac
+            cpu = {"value": mn / t_or, "unit": "entries/s", "cores": cores,
+                   "kind": "oracle",
+                   "sample": f"FP64 oracle seed PCP in full ({t_seed:.2f} s) "
+                             f"+ Algorithm 1 on {frac:.0%} of the column and "
+                             f"row problems and {frac:.0%} of the S pass "
+                             f"({t_rest:.2f} s), that part scaled by "
+                             f"1/{frac:g} to the whole workload"}
+    lat = sorted(rec["step_ms"])
+    out = {
+        "value": job_value(ws, mn, rec["t_step"]), "unit": "entries/s",
+        "ms_per_step": rec["t_step"], "steps": rec["steps"],
+        "warmup": rec["warmup"],
+        "dtype": {"fp32": "f32", "bf16": "bf16+f32", "tf32": "tf32+f32",
+                  "fp32simt": "f32"}[rec["precision"]],
+        "latency_ms": {"p50": lat[len(lat) // 2],
+                       "p99": lat[min(len(lat) - 1,
+                                      int(math.ceil(0.99 * len(lat))) - 1)]},
+        "wall_s_timed_loop": rec["wall"],
+        "stages_ms": mean, "stages": stages,
+        "seed_iters": info["seed_iters"], "filter_iters_max": kiter,
+        "parity": parity, "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": rec["e2e"], "clocks": rec["clocks"],
+        "gpu_launches": rec["launches"],
+    }
+    return out
 
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else
+                                "gloo")
+    torch.cuda.set_device(local)
+    import paper_1108_5359_gb300 as pk
+    from paper_1108_5359_gb300 import build as pkbuild
+    pkbuild.build()
+    pk.load()
+    dev = torch.device("cuda", local)
+    large = args.workload == "large"
+    pseed = rank_seed(args.seed, rank)
+    P, M32 = make_problem(pseed, args.small, large, args.size)
+    wl, desc = workload_name(args)
+    cpu_mode = None if args.no_cpu_baseline else (0.01 if large else "full")
+    rec = measure_single(pk, torch, dev, P, M32, wl, args.precision,
+                         args.steps, args.warmup, ws=ws, pseed=pseed,
+                         want_e2e=not args.no_e2e, cpu_mode=cpu_mode,
+                         local=local)
+    body = report(pk, rec, rank)
+    del rec
+    subs = {}
+    # extra records on one GPU: the largest single-GPU configuration in its
+    # own precision form, and the batched form against per-instance solves
+    if ws == 1 and not args.no_sub and not args.small and not large:
+        P3, M3 = make_problem(args.seed, large=True)
+        rec3 = measure_single(pk, torch, dev, P3, M3, LARGE, "bf16",
+                              min(args.steps, 10), 3, cpu_mode=(
+                                  None if args.no_cpu_baseline else 0.01),
+                              local=local)
+        r3 = report(pk, rec3, rank)
+        r3["config"] = {"workload": LARGE, "desc": LARGE_DESC +
+                        "; Algorithm 1 in BF16 one-pass products then "
+                        "split-TF32 refinement (PCP_BF16_REFINED)",
+                        "l2": "inputs larger than L2, and a 256 MB memset "
+                              "between steps outside the timed span"}
+        subs["large"] = r3
+        del rec3, P3, M3
+        subs["batch"] = batch_record(pk, torch, dev, count=64, steps=3,
+                                     warmup=3, seed=args.seed, r_max=25)
     if rank == 0:
-        lat = sorted(step_ms)
-        out = {
-            "metric": METRIC, "value": value, "unit": "entries/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup),
-            "ms_per_step": t_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16+f32",
-                      "tf32": "tf32+f32", "fp32simt": "f32"}[args.precision],
-            "data": "synthetic",
-            "config": {"workload": workload_name(args)[0],
-                       "desc": workload_name(args)[1], "global_batch": ws,
-                       "parallelism": f"replicas{ws}",
-                       "l2": "flushed between steps (256 MB memset outside "
-                             "the timed span)",
-                       "seed_dtype": "f64"},
-            "latency_ms": {"p50": lat[len(lat) // 2],
-                           "p99": lat[min(len(lat) - 1,
-                                          int(math.ceil(0.99 * len(lat))) - 1)]},
-            "wall_s_timed_loop": wall,
-            "stages_ms": mean, "stages": stages,
-            "seed_iters": last_info["seed_iters"],
-            "filter_iters_max": kiter,
-            "parity": parity, "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": e2e, "clocks": clocks,
-            "gpu_launches": 6 * args.steps,
-        }
+        out = {"metric": METRIC, "value": body.pop("value"),
+               "unit": body.pop("unit"), "n_gpus": ws,
+               "steps": body.pop("steps"), "warmup": body.pop("warmup"),
+               "ms_per_step": body.pop("ms_per_step"),
+               "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": body.pop("dtype"),
+               "data": "synthetic",
+               "config": {"workload": wl, "desc": desc, "global_batch": ws,
+                          "parallelism": f"replicas{ws}",
+                          "l2": "flushed between steps (256 MB memset "
+                                "outside the timed span)",
+                          "seed_dtype": SEED_DTYPE}}
+        out.update(body)
+        out.update(subs)
         print(json.dumps(out), flush=True)
-    plan.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
-
 
 # -------------------------------------------------------------------------
 # batched and served forms (extra lines, not the default bench line)
@@ -553,20 +652,15 @@ def _pct(v, q):
     return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
 
 
-def run_batch(args):
+def batch_record(pk, torch, dev, count, steps, warmup, seed, r_max):
     """Uneven instances: one pcp_l1filter_batch call per step against one
-    pcp_l1filter_solve per instance (plans made outside the timed span)."""
-    import torch
-    import paper_1108_5359_gb300 as pk
-    from paper_1108_5359_gb300 import build as pkbuild, synth
-    pkbuild.build()
-    pk.load()
+    pcp_l1filter_solve per instance (plans made outside the timed span);
+    returns the record."""
+    from paper_1108_5359_gb300 import synth
     t0 = time.perf_counter()
-    Ps = synth.uneven_instances(count=args.count, seed=args.seed,
-                                r_max=args.r_max, keep_truth=False,
-                                dtype=np.float32)
+    Ps = synth.uneven_instances(count=count, seed=seed, r_max=r_max,
+                                keep_truth=False, dtype=np.float32)
     t_gen = time.perf_counter() - t0
-    dev = torch.device("cuda", 0)
     bufs, probs, plans = [], [], []
     for P in Ps:
         dM = pk.colmajor(P.m, P.n, device=dev)
@@ -578,7 +672,7 @@ def run_batch(args):
         # seeds by order, grown on a failed rank test (Section 3.5)
         prm = pk.pcp_params_default(P.m, P.n, P.r)
         prm.grow_seed = 1
-        ro, co = synth.seed_orders(P.m, P.n, P.rows, P.cols, seed=args.seed)
+        ro, co = synth.seed_orders(P.m, P.n, P.rows, P.cols, seed=seed)
         probs.append(pk.problem(prm, dM, Lu, Lv, S, row_order=ro,
                                 col_order=co))
         prm2 = pk.pcp_params_default(P.m, P.n, P.r)
@@ -611,7 +705,7 @@ def run_batch(args):
             done_ms.append(e0.elapsed_time(e))
         return done_ms
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         flush.zero_()
         st, infos = batched()
         flush.zero_()
@@ -621,7 +715,7 @@ def run_batch(args):
     sampler = ClockSampler(0)
     sampler.start()
     b_ms, p_ms, p_lat = [], [], []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -638,8 +732,8 @@ def run_batch(args):
     clocks = sampler.stop()
     # parity: exact recovery on a sample of instances (regenerated with truth)
     check = sorted(set([0, len(Ps) // 2, len(Ps) - 1]))
-    truth = synth.uneven_instances(count=args.count, seed=args.seed,
-                                   r_max=args.r_max, indices=check)
+    truth = synth.uneven_instances(count=count, seed=seed, r_max=r_max,
+                                   indices=check)
     par = []
     for i, T in zip(check, truth):
         dM, Lu, Lv, S = bufs[i]
@@ -656,12 +750,12 @@ def run_batch(args):
     out = {
         "metric": METRIC, "workload": "batch",
         "value": ok_entries / (tb * 1e-3),
-        "unit": "entries/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": tb,
+        "unit": "entries/s", "n_gpus": 1, "steps": steps,
+        "warmup": max(3, warmup), "ms_per_step": tb,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"uneven{args.count}_r3-{args.r_max}",
-                   "desc": f"{args.count} instances, m~U[300,4000], "
-                           f"n~U[200,3000], r~U[3,{args.r_max}], density "
+        "config": {"workload": f"uneven{count}_r3-{r_max}",
+                   "desc": f"{count} instances, m~U[300,4000], "
+                           f"n~U[200,3000], r~U[3,{r_max}], density "
                            "U[0.02,0.15], values U[-50,50], seed 10r x 10r, "
                            "FP32 M",
                    "entries_per_step": entries,
@@ -680,9 +774,22 @@ def run_batch(args):
         "statuses": {str(k): statuses.count(k) for k in set(statuses)},
         "parity_sample": par, "clocks": clocks,
     }
-    print(json.dumps(out), flush=True)
     for pl in plans:
         pl.close()
+    del bufs, probs, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args):
+    import torch
+    import paper_1108_5359_gb300 as pk
+    from paper_1108_5359_gb300 import build as pkbuild
+    pkbuild.build()
+    pk.load()
+    out = batch_record(pk, torch, torch.device("cuda", 0), args.count,
+                       args.steps, args.warmup, args.seed, args.r_max)
+    print(json.dumps(out), flush=True)
 
 
 def run_serve(args):

@@ -56,14 +56,14 @@ typedef enum pcp_status {
   PCP_ERR_UNSUPPORTED = -11   /* option not available on this device */
 } pcp_status;
 
-/* Arithmetic of Algorithm 1 (the seed PCP is FP64 in every mode). */
+/* Arithmetic of Algorithm 1 (the seed PCP is the same in every mode). */
 typedef enum pcp_precision {
   PCP_FP32 = 0,          /* FP32-accurate, kernel chosen by the library:
                             split-TF32 tensor-core products (three passes,
                             ~2^-21 relative), or, where both kernels take
-                            the shape (p <= 256, r <= 32), whichever of it
-                            and the SIMT FP32 kernel the first call on that
-                            shape class measured faster */
+                            the shape (p <= 256, r <= 32), the SIMT FP32
+                            kernel where the compiled-in tuning table says
+                            it is faster (pcp_l1_filter_kernel) */
   PCP_BF16_REFINED = 1,  /* one-pass BF16 tensor-core products (inputs
                             rounded to BF16, FP32 accumulation) for the
                             first lowp_iters iterations, then split-TF32
@@ -126,9 +126,19 @@ typedef struct pcp_params {
                                (row_order / col_order or the library's own
                                sampling, not seed_rows / seed_cols) and a
                                pcp_info for the solve */
-  int32_t seed_ctas;        /* CTAs of the whole-GPU seed PCP; 0 = one per
-                               row / column of the seed up to the co-resident
-                               limit.  The result does not depend on it. */
+  int32_t seed_ctas;        /* team of the seed PCP: 1..16 = one thread-
+                               block cluster of that many CTAs (hardware
+                               cluster barrier; the grid form below when the
+                               device cannot hold it), more = a cooperative
+                               grid of that many CTAs (software grid barrier,
+                               up to the co-resident limit), 0 = the
+                               library's choice.  The result does not depend
+                               on it (fixed partial-sum slots). */
+  int64_t wait_timeout_ns;  /* limit of each bounded device wait of the seed
+                               stage (its grid barrier), in ns; <= 0 means
+                               2 s.  A wait that runs out ends the seed
+                               kernel on every CTA and the solve returns
+                               PCP_ERR_TIMEOUT (the device stays usable). */
 } pcp_params;
 
 /* Diagnostics of one solve. */
@@ -151,6 +161,16 @@ typedef struct pcp_info {
   int32_t seed_rank_raw;    /* rank of L^s before the cap at r (Eq.
                                rank_test uses it) */
   double filter_iters_mean; /* mean Algorithm 1 iterations per problem */
+  int32_t filter_kernel;    /* Algorithm 1 kernel of the column filter
+                               (PCP_KERNEL_SIMT or PCP_KERNEL_TENSOR); the
+                               row filter's is pcp_l1_filter_kernel(n', r,
+                               precision) */
+  int32_t launches;         /* kernels this call launched on the device
+                               (every stage, seed growth included) */
+  int32_t seed_team;        /* the seed PCP's team of CTAs: c > 0 for one
+                               thread-block cluster of c CTAs, -g for a
+                               cooperative grid of g CTAs */
+  int32_t pad_info;
 } pcp_info;
 
 /* One instance of a batched or served solve: its parameters and buffers
@@ -386,7 +406,8 @@ pcp_status pcp_seed_pcp_static(const double* dD, int32_t mp, int32_t np,
  * codes: 1 prologue norms, 2 T = G^T Omega, 3 Gram of T, 4 Cholesky QR of T,
  * 5 P = G Psi, 6 Gram of P, 7 power-step orthonormalisation, 8 Jacobi
  * eigen-solve, 9 rotation to Ritz vectors, 10 ALM start, 11 ALM update,
- * 12 set-up of the eigen-solve.
+ * 12 set-up of the eigen-solve, 13 / 14 FP64 refinement of the Ritz basis
+ * (Gram, rotation), 15 the final FP64 skinny SVD of L^s.
  * Synchronises `stream`.  Returns the number of records, -1 on error. */
 int32_t pcp_seed_trace(const void* d_work, int32_t mp, int32_t np,
                        int32_t kmax, uint64_t* h_out, int32_t cap,
@@ -423,6 +444,21 @@ pcp_status pcp_l1_filter(const float* dM, const int32_t* d_pidx, int32_t p,
                          int32_t max_iter, int32_t precision,
                          int32_t lowp_iters, int32_t* d_iters,
                          void* stream);
+
+/* Algorithm 1 kernels (pcp_info.filter_kernel, pcp_l1_filter_kernel). */
+enum {
+  PCP_KERNEL_SIMT = 1,   /* adm_f32_kernel: FP32 FMA on the CUDA cores */
+  PCP_KERNEL_TENSOR = 2  /* adm_tc_kernel: mma.sync tensor-core products */
+};
+
+/* The Algorithm 1 kernel pcp_l1_filter (and every solve) runs for problems
+ * of length p, rank r and the given precision: PCP_KERNEL_SIMT or
+ * PCP_KERNEL_TENSOR, or PCP_ERR_ARG for sizes or a precision it refuses.
+ * For PCP_FP32 the choice is fixed per (p, r) class by a table compiled
+ * into the library (written by a committed tuning run that timed both
+ * kernels on GB300), so the same inputs give the same bits in every
+ * process; the batched and served forms use the same table. */
+int32_t pcp_l1_filter_kernel(int32_t p, int32_t r, int32_t precision);
 
 /* Stage 5: factor assembly (Eq. l1s').  From the seed's FP64 skinny SVD
  * (dU mp x ku ld mp, dSigma, dV np x ku ld np, rank *d_rank) write

@@ -28,7 +28,7 @@ __all__ = [
     "pcp_plan_graph_launches",
     "pcp_gather_seed",
     "pcp_seed_workspace_bytes", "pcp_seed_pcp", "pcp_seed_pcp_static",
-    "pcp_l1_filter",
+    "pcp_l1_filter", "pcp_l1_filter_kernel",
     "pcp_assemble_factors", "pcp_spass", "PCP_SPASS_AUTO", "PCP_SPASS_SIMT",
     "PCP_SPASS_TENSOR", "pcp_plan_seed_trace", "Plan",
     "solve", "load", "SEED_PHASES", "PCPProblem", "problem",
@@ -379,7 +379,7 @@ SEED_PHASES = {1: "prologue", 2: "T=G^T Omega", 3: "gram(T)", 4: "cholqr(T)",
                5: "P=G Psi", 6: "gram(P)", 7: "power orth", 8: "jacobi",
                9: "rotate", 10: "alm start", 11: "alm update",
                12: "jacobi setup", 13: "refine gram(Pt)",
-               14: "refine apply"}
+               14: "refine apply", 15: "final FP64 SVD"}
 
 
 def pcp_l1_filter(M, d_pidx, sp, d_qidx, sq, A, r, Z, ldz, eps, rho,
@@ -392,6 +392,15 @@ def pcp_l1_filter(M, d_pidx, sp, d_qidx, sq, A, r, Z, ldz, eps, rho,
         d_qidx.numel(), sq, pA, lda, r, _ptr(d_rank), _ptr(d_scale), _ptr(Z),
         ldz, eps, rho, beta0_scale, beta_bar_ratio, max_iter, precision,
         lowp_iters, _ptr(d_iters), _stream(stream)), "pcp_l1_filter")
+
+
+def pcp_l1_filter_kernel(p, r, precision=PCP_FP32):
+    """PCP_KERNEL_SIMT (1) or PCP_KERNEL_TENSOR (2): the Algorithm 1 kernel
+    the library runs for problems of length p and rank r."""
+    k = load().pcp_l1_filter_kernel(int(p), int(r), int(precision))
+    if k < 0:
+        check(k, "pcp_l1_filter_kernel")
+    return k
 
 
 def pcp_assemble_factors(U, Sigma, V, d_rank, r, d_rows, d_cols, Lu, Lv, U32,

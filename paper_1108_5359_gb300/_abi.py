@@ -38,6 +38,11 @@ PCP_FP64 = 3
 PCP_FP32_TENSOR = 4
 PCP_FP32_SIMT = 5
 
+PCP_KERNEL_SIMT = 1
+PCP_KERNEL_TENSOR = 2
+KERNEL_NAMES = {PCP_KERNEL_SIMT: "adm_f32_kernel",
+                PCP_KERNEL_TENSOR: "adm_tc_kernel"}
+
 PCP_SPASS_AUTO = 0
 PCP_SPASS_SIMT = 1
 PCP_SPASS_TENSOR = 2
@@ -63,6 +68,7 @@ class PCPParams(C.Structure):
         ("col_order", C.POINTER(C.c_int64)),
         ("seed_m", C.c_int32), ("seed_n", C.c_int32),
         ("grow_seed", C.c_int32), ("seed_ctas", C.c_int32),
+        ("wait_timeout_ns", C.c_int64),
     ]
 
 
@@ -77,6 +83,8 @@ class PCPInfo(C.Structure):
         ("t_spass_ms", C.c_float), ("t_total_ms", C.c_float),
         ("status", C.c_int32), ("seed_rank_raw", C.c_int32),
         ("filter_iters_mean", C.c_double),
+        ("filter_kernel", C.c_int32), ("launches", C.c_int32),
+        ("seed_team", C.c_int32), ("pad_info", C.c_int32),
     ]
 
     def as_dict(self):
@@ -130,6 +138,7 @@ PROTOTYPES = {
     "pcp_l1_filter": (_i32, [_vp, _vp, _i32, _i64, _vp, _i32, _i64, _vp, _i32,
                              _i32, _vp, _vp, _vp, _i64, _f64, _f64, _f64, _f64,
                              _i32, _i32, _i32, _vp, _vp]),
+    "pcp_l1_filter_kernel": (_i32, [_i32, _i32, _i32]),
     "pcp_assemble_factors": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _i32,
                                     _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp,
                                     _vp, _vp]),

@@ -45,7 +45,9 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
                           double mu_max_ratio, int max_iter, int k0, int kmax,
                           double rank_cut, int r_cap, void* d_work,
                           double* dU, double* dSigma, double* dV,
-                          cudaStream_t st, int** d_rank_out, int ctas);
+                          cudaStream_t st, int** d_rank_out, int ctas,
+                          unsigned long long timeout_ns, int* launches,
+                          int* team_out);
 pcp_status seed_read_ctl(void* d_work, int mp, int np, int kmax,
                          cudaStream_t st, int* rank, int* iters,
                          double* residual, int* converged, int* error,
@@ -159,6 +161,9 @@ struct pcp_plan {
   int async_calls = 0;
   int64_t graph_launches = 0;
   bool graph_off = false;
+  // kernels launched since the public entry point began (pcp_info.launches)
+  int launches = 0;
+  int seed_team = 0;  // the last seed launch's team (pcp_info.seed_team)
 };
 
 extern "C" const char* pcp_last_error(void) { return pcp::g_err; }
@@ -532,6 +537,7 @@ extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
                                          int64_t* h_seed_rows_out,
                                          int64_t* h_seed_cols_out,
                                          pcp_info* info, void* stream) {
+  if (P) P->launches = 0;
   if (P && !info) {
     if (h_seed_rows_out || h_seed_cols_out) {
       pcp_status s0 = upload_indices(P, (cudaStream_t)stream);
@@ -587,8 +593,10 @@ static pcp_status grow_loop(pcp_plan* P, const float* dM, int64_t ldm,
       if (s2 != PCP_OK) return s2;
     }
     cur = P->child;
+    P->child->launches = P->launches;  // info->launches counts every attempt
     st = solve_once(P->child, dM, ldm, dLu, dLv, dS, lds, h_seed_rows_out,
                     h_seed_cols_out, info, stream);
+    P->launches = P->child->launches;
   }
   return st;
 }
@@ -621,6 +629,7 @@ extern "C" pcp_status pcp_l1filter_solve_host(pcp_plan* P, const float* hM,
   PCP_ARG(!hS || lds >= P->m, "pcp_l1filter_solve_host: lds < m");
   pcp_status s = ensure_host_buffers(P, hS != nullptr);
   if (s != PCP_OK) return s;
+  P->launches = 0;
   // a page-locked M is read in place by the seed gather (the device reads
   // host memory directly), so the seed need not wait for the whole copy
   HostIO io{hM, nullptr, ldm, hLu, hLv, hS, lds};
@@ -705,19 +714,25 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
           : pcp::gather_seed(dM, ldm, P->d_rows, P->mp, P->d_cols, P->np,
                              P->d_Ms, P->d_bad, st);
   if (s != PCP_OK) return s;
+  ++P->launches;
   // stage 2: seed PCP (FP64)
   int* d_rank = nullptr;
   s = pcp::seed_pcp_async(P->d_Ms, P->mp, P->np, P->lam_seed, q.seed_tol,
                           q.seed_rho, q.seed_mu_scale, q.seed_mu_max_ratio,
                           q.seed_max_iter, P->k0, P->kmax, q.rank_cut, P->r,
                           P->d_seed_work, P->d_U, P->d_Sigma, P->d_V, st,
-                          &d_rank, q.seed_ctas);
+                          &d_rank, q.seed_ctas,
+                          q.wait_timeout_ns > 0
+                              ? (unsigned long long)q.wait_timeout_ns
+                              : 0ull,
+                          &P->launches, &P->seed_team);
   if (s != PCP_OK) return s;
   // stage 5 (seed rows of the factors) + FP32 bases for the filters
   s = pcp_assemble_factors(P->d_U, P->d_Sigma, P->d_V, P->mp, P->np, P->kmax,
                            d_rank, P->r, P->d_rows, P->d_cols, dLu, P->m, dLv,
                            P->n, P->d_U32, P->d_V32, P->d_inv_sigma, st);
   if (s != PCP_OK) return s;
+  ++P->launches;
   if (timed) PCP_CUDA(cudaEventRecord(P->ev[1], st));
   if (hio) PCP_CUDA(cudaStreamWaitEvent(st, cev[1], 0));  // all of M landed
   // stages 3 and 4: column and row filtering (Algorithm 1), the row filter
@@ -731,12 +746,14 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
                     q.beta_bar_ratio, q.filter_max_iter, q.precision,
                     q.lowp_iters, P->d_iters, st);
   if (s != PCP_OK) return s;
+  P->launches += ncb > 0;
   s = pcp_l1_filter(dM, P->d_cols, P->np, ldm, P->d_rbar, (int32_t)nrb, 1,
                     P->d_V32, P->np, P->r, d_rank, P->d_inv_sigma, dLu, P->m,
                     q.filter_tol, q.filter_rho, q.beta0_scale,
                     q.beta_bar_ratio, q.filter_max_iter, q.precision,
                     q.lowp_iters, P->d_iters + ncb, P->side_st);
   if (s != PCP_OK) return s;
+  P->launches += nrb > 0;
   PCP_CUDA(cudaEventRecord(P->join_ev, P->side_st));
   PCP_CUDA(cudaStreamWaitEvent(st, P->join_ev, 0));
   if (timed) PCP_CUDA(cudaEventRecord(P->ev[2], st));
@@ -760,6 +777,7 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
       s = pcp_spass(dM + j0 * ldm, ldm, dLu, P->m, dLv + j0, P->n, P->r,
                     dS + j0 * lds, lds, P->m, nc, st);
       if (s != PCP_OK) return s;
+      ++P->launches;
       PCP_CUDA(cudaEventRecord(cev[4 + c], st));
       PCP_CUDA(cudaStreamWaitEvent(P->copy_st, cev[4 + c], 0));
       PCP_CUDA(cudaMemcpy2DAsync(hio->hS + j0 * hio->lds,
@@ -771,6 +789,7 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
     s = pcp_spass(dM, ldm, dLu, P->m, dLv, P->n, P->r, dS, lds, P->m, P->n,
                   st);
     if (s != PCP_OK) return s;
+    ++P->launches;
   }
   if (hio) {
     // this stream's later work (and its synchronisation) follows the copies
@@ -824,6 +843,12 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
   info->filter_iters_max = imax;
   info->problems_unconverged = unconv;
   info->filter_iters_mean = it.empty() ? 0.0 : isum / (double)it.size();
+  info->filter_kernel =
+      pcp_l1_filter_kernel(P->mp, P->r, q.precision) == PCP_KERNEL_SIMT
+          ? PCP_KERNEL_SIMT
+          : PCP_KERNEL_TENSOR;
+  info->launches = P->launches;
+  info->seed_team = P->seed_team;
   // Eq. rank_test on the numerical rank before the cap at the target r
   info->rank_ok = (rank_raw >= 1 &&
                    (double)P->mp / rank_raw >= q.s_r - 1e-9 &&

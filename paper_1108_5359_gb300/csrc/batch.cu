@@ -337,6 +337,8 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
     t.U = reinterpret_cast<double*>(base + o_U[i]);
     t.Sigma = reinterpret_cast<double*>(base + o_Sig[i]);
     t.V = reinterpret_cast<double*>(base + o_V[i]);
+    t.timeout_ns = q.wait_timeout_ns > 0 ? (unsigned long long)q.wait_timeout_ns
+                                         : 0ull;
     b.d_rank = seed_rank_ptr_cta(b.d_work, b.mp, b.np, b.kmax);
     float* U32 = reinterpret_cast<float*>(base + o_U32[i]);
     float* V32 = reinterpret_cast<float*>(base + o_V32[i]);

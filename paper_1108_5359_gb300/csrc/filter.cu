@@ -37,7 +37,6 @@
 //     never write again) so every problem stops exactly at its own test.
 #include <algorithm>
 #include <atomic>
-#include <mutex>
 #include <cstring>
 #include <vector>
 
@@ -313,15 +312,15 @@ size_t args_block_bytes(int nsets) {
 
 }  // namespace
 
-// ---- kernel choice for PCP_FP32 (autotuned) --------------------------------
+// ---- kernel choice for PCP_FP32 ---------------------------------------------
 // PCP_FP32 asks for FP32 accuracy without naming a kernel.  For shapes both
-// kernels take (p <= 256, r <= 32) the first pcp_l1_filter call of each
-// (p class, r class) times the two kernels on its own problems and keeps the
-// faster one for the rest of the process; the tensor-core kernel is the
-// choice until then (and for the batched form, which never tunes).
+// kernels take (p <= 256, r <= 32) the choice is read from a table compiled
+// into the library (filter_table.inc, written by a tuning run that timed
+// both kernels per class), so it is a function of the shape alone: the same
+// input gives the same bits in every process and in the single, batched
+// and served forms.
 namespace {
-std::mutex g_tune_mu;
-int g_tune[3][4] = {};  // [p <= 64/128/256][r class]: 0 untuned, 1 SIMT, 2 TC
+#include "filter_table.inc"
 
 int tune_slot_p(int p) { return p <= 64 ? 0 : (p <= 128 ? 1 : 2); }
 int tune_slot_r(int r) { return (r - 1) / 8; }
@@ -331,8 +330,7 @@ bool filter_uses_simt(int precision, int p, int r) {
   if (p > 256 || r > 32) return false;
   if (precision == PCP_FP32_SIMT) return true;
   if (precision != PCP_FP32) return false;
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  return g_tune[tune_slot_p(p)][tune_slot_r(r)] == 1;
+  return kFp32KernelTable[tune_slot_p(p)][tune_slot_r(r)] == PCP_KERNEL_SIMT;
 }
 
 size_t filter_batch_bytes(const FilterSet* sets, int nsets) {
@@ -488,41 +486,6 @@ extern "C" pcp_status pcp_l1_filter(
     if (p <= 128) return pcp::dispatch_r<16>(a, st);
     return pcp::dispatch_r<32>(a, st);
   };
-  int tuned = 0;
-  if (precision == PCP_FP32 && p <= 256 && r <= 32) {
-    std::lock_guard<std::mutex> lock(pcp::g_tune_mu);
-    tuned = pcp::g_tune[pcp::tune_slot_p(p)][pcp::tune_slot_r(r)];
-  }
-  if (precision == PCP_FP32 && p <= 256 && r <= 32 && tuned == 0) {
-    // time both kernels on these problems (each writes the full result)
-    // twice, the first round absorbing module loading and clock ramp-up;
-    // keep the faster by its best time, and make sure its result is the
-    // one left in Z
-    cudaEvent_t ev[5];
-    for (auto& x : ev) PCP_CUDA(cudaEventCreate(&x));
-    PCP_CUDA(cudaEventRecord(ev[0], st));
-    for (int round = 0; round < 2; ++round) {
-      if ((e = run_simt()) != cudaSuccess)
-        return pcp::cuda_fail(e, "adm_f32_kernel launch", __FILE__, __LINE__);
-      PCP_CUDA(cudaEventRecord(ev[1 + 2 * round], st));
-      if ((e = pcp::l1_filter_tc_launch(a, st)) != cudaSuccess)
-        return pcp::cuda_fail(e, "adm_tc_kernel launch", __FILE__, __LINE__);
-      PCP_CUDA(cudaEventRecord(ev[2 + 2 * round], st));
-    }
-    PCP_CUDA(cudaEventSynchronize(ev[4]));
-    float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int q = 0; q < 4; ++q) cudaEventElapsedTime(&t[q], ev[q], ev[q + 1]);
-    for (auto& x : ev) cudaEventDestroy(x);
-    const float t_simt = std::min(t[0], t[2]), t_tc = std::min(t[1], t[3]);
-    const int choice = t_simt < t_tc ? 1 : 2;
-    {
-      std::lock_guard<std::mutex> lock(pcp::g_tune_mu);
-      pcp::g_tune[pcp::tune_slot_p(p)][pcp::tune_slot_r(r)] = choice;
-    }
-    if (choice == 1 && (e = run_simt()) != cudaSuccess)
-      return pcp::cuda_fail(e, "adm_f32_kernel launch", __FILE__, __LINE__);
-    return PCP_OK;
-  }
   if (pcp::filter_uses_simt(precision, p, r)) {
     if ((e = run_simt()) != cudaSuccess)
       return pcp::cuda_fail(e, "adm_f32_kernel launch", __FILE__, __LINE__);
@@ -532,4 +495,17 @@ extern "C" pcp_status pcp_l1_filter(
       return pcp::cuda_fail(e, "adm_tc_kernel launch", __FILE__, __LINE__);
   }
   return PCP_OK;
+}
+
+extern "C" int32_t pcp_l1_filter_kernel(int32_t p, int32_t r,
+                                        int32_t precision) {
+  PCP_ARG(p >= 1 && p <= 512 && r >= 1 && r <= 64,
+          "pcp_l1_filter_kernel: p=%d r=%d outside [1, 512] x [1, 64]", p, r);
+  PCP_ARG(precision >= PCP_FP32 && precision <= PCP_FP32_SIMT &&
+              precision != PCP_FP64,
+          "pcp_l1_filter_kernel: precision %d not available", precision);
+  PCP_ARG(precision != PCP_FP32_SIMT || (p <= 256 && r <= 32),
+          "pcp_l1_filter_kernel: the SIMT form takes p <= 256 and r <= 32");
+  return pcp::filter_uses_simt(precision, p, r) ? PCP_KERNEL_SIMT
+                                                : PCP_KERNEL_TENSOR;
 }

@@ -9,7 +9,7 @@ namespace pcp {
 // workspace): barrier state, status and diagnostics.
 struct SeedCtl {
   unsigned int bar_count;  // grid barrier arrivals since the launch
-  unsigned int pad0;
+  int fin_sweeps;          // Jacobi sweeps of the final FP64 SVD of the core
   int error;
   int iters;
   int rank;
@@ -33,6 +33,7 @@ struct SeedTask {
   double lam, tol, rho, mu_scale, mu_max_ratio, rank_cut;
   void* work;  // seed_workspace_bytes_cta(mp, np, kmax) bytes
   double *U, *Sigma, *V;  // outputs, ld mp / np, kmax columns
+  unsigned long long timeout_ns;  // limit of one barrier wait; 0 = default
 };
 
 size_t seed_workspace_bytes_cta(int mp, int np, int kmax);

@@ -52,6 +52,17 @@ constexpr int kSeedTraceCap = 4096;  // (timestamp, phase) records
 constexpr int kSeedTeamMax = 64;     // largest team of the batched solver
 constexpr int kSeedMaxSide = 512;    // largest m', n'
 constexpr int kSeedGemmGroup = 4;    // tasks per pass of the tall products
+// The tall and rank-k products of the ALM run in FP32 while its residual is
+// above this (their ~1e-7 relative error is far below what the inexact ALM
+// leaves there), FP64 after.
+#ifndef PCP_SEED_LOWP_RES
+#define PCP_SEED_LOWP_RES 1e-4
+#endif
+constexpr double kSeedLowpRes = PCP_SEED_LOWP_RES;
+// Largest single-cluster team (a non-portable cluster size on this part).
+constexpr int kSeedClusterMax = 16;
+// limit of one grid-barrier wait when the caller gives none
+constexpr unsigned long long kSeedDefaultWaitNs = 2000000000ull;  // 2 s
 // Partial-sum slots of the grid solver: fixed, so a solve's result does not
 // depend on its CTA count; one per SM of this part (a sweep on the 200 x 200
 // seed: 3.34 ms with 512 slots, 3.05 ms with 152, 3.15 ms with 76; on the
@@ -115,6 +126,9 @@ struct alignas(16) SeedArgs {
   int mp, np, kmax, k0;
   double lam, tol, rho, mu_scale, mu_max_ratio, rank_cut;
   int max_iter, r_cap;
+  // the tall and rank-k products run in FP32 while the ALM residual is
+  // above this, FP64 after
+  double lowp_res;
   // partial-sum slots of the three reductions (norms of D, Ritz values,
   // residual): fixed per solve, so the summation order (and the result)
   // does not depend on how many CTAs the team has
@@ -155,7 +169,6 @@ __device__ bool grid_sync(SeedCtl* ctl, unsigned int nblocks,
                  : "memory");
     const unsigned int target = (arrived / nblocks + 1) * nblocks;
     const unsigned long long t0 = globaltimer_ns();
-    unsigned int spins = 0;
     while (true) {
       unsigned int cur;
       asm volatile("ld.acquire.gpu.u32 %0, [%1];"
@@ -164,7 +177,9 @@ __device__ bool grid_sync(SeedCtl* ctl, unsigned int nblocks,
                    : "memory");
       if ((int)(cur - target) >= 0) break;
       if (*(volatile int*)&ctl->error) break;
-      if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > timeout_ns) {
+      // the clock is read on every spin (each spin is an L2 round trip, far
+      // longer than the read), so a wait ends within one spin of its limit
+      if (globaltimer_ns() - t0 > timeout_ns) {
         atomicExch(&ctl->error, (int)PCP_ERR_TIMEOUT);
         break;
       }
@@ -639,12 +654,223 @@ __device__ float* block_jacobi32(float* A0, float* A1, float* V, int k,
   return A;
 }
 
-// The ALM body, run by a team of CTAs: the whole cooperative grid (kGrid,
-// phases separated by the software grid barrier) or a single CTA (one seed
-// per CTA, phases separated by __syncthreads).  b / nb: this CTA's position
-// in the team.
-template <bool kGrid>
+// ---- FP64 finalisation helpers (the skinny SVD of the converged iterate) ---
+
+// Gm[a*kmax + b] = sc_a sc_b sum_t X[t*kmax + sel_a] X[t*kmax + sel_b] for
+// a, b < nk (sc = 1 when null); one warp per entry a <= b with a fixed
+// summation order, both triangles written.
+__device__ void gram_sel(const double* X, int nrows, int kmax, const int* sel,
+                         const double* sc, int nk, double* Gm, int bid,
+                         int nblk) {
+  const int lane = threadIdx.x & 31;
+  const int gw = bid * (kSeedThreads / 32) + (threadIdx.x >> 5);
+  const int nw = nblk * (kSeedThreads / 32);
+  const int npairs = nk * (nk + 1) / 2;
+  for (int pq = gw; pq < npairs; pq += nw) {
+    int a = 0, rem = pq;
+    while (rem >= nk - a) {
+      rem -= nk - a;
+      ++a;
+    }
+    const int b = a + rem;
+    const int ca = sel[a], cb = sel[b];
+    double s0 = 0.0, s1 = 0.0;
+    int t = lane;
+    for (; t + 32 < nrows; t += 64) {
+      s0 = fma(ldg_cg(X + (size_t)t * kmax + ca),
+               ldg_cg(X + (size_t)t * kmax + cb), s0);
+      s1 = fma(ldg_cg(X + (size_t)(t + 32) * kmax + ca),
+               ldg_cg(X + (size_t)(t + 32) * kmax + cb), s1);
+    }
+    for (; t < nrows; t += 32)
+      s0 = fma(ldg_cg(X + (size_t)t * kmax + ca),
+               ldg_cg(X + (size_t)t * kmax + cb), s0);
+    double v = warp_sum(s0 + s1);
+    if (sc) v = v * sc[a] * sc[b];
+    if (lane == 0) {
+      __stcg(Gm + a * kmax + b, v);
+      __stcg(Gm + b * kmax + a, v);
+    }
+  }
+}
+
+// 1/sqrt(x) to FP64 accuracy without the FP64 divide / square-root
+// sequences (hundreds of cycles on this part): an FP32 estimate refined by
+// two Newton steps y <- y (3/2 - x y^2 / 2), each doubling the correct bits
+// (~2^-23 -> 2^-46 -> full).  0 for x <= 0 (a dead direction).
+__device__ __forceinline__ double rsqrt_f64(double x) {
+  if (!(x > 0.0)) return 0.0;
+  float xf = (float)x;
+  double y;
+  if (xf > 0.0f && xf < 3.0e38f) {
+    y = (double)rsqrtf(xf);
+  } else {
+    y = 1.0 / sqrt(x);  // outside the FP32 range (not met in practice)
+  }
+  const double h = 0.5 * x;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
+// Cholesky A = R^T R (R upper) of two nk x nk SPD matrices in FP64, in
+// place (row-major, stride nk), side by side.  Step j: threads 0 and 32
+// form y_j = 1/sqrt(a_jj) of their matrix; then every trailing entry
+// a_ab -= (a_ja a_jb) y_j^2 (a <= b, both > j) with row j left unscaled; at
+// the end row j is scaled by y_j (R_jj = sqrt(a_jj), R_jb = a_jb / R_jj) and
+// the strict lower triangle zeroed.  y0 / y1 keep the reciprocal pivots
+// 1 / R_jj.  A non-positive pivot gives y = 0: that row of R is zero.
+__device__ void chol2_f64(double* A0, double* A1, int nk, double* y0,
+                          double* y1) {
+  const int tid = threadIdx.x;
+  for (int j = 0; j < nk; ++j) {
+    if (tid == 0) y0[j] = rsqrt_f64(A0[j * nk + j]);
+    if (tid == 32) y1[j] = rsqrt_f64(A1[j * nk + j]);
+    __syncthreads();
+    const int w = nk - j - 1;
+    const double yy0 = y0[j] * y0[j], yy1 = y1[j] * y1[j];
+    for (int idx = tid; idx < 2 * w * w; idx += kSeedThreads) {
+      const int m = idx >= w * w;
+      const int e = idx - m * w * w;
+      const int ra = j + 1 + e / w, rb = j + 1 + e % w;
+      if (rb < ra) continue;
+      double* A = m ? A1 : A0;
+      const double yy = m ? yy1 : yy0;
+      A[ra * nk + rb] =
+          fma(-(A[j * nk + ra] * yy), A[j * nk + rb], A[ra * nk + rb]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < 2 * nk * nk; idx += kSeedThreads) {
+    const int m = idx >= nk * nk;
+    const int e = idx - m * nk * nk;
+    const int ra = e / nk, rb = e - ra * nk;
+    double* A = m ? A1 : A0;
+    const double* y = m ? y1 : y0;
+    A[e] = rb >= ra ? A[e] * y[ra] : 0.0;
+  }
+  __syncthreads();
+}
+
+// Solve R X = B in place for two upper-triangular systems (R0 X0 = B0,
+// R1 X1 = B1; nk x nk, row-major, reciprocal pivots y0 / y1), all columns at
+// once: row a from the last up, x_a = b_a / R_aa, then b_c -= R_ca x_a for
+// the rows c above it.
+__device__ void backsub2_f64(const double* R0, const double* R1, double* B0,
+                             double* B1, int nk, const double* y0,
+                             const double* y1) {
+  const int tid = threadIdx.x;
+  for (int ra = nk - 1; ra >= 0; --ra) {
+    for (int idx = tid; idx < 2 * nk; idx += kSeedThreads) {
+      const int m = idx >= nk, q = idx - m * nk;
+      double* B = m ? B1 : B0;
+      B[ra * nk + q] *= (m ? y1 : y0)[ra];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 2 * ra * nk; idx += kSeedThreads) {
+      const int m = idx >= ra * nk;
+      const int e = idx - m * ra * nk;
+      const int rc = e / nk, q = e - rc * nk;
+      double* B = m ? B1 : B0;
+      const double* R = m ? R1 : R0;
+      B[rc * nk + q] = fma(-R[rc * nk + ra], B[ra * nk + q], B[rc * nk + q]);
+    }
+    __syncthreads();
+  }
+}
+
+// One-sided (Hestenes) Jacobi in FP64 on the columns of the nk x nk matrix
+// C (row-major), accumulating the rotations in W (set to I here): on
+// return C's columns are orthogonal (C_in W = C_out) and W is orthogonal.
+// Parallel round-robin ordering (every pair of columns meets once per
+// sweep), one warp per pair, lanes over rows.  The pair (p, q), p < q, is
+// rotated when (x.y)^2 > 1e-28 (x.x)(y.y): t = tan of the angle from the
+// FP32 quadratic formula (the next sweep corrects its FP32 error), c =
+// (1 + t^2)^-1/2 by rsqrt_f64, s = t c, so every rotation is orthogonal to
+// FP64 rounding.  Sweeps until one rotates nothing (at most 16).  Returns
+// the number of sweeps.
+__device__ int hestenes_f64(double* C, double* W, int nk) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  for (int idx = tid; idx < nk * nk; idx += kSeedThreads)
+    W[idx] = (idx / nk == idx % nk) ? 1.0 : 0.0;
+  __syncthreads();
+  if (nk < 2) return 0;
+  const int nkp = (nk + 1) & ~1;
+  const int half = nkp / 2;
+  int sweep = 0;
+  while (sweep < 16) {
+    ++sweep;
+    int rot = 0;
+    for (int rd = 0; rd < nkp - 1; ++rd) {
+      for (int i = wid; i < half; i += kSeedThreads / 32) {
+        const int s0 = i, s1 = nkp - 1 - i;  // slots of the pair
+        const int x0 = s0 == 0 ? 0 : 1 + (s0 - 1 + rd) % (nkp - 1);
+        const int x1 = 1 + (s1 - 1 + rd) % (nkp - 1);
+        const int p = min(x0, x1), q = max(x0, x1);
+        if (q >= nk) continue;  // padding column (odd nk)
+        const int r0 = lane, r1 = lane + 32;
+        const double xp0 = r0 < nk ? C[r0 * nk + p] : 0.0;
+        const double xq0 = r0 < nk ? C[r0 * nk + q] : 0.0;
+        const double xp1 = r1 < nk ? C[r1 * nk + p] : 0.0;
+        const double xq1 = r1 < nk ? C[r1 * nk + q] : 0.0;
+        const double al = warp_sum(fma(xp0, xp0, xp1 * xp1));
+        const double be = warp_sum(fma(xq0, xq0, xq1 * xq1));
+        const double ga = warp_sum(fma(xp0, xq0, xp1 * xq1));
+        if (!(al > 0.0 && be > 0.0 && ga * ga > 1e-28 * al * be)) continue;
+        const float z = (float)(be - al) / (2.0f * (float)ga);
+        const float tf = copysignf(1.0f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.0f)));
+        if (tf == 0.0f) continue;
+        rot = 1;
+        const double t = (double)tf;
+        const double c = rsqrt_f64(fma(t, t, 1.0));
+        const double sn = t * c;
+        if (r0 < nk) {
+          C[r0 * nk + p] = fma(c, xp0, -sn * xq0);
+          C[r0 * nk + q] = fma(sn, xp0, c * xq0);
+          const double wp = W[r0 * nk + p], wq = W[r0 * nk + q];
+          W[r0 * nk + p] = fma(c, wp, -sn * wq);
+          W[r0 * nk + q] = fma(sn, wp, c * wq);
+        }
+        if (r1 < nk) {
+          C[r1 * nk + p] = fma(c, xp1, -sn * xq1);
+          C[r1 * nk + q] = fma(sn, xp1, c * xq1);
+          const double wp = W[r1 * nk + p], wq = W[r1 * nk + q];
+          W[r1 * nk + p] = fma(c, wp, -sn * wq);
+          W[r1 * nk + q] = fma(sn, wp, c * wq);
+        }
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rot)) break;
+  }
+  return sweep;
+}
+
+// Hardware barrier over the CTAs of this thread-block cluster, with release
+// / acquire ordering of their memory operations at cluster scope (the
+// cross-CTA data lives in global memory and is read with L2 loads).  Every
+// thread of every CTA of the cluster calls it the same number of times.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n"
+      "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// How a seed's team of CTAs separates the phases of an ALM iteration.
+enum { kTeamCta = 0,      // one CTA: __syncthreads
+       kTeamGrid = 1,     // cooperative grid: software grid barrier
+       kTeamCluster = 2   // one thread-block cluster: hardware barrier
+};
+
+// The ALM body, run by a team of CTAs: a cooperative grid (phases separated
+// by the software grid barrier), one thread-block cluster (the hardware
+// cluster barrier) or a single CTA (one seed per CTA, __syncthreads).
+// b / nb: this CTA's position in the team.  The partial-sum slots of the
+// reductions are fixed per solve, so every team form gives the same bits.
+template <int kMode>
 __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
+  constexpr bool kGrid = kMode != kTeamCta;  // a team of several CTAs
   extern __shared__ __align__(16) double sm[];
   const int kmax = a.kmax;
   double* red = sm;                      // kSeedThreads
@@ -673,8 +899,11 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
       kGrid ? max(1, min(kSeedThreads / 32, (max(mp, np) + nb - 1) / nb))
             : kSeedThreads / 32;
   auto team_sync = [&]() -> bool {
-    if (kGrid) return grid_sync(ctl, nb, tmo);
-    __syncthreads();
+    if (kMode == kTeamGrid) return grid_sync(ctl, nb, tmo);
+    if (kMode == kTeamCluster)
+      cluster_sync_all();
+    else
+      __syncthreads();
     return true;
   };
 
@@ -751,8 +980,8 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
 
   while (true) {
     // ---- T = G^T Omega ------------------------------------------------------
-    tall_gemm_t(a.G, mp, mp, np, a.Om, res > 1e-4 ? a.Om32 : nullptr, k, kmax,
-                a.T, gred, xs, b, nb);
+    tall_gemm_t(a.G, mp, mp, np, a.Om, res > a.lowp_res ? a.Om32 : nullptr, k,
+                kmax, a.T, gred, xs, b, nb);
     if (!team_sync()) return;
     trace_mark(a, 2);
     gram(a.T, np, k, kmax, a.Gam, b, nb);
@@ -763,8 +992,8 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     if (!team_sync()) return;
     trace_mark(a, 4);
     // ---- P = G Psi ------------------------------------------------------------
-    tall_gemm_t(a.Gt, np, np, mp, a.Psi, res > 1e-4 ? a.Psi32 : nullptr, k,
-                kmax, a.P, gred, xs, b, nb);
+    tall_gemm_t(a.Gt, np, np, mp, a.Psi, res > a.lowp_res ? a.Psi32 : nullptr,
+                k, kmax, a.P, gred, xs, b, nb);
     if (stage >= 2) gram(a.Psi, np, k, kmax, a.Gam2, b, nb);  // E = Psi1^T Psi1 - I
     if (!team_sync()) return;
     trace_mark(a, 5);
@@ -1189,7 +1418,7 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     // their ~1e-7 relative error is far below what the inexact ALM leaves
     // at that point, and this part's FP64 pipe (2 FMA/clk/SM) made them the
     // update's cost on the 500 x 500 seed.  Every later iteration is FP64.
-    const bool lowp = res > 1e-4;
+    const bool lowp = res > a.lowp_res;
     if (TT > 0) {
       const int kp = k | 1;  // odd row pitch: conflict-free reads
       double* Pts = Vd;                 // [TT][kp]
@@ -1300,51 +1529,143 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     k = knext;
   }
 
-  // ---- outputs: skinny SVD of L^s sorted by decreasing singular value -------
-  // this iteration's factors: U = Pt / s, Sigma = s - tau, V = PsiT;
-  // rank = #{s - tau > rank_cut * max(s - tau)}, capped at r_cap.
+  // ---- outputs: the skinny SVD of L^s in FP64 ------------------------------
+  // The iterate is L^s = Pt diag(d) PsiT^T.  Its bases carry the ~1e-7 loss
+  // of orthogonality of the FP32 k x k factorisations, while Algorithm 1
+  // (step 2, Eq. l1g) takes A^T A = I; so the factors are re-orthonormalised
+  // once here, in FP64.  With K the nk columns whose Ritz value s exceeds
+  // tau (the rest are shrunk to zero):
+  //   Ut = Pt_K diag(1/s_K),  Vt = PsiT_K            (nearly orthonormal)
+  //   Ut = Qu Ru,  Vt = Qv Rv                        (Cholesky QR, FP64)
+  //   C = Ru diag(s_K - tau) Rv^T                    (nk x nk, ~diagonal)
+  //   C Wv = Wu diag(sigma)                          (one-sided Jacobi, FP64)
+  //   U^s = Ut Ru^-1 Wu,  V^s = Vt Rv^-1 Wv,  Sigma^s = sigma (sorted)
+  // so U^s Sigma^s V^sT is the iterate's L^s to FP64 rounding and U^s, V^s
+  // are orthonormal to FP64 rounding.  rank = #{sigma > rank_cut sigma_1},
+  // capped at r_cap.
+  __shared__ double f_is[kSeedKmaxLimit];   // 1 / s_K
+  __shared__ double f_sig[kSeedKmaxLimit];  // sigma_K (scaled), then sigma
+  __shared__ double f_y[2][kSeedKmaxLimit]; // reciprocal pivots of Ru, Rv
+  __shared__ int f_sel[kSeedKmaxLimit];     // K
+  __shared__ int f_ord[kSeedKmaxLimit];     // output order (decreasing sigma)
+  __shared__ int f_n[3];                    // nk, rank, rank before the cap
+  __shared__ double f_p2;                   // power-of-two scale of C
   if (tid == 0) {
-    int* order = prs;
-    int cnt = 0;
-    for (int c = 0; c < k; ++c) order[c] = c;
-    for (int x = 1; x < k; ++x) {  // insertion sort, decreasing s
-      const int v = order[x];
-      int y = x - 1;
-      while (y >= 0 && lam[order[y]] < lam[v]) {
-        order[y + 1] = order[y];
-        --y;
+    int nk = 0;
+    double smx = 0.0;
+    for (int c = 0; c < k; ++c)
+      if (lam[c] > tau) {
+        f_sel[nk++] = c;
+        smx = fmax(smx, lam[c] - tau);
       }
-      order[y + 1] = v;
-    }
-    const double top = lam[order[0]] - tau;
-    for (int c = 0; c < k; ++c) {
-      const double sv = lam[order[c]] - tau;
-      if (sv > 0.0 && sv > a.rank_cut * top) ++cnt;
-    }
-    dead[1] = cnt;
-    if (a.r_cap > 0) cnt = min(cnt, a.r_cap);
-    dead[0] = cnt;
+    f_n[0] = nk;
+    int e = 0;
+    frexp(smx, &e);
+    f_p2 = nk > 0 ? ldexp(1.0, -e) : 1.0;
   }
   __syncthreads();
-  const int rank = dead[0];
-  const int* order = prs;
+  const int nk = f_n[0];
+  for (int q = tid; q < nk; q += kSeedThreads) {
+    const double sq = lam[f_sel[q]];
+    f_is[q] = 1.0 / sq;
+    f_sig[q] = (sq - tau) * f_p2;
+  }
+  __syncthreads();
+  // Grams of Ut and Vt (distributed over the team, fixed summation order)
+  gram_sel(Ptc, mp, kmax, f_sel, f_is, nk, a.Gam, b, nb);
+  gram_sel(PsiTc, np, kmax, f_sel, nullptr, nk, a.Gam2, b, nb);
+  if (!team_sync()) return;
+  // every CTA: the same nk x nk factorisations on the same data (identical
+  // results), in the dynamic shared memory the iteration is done with
+  double* Ru = sm;
+  double* Rv = Ru + nk * nk;
+  double* Cm = Rv + nk * nk;
+  double* Wv = Cm + nk * nk;
+  for (int idx = tid; idx < nk * nk; idx += kSeedThreads) {
+    const int p = idx / nk, q = idx - p * nk;
+    Ru[idx] = ldg_cg(a.Gam + p * kmax + q);
+    Rv[idx] = ldg_cg(a.Gam2 + p * kmax + q);
+  }
+  __syncthreads();
+  chol2_f64(Ru, Rv, nk, f_y[0], f_y[1]);
+  for (int idx = tid; idx < nk * nk; idx += kSeedThreads) {
+    const int p = idx / nk, q = idx - p * nk;
+    double acc = 0.0;
+    for (int c = max(p, q); c < nk; ++c)
+      acc = fma(Ru[p * nk + c] * f_sig[c], Rv[q * nk + c], acc);
+    Cm[idx] = acc;
+  }
+  __syncthreads();
+  const int fsweeps = hestenes_f64(Cm, Wv, nk);
+  // sigma_q = ||C e_q||, Wu = C diag(1/sigma)
+  for (int q = tid; q < nk; q += kSeedThreads) {
+    double ss = 0.0;
+    for (int p = 0; p < nk; ++p) ss = fma(Cm[p * nk + q], Cm[p * nk + q], ss);
+    f_sig[q] = sqrt(ss);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < nk * nk; idx += kSeedThreads) {
+    const int q = idx - (idx / nk) * nk;
+    Cm[idx] = f_sig[q] > 0.0 ? Cm[idx] / f_sig[q] : 0.0;
+  }
+  __syncthreads();
+  // Mu = diag(1/s_K) Ru^-1 Wu (in Cm), Mv = Rv^-1 Wv (in Wv)
+  backsub2_f64(Ru, Rv, Cm, Wv, nk, f_y[0], f_y[1]);
+  for (int idx = tid; idx < nk * nk; idx += kSeedThreads)
+    Cm[idx] *= f_is[idx / nk];
+  if (tid == 0) {
+    for (int q = 0; q < nk; ++q) f_ord[q] = q;
+    for (int x = 1; x < nk; ++x) {  // insertion sort, decreasing sigma
+      const int v = f_ord[x];
+      int y = x - 1;
+      while (y >= 0 && f_sig[f_ord[y]] < f_sig[v]) {
+        f_ord[y + 1] = f_ord[y];
+        --y;
+      }
+      f_ord[y + 1] = v;
+    }
+    int cnt = 0;
+    const double top = nk > 0 ? f_sig[f_ord[0]] : 0.0;
+    for (int q = 0; q < nk; ++q) {
+      const double sv = f_sig[f_ord[q]];
+      if (sv > 0.0 && sv > a.rank_cut * top) ++cnt;
+    }
+    f_n[2] = cnt;
+    f_n[1] = a.r_cap > 0 ? min(cnt, a.r_cap) : cnt;
+  }
+  __syncthreads();
+  const int rank = f_n[1];
   for (int i = b; i < mp; i += nb)
-    for (int c = tid; c < kmax; c += kSeedThreads)
-      a.U[i + (size_t)c * mp] =
-          (c < rank) ? ldg_cg(Ptc + (size_t)i * kmax + order[c]) /
-                           lam[order[c]]
-                     : 0.0;
+    for (int c = tid; c < kmax; c += kSeedThreads) {
+      double acc = 0.0;
+      if (c < rank) {
+        const int oc = f_ord[c];
+        const double* pr = Ptc + (size_t)i * kmax;
+        for (int q = 0; q < nk; ++q)
+          acc = fma(ldg_cg(pr + f_sel[q]), Cm[q * nk + oc], acc);
+      }
+      a.U[i + (size_t)c * mp] = acc;
+    }
   for (int j = b; j < np; j += nb)
-    for (int c = tid; c < kmax; c += kSeedThreads)
-      a.V[j + (size_t)c * np] =
-          (c < rank) ? ldg_cg(PsiTc + (size_t)j * kmax + order[c]) : 0.0;
+    for (int c = tid; c < kmax; c += kSeedThreads) {
+      double acc = 0.0;
+      if (c < rank) {
+        const int oc = f_ord[c];
+        const double* pr = PsiTc + (size_t)j * kmax;
+        for (int q = 0; q < nk; ++q)
+          acc = fma(ldg_cg(pr + f_sel[q]), Wv[q * nk + oc], acc);
+      }
+      a.V[j + (size_t)c * np] = acc;
+    }
+  trace_mark(a, 15);
   if (b == 0) {
     for (int c = tid; c < kmax; c += kSeedThreads)
-      a.Sigma[c] = (c < rank) ? lam[order[c]] - tau : 0.0;
+      a.Sigma[c] = (c < rank) ? f_sig[f_ord[c]] / f_p2 : 0.0;
     if (tid == 0) {
       ctl->iters = it;
       ctl->rank = rank;
-      ctl->rank_raw = dead[1];
+      ctl->rank_raw = f_n[2];
+      ctl->fin_sweeps = fsweeps;
       ctl->converged = converged ? 1 : 0;
       ctl->residual = res;
       ctl->k_final = k;
@@ -1383,7 +1704,15 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
 
 __global__ void __launch_bounds__(kSeedThreads, 2)
     seed_alm_kernel(const SeedArgs a) {
-  seed_alm_body<true>(a, blockIdx.x, gridDim.x);
+  seed_alm_body<kTeamGrid>(a, blockIdx.x, gridDim.x);
+}
+
+// The same solve on one thread-block cluster (the whole grid is a single
+// cluster of up to kSeedClusterMax CTAs): phases separated by the hardware
+// cluster barrier instead of the software grid barrier.
+__global__ void __launch_bounds__(kSeedThreads, 1)
+    seed_alm_cluster_kernel(const SeedArgs a) {
+  seed_alm_body<kTeamCluster>(a, blockIdx.x, gridDim.x);
 }
 
 // Batched form: CTA x belongs to the team of seed team[x].x, at position
@@ -1396,9 +1725,9 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
   const int4 t = team[blockIdx.x];
   const SeedArgs a = args[t.x];
   if (t.z == 1)
-    seed_alm_body<false>(a, 0, 1);
+    seed_alm_body<kTeamCta>(a, 0, 1);
   else
-    seed_alm_body<true>(a, t.y, t.z);
+    seed_alm_body<kTeamGrid>(a, t.y, t.z);
 }
 
 // Control blocks start at zero (barrier counters included) before any team
@@ -1413,11 +1742,15 @@ __global__ void seed_ctl_zero_kernel(const SeedArgs* __restrict__ args,
 }
 
 size_t seed_smem_bytes(int kmax) {
-  return sizeof(double) * ((size_t)kmax * kmax + kSeedThreads +
-                           kSeedGemmGroup * (kSeedMaxSide + kSeedThreads) +
-                           4 * kmax) +
-         sizeof(float) * ((size_t)3 * kmax * kmax) +
-         sizeof(int) * 2 * kmax + (size_t)kmax * kmax;
+  const size_t iter = sizeof(double) * ((size_t)kmax * kmax + kSeedThreads +
+                                        kSeedGemmGroup *
+                                            (kSeedMaxSide + kSeedThreads) +
+                                        4 * kmax) +
+                      sizeof(float) * ((size_t)3 * kmax * kmax) +
+                      sizeof(int) * 2 * kmax + (size_t)kmax * kmax;
+  // the final FP64 SVD: Ru, Rv, C, Wv (nk x nk each, nk <= kmax)
+  const size_t fin = sizeof(double) * 4 * (size_t)kmax * kmax;
+  return std::max(iter, fin);
 }
 
 }  // namespace
@@ -1429,7 +1762,7 @@ void fill_seed_args(SeedArgs& a, const SeedLayout& L, char* w,
                     double rho, double mu_scale, double mu_max_ratio,
                     int max_iter, int k0, int kmax, double rank_cut,
                     int r_cap, double* dU, double* dSigma, double* dV,
-                    bool trace) {
+                    bool trace, unsigned long long timeout_ns) {
   a.D = dD;
   a.mp = mp;
   a.np = np;
@@ -1443,7 +1776,8 @@ void fill_seed_args(SeedArgs& a, const SeedLayout& L, char* w,
   a.rank_cut = rank_cut;
   a.max_iter = max_iter;
   a.r_cap = r_cap;
-  a.timeout_ns = 2000000000ull;  // 2 s per barrier wait
+  a.timeout_ns = timeout_ns > 0 ? timeout_ns : kSeedDefaultWaitNs;
+  a.lowp_res = kSeedLowpRes;
   a.nv = kSeedTeamMax;
   a.ctl = reinterpret_cast<SeedCtl*>(w + L.ctl);
   a.part = reinterpret_cast<double*>(w + L.part);
@@ -1501,7 +1835,7 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
     SeedArgs a;
     fill_seed_args(a, L, w, t.D, t.mp, t.np, t.lam, t.tol, t.rho, t.mu_scale,
                    t.mu_max_ratio, t.max_iter, t.k0, t.kmax, t.rank_cut,
-                   t.r_cap, t.U, t.Sigma, t.V, false);
+                   t.r_cap, t.U, t.Sigma, t.V, false, t.timeout_ns);
     std::memcpy(hb + (size_t)i * seed_args_bytes(), &a, sizeof(a));
     kmax_all = std::max(kmax_all, t.kmax);
   }
@@ -1576,17 +1910,54 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   return PCP_OK;
 }
 
+// Launch the solve as one cluster of nc CTAs.  PCP_ERR_UNSUPPORTED (nothing
+// launched) when the device cannot schedule such a cluster.
+static pcp_status seed_cluster_launch(const SeedArgs& a, int nc, size_t smem,
+                                      cudaStream_t st) {
+  PCP_CUDA(cudaFuncSetAttribute(seed_alm_cluster_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+  if (nc > 8)
+    PCP_CUDA(cudaFuncSetAttribute(
+        seed_alm_cluster_kernel,
+        cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nc);
+  cfg.blockDim = dim3(kSeedThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = nc;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int fit = 0;
+  if (cudaOccupancyMaxActiveClusters(&fit, seed_alm_cluster_kernel, &cfg) !=
+          cudaSuccess ||
+      fit < 1) {
+    cudaGetLastError();
+    return PCP_ERR_UNSUPPORTED;
+  }
+  PCP_CUDA(cudaLaunchKernelEx(&cfg, seed_alm_cluster_kernel, a));
+  return PCP_OK;
+}
+
 pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
                           double tol, double rho, double mu_scale,
                           double mu_max_ratio, int max_iter, int k0, int kmax,
                           double rank_cut, int r_cap, void* d_work,
                           double* dU, double* dSigma, double* dV,
-                          cudaStream_t st, int** d_rank_out, int ctas) {
+                          cudaStream_t st, int** d_rank_out, int ctas,
+                          unsigned long long timeout_ns, int* launches,
+                          int* team_out) {
   const SeedLayout L = seed_layout(mp, np, kmax, kMaxCoopBlocks);
   char* w = static_cast<char*>(d_work);
   SeedArgs a;
   fill_seed_args(a, L, w, dD, mp, np, lam, tol, rho, mu_scale, mu_max_ratio,
-                 max_iter, k0, kmax, rank_cut, r_cap, dU, dSigma, dV, true);
+                 max_iter, k0, kmax, rank_cut, r_cap, dU, dSigma, dV, true,
+                 timeout_ns);
   if (d_rank_out) *d_rank_out = &a.ctl->rank;
 
   const size_t smem = seed_smem_bytes(kmax);
@@ -1607,6 +1978,20 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
     set_error("seed PCP: kernel does not fit on an SM (smem %zu)", smem);
     return PCP_ERR_UNSUPPORTED;
   }
+  a.nv = kSeedGridSlots;
+  PCP_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(SeedCtl), st));
+  // One thread-block cluster of `ctas` CTAs (1 .. kSeedClusterMax) when
+  // asked for and the device can hold it; the same slots, so the same bits.
+  if (ctas >= 1 && ctas <= kSeedClusterMax) {
+    pcp_status cs = seed_cluster_launch(a, ctas, smem, st);
+    if (cs == PCP_OK) {
+      if (launches) ++*launches;
+      if (team_out) *team_out = ctas;
+      return PCP_OK;
+    }
+    if (cs != PCP_ERR_UNSUPPORTED) return cs;
+    ctas = 0;  // no room for the cluster: the grid form below
+  }
   // One CTA per SM, or one per column/row task (max(m', n')) when there are
   // fewer: a sweep on the 200 x 200 seed measured 3.58 ms at 152 CTAs
   // against 3.92 ms at 200 (48 SMs doubled up) and 3.9 ms at 304, and the
@@ -1617,11 +2002,11 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
   const int cap = std::min(sms * per_sm, kMaxCoopBlocks);
   const int grid = ctas > 0 ? std::min(ctas, cap)
                             : std::min(std::min(cap, sms), std::max(mp, np));
-  a.nv = kSeedGridSlots;
-  PCP_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(SeedCtl), st));
   void* args[] = {&a};
   PCP_CUDA(cudaLaunchCooperativeKernel((const void*)seed_alm_kernel, grid,
                                        kSeedThreads, args, smem, st));
+  if (launches) ++*launches;
+  if (team_out) *team_out = -grid;
   return PCP_OK;
 }
 
@@ -1678,7 +2063,7 @@ extern "C" pcp_status pcp_seed_pcp(const double* dD, int32_t mp, int32_t np,
   pcp_status s = pcp::seed_pcp_async(dD, mp, np, lambda, tol, rho, mu_scale,
                                      mu_max_ratio, max_iter, k0, kmax,
                                      rank_cut, r_cap, d_work, dU, dSigma, dV,
-                                     st, nullptr, 0);
+                                     st, nullptr, 0, 0, nullptr, nullptr);
   if (s != PCP_OK) return s;
   int rank = 0, iters = 0, conv = 0, err = 0;
   double resid = 0;

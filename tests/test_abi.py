@@ -132,3 +132,31 @@ def test_precision_forms_of_algorithm_1(lib):
                                None, None, None, 1, 1e-6, 1.5, 1.0, 1e10, 10,
                                prec, 4, None, None)
         assert st == want, (prec, st)
+
+
+def test_filter_kernel_choice_is_a_function_of_the_shape(lib):
+    # the PCP_FP32 kernel comes from the compiled-in tuning table: a host
+    # lookup, the same answer on every call and in every process
+    from paper_1108_5359_gb300 import _abi
+    k = lib.pcp_l1_filter_kernel
+    for p, r in ((50, 5), (200, 20), (250, 25), (256, 32)):
+        got = {k(p, r, _abi.PCP_FP32) for _ in range(3)}
+        assert len(got) == 1
+        assert got.pop() in (_abi.PCP_KERNEL_SIMT, _abi.PCP_KERNEL_TENSOR)
+    # shapes only one kernel takes, and the explicit forms
+    assert k(500, 50, _abi.PCP_FP32) == _abi.PCP_KERNEL_TENSOR
+    assert k(200, 40, _abi.PCP_FP32) == _abi.PCP_KERNEL_TENSOR
+    assert k(200, 20, _abi.PCP_FP32_SIMT) == _abi.PCP_KERNEL_SIMT
+    assert k(200, 20, _abi.PCP_FP32_TENSOR) == _abi.PCP_KERNEL_TENSOR
+    assert k(200, 20, _abi.PCP_BF16_REFINED) == _abi.PCP_KERNEL_TENSOR
+    assert k(600, 20, _abi.PCP_FP32) == _abi.PCP_ERR_ARG
+    assert k(300, 20, _abi.PCP_FP32_SIMT) == _abi.PCP_ERR_ARG
+    assert k(200, 20, _abi.PCP_FP64) == _abi.PCP_ERR_ARG
+
+
+def test_table_written_by_the_tuning_run_is_well_formed():
+    text = open(os.path.join(ROOT, "paper_1108_5359_gb300", "csrc",
+                             "filter_table.inc")).read()
+    rows = re.findall(r"\{\s*([12])\s*,\s*([12])\s*,\s*([12])\s*,\s*([12])\s*\}",
+                      text)
+    assert len(rows) == 3

@@ -190,3 +190,20 @@ def test_batch_grows_failed_seeds():
     L = to_host(Lu) @ to_host(Lv).T
     assert relerr(L, L0) < TOL and relerr(to_host(S), S0) < TOL
     assert infos[1].seed_m == 50
+
+
+def test_batch_matches_oracle_at_bench_seed_sizes():
+    # the batched seed teams at the batched bench's seed sizes (r up to 25,
+    # seeds up to 250 x 250), beside smaller instances, against the oracle
+    Ps = [synth.make_config("c2_5000_r20", seed=2, m=1300, n=1250),
+          synth.make_config("c2_5000_r20", seed=5, m=1100, n=900, r=25,
+                            density=0.08, lo=-50.0, hi=50.0),
+          synth.make_config("c1_500_r5", seed=3)]
+    st, out = _run_batch(Ps)
+    for i, (P, o) in enumerate(zip(Ps, out)):
+        assert o["info"]["status"] == 0, (i, o["info"])
+        M = P.M.astype(np.float32).astype(np.float64)
+        ref = l1filter.l1_filter_pcp(M, P.rows, P.cols, r=P.r)
+        assert o["info"]["rank"] == ref.rank == P.r
+        assert relerr(_L(o), ref.L) < TOL, i
+        assert relerr(o["S"].astype(np.float64), ref.S) < TOL, i

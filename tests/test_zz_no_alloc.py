@@ -7,21 +7,21 @@ device array owned by the library instead of a caller buffer.  This file
 runs last so that a failure here leaves every other test already run.
 
 Checked through the C ABI: two calls in a row on different seeds (so the
-second call starts from the first call's leftover scratch) give the same
-L^s, rank and iteration count as pcp_seed_pcp with its own workspace, within
-the tolerance the seed parity tests use; an oversized seed is refused with a
-clear error before any device work.
+second call starts from the first call's leftover scratch) give bit for bit
+the same U^s, Sigma^s, V^s, rank, iteration count and residual as
+pcp_seed_pcp with its own workspace.  Both run the same kernel on the same
+input, and the seed's reductions sum fixed partial-sum slots in a fixed
+order, so any difference would come from state left in the shared array by
+the previous call.  An oversized seed is refused with a clear error before
+any device work.
 """
 import numpy as np
 import pytest
 
 from paper_1108_5359_gb300 import synth
-from tests.gpuhelp import build_and_load, relerr, to_dev_cm, to_host
+from tests.gpuhelp import build_and_load, to_dev_cm, to_host
 
 pytestmark = pytest.mark.gpu
-
-TOL = 1e-6  # as in test_gpu_seed.py
-
 
 def _k(mp, np_, r):
     k0 = min((r + max(6, r // 4) + 1) // 2 * 2, min(mp, np_) // 2 * 2)
@@ -35,11 +35,6 @@ def _outputs(mp, np_, kmax):
     V = torch.zeros((kmax, np_), dtype=torch.float64, device="cuda").t()
     S = torch.zeros(kmax, dtype=torch.float64, device="cuda")
     return U, S, V
-
-
-def _lowrank(U, s, V, rank):
-    U, s, V = to_host(U), to_host(s), to_host(V)
-    return (U[:, :rank] * s[:rank]) @ V[:, :rank].T
 
 
 def _seed_problem(cfg, seed, **kw):
@@ -71,8 +66,9 @@ def test_static_matches_workspace_two_calls_in_a_row():
             a["mu_max_ratio"], a["max_iter"], a["k0"], a["kmax"],
             a["rank_cut"], a["r_cap"], U, S, V)
         torch.cuda.synchronize()
-        static_out.append((st, rank, iters, res, _lowrank(U, S, V, rank)))
-    for (D, r), (st, rank, iters, res, Ls) in zip(cases, static_out):
+        static_out.append((st, rank, iters, res,
+                           (to_host(U), to_host(S), to_host(V))))
+    for (D, r), (st, rank, iters, res, outs) in zip(cases, static_out):
         a = _args(D, r)
         U, S, V = _outputs(D.shape[0], D.shape[1], a["kmax"])
         work = torch.empty(pk.pcp_seed_workspace_bytes(D.shape[0], D.shape[1],
@@ -83,12 +79,12 @@ def test_static_matches_workspace_two_calls_in_a_row():
             a["mu_max_ratio"], a["max_iter"], a["k0"], a["kmax"],
             a["rank_cut"], a["r_cap"], work, U, S, V)
         torch.cuda.synchronize()
-        Lw = _lowrank(U, S, V, rank2)
         assert st == st2 == 0
         assert rank == rank2 == r
         assert iters == iters2
-        assert res <= 1e-7 and res2 <= 1e-7
-        assert relerr(Ls, Lw) < TOL
+        assert res == res2 and res <= 1e-7
+        for got, want in zip(outs, (to_host(U), to_host(S), to_host(V))):
+            np.testing.assert_array_equal(got, want)
 
 
 def test_static_refuses_oversized_seed():
