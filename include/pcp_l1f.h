@@ -282,6 +282,34 @@ void pcp_plan_destroy(pcp_plan* plan);
 pcp_status pcp_l1filter_batch(int32_t count, const pcp_problem* probs,
                               pcp_info* infos, void* stream);
 
+/* Batch plans: pcp_l1filter_batch with its workspace allocated once and its
+ * launches (batched gather, seed teams, assembly, one Algorithm 1 launch
+ * per kernel shape over every instance's problems, diagnostics, S passes)
+ * captured into a CUDA graph that each run replays.
+ *
+ * pcp_l1filter_batch_plan runs the batch once directly (on `stream`,
+ * synchronising it; instances with grow_seed settle their seed size as
+ * Section 3.5 says), then fixes every instance's seed at the size it ended
+ * with, allocates the workspace (cudaMalloc), uploads the index sets and
+ * captures the launches.  The plan copies the pcp_problem array and the
+ * host index arrays it points to; the device buffers (dM, dLu, dLv, dS)
+ * must stay valid for the plan's lifetime, and each run reads M and writes
+ * the outputs again.  PCP_ERR_ARG / PCP_ERR_CUDA / PCP_ERR_NOMEM on
+ * failure (no plan); a per-instance status such as PCP_ERR_RANK_TEST does
+ * not stop the plan (that instance keeps its last seed).
+ *
+ * pcp_l1filter_batch_run replays the graph on `stream`.  Without infos the
+ * call is asynchronous; with infos (count entries) it synchronises and
+ * fills one pcp_info per instance (t_total_ms = the replay; stage times 0)
+ * and returns the first non-OK status.  Runs of one plan must not overlap
+ * on the GPU (they share its workspace); different plans may. */
+typedef struct pcp_batch_plan pcp_batch_plan;
+pcp_status pcp_l1filter_batch_plan(int32_t count, const pcp_problem* probs,
+                                   void* stream, pcp_batch_plan** out);
+pcp_status pcp_l1filter_batch_run(pcp_batch_plan* plan, pcp_info* infos,
+                                  void* stream);
+void pcp_batch_plan_destroy(pcp_batch_plan* plan);
+
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of independent solves (no counterpart in
  * the paper, which solves one matrix at a time; built on the batched form).

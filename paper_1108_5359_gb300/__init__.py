@@ -32,7 +32,8 @@ __all__ = [
     "pcp_assemble_factors", "pcp_spass", "PCP_SPASS_AUTO", "PCP_SPASS_SIMT",
     "PCP_SPASS_TENSOR", "pcp_plan_seed_trace", "Plan",
     "solve", "load", "SEED_PHASES", "PCPProblem", "problem",
-    "pcp_l1filter_batch", "Server", "pcp_serve_create", "pcp_serve_submit",
+    "pcp_l1filter_batch", "BatchPlan", "pcp_l1filter_batch_plan",
+    "pcp_l1filter_batch_run", "pcp_batch_plan_destroy", "Server", "pcp_serve_create", "pcp_serve_submit",
     "pcp_serve_poll", "pcp_serve_wait", "pcp_serve_stop", "pcp_serve_destroy",
 ]
 
@@ -236,6 +237,53 @@ def pcp_l1filter_batch(problems, info=True, stream=None,
     if raise_on_error and st != PCP_OK:
         check(st, "pcp_l1filter_batch")
     return st, (list(infos)[:n] if infos is not None else None)
+
+
+class BatchPlan:
+    """Owns a pcp_batch_plan (workspace + captured graph of a batch) and the
+    problems' tensors it reads and writes on every run."""
+
+    def __init__(self, problems, stream=None):
+        n = len(problems)
+        self._problems = list(problems)
+        arr = (PCPProblem * max(n, 1))(*[q.c for q in problems])
+        self.count = n
+        self.handle = C.c_void_p()
+        check(load().pcp_l1filter_batch_plan(n, arr, _stream(stream),
+                                             C.byref(self.handle)),
+              "pcp_l1filter_batch_plan")
+
+    def run(self, info=True, stream=None, raise_on_error=True):
+        """Replay the batch; returns (status, [PCPInfo] or None)."""
+        infos = (PCPInfo * max(self.count, 1))() if info else None
+        st = load().pcp_l1filter_batch_run(self.handle, infos,
+                                           _stream(stream))
+        if raise_on_error and st != PCP_OK:
+            check(st, "pcp_l1filter_batch_run")
+        return st, (list(infos)[:self.count] if infos is not None else None)
+
+    def close(self):
+        if self.handle:
+            load().pcp_batch_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pcp_l1filter_batch_plan(problems, stream=None):
+    return BatchPlan(problems, stream)
+
+
+def pcp_l1filter_batch_run(plan, info=True, stream=None, raise_on_error=True):
+    return plan.run(info, stream, raise_on_error)
+
+
+def pcp_batch_plan_destroy(plan):
+    plan.close()
 
 
 class Server:

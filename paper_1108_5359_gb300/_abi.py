@@ -117,6 +117,10 @@ PROTOTYPES = {
     "pcp_plan_destroy": (None, [_vp]),
     "pcp_l1filter_batch": (_i32, [_i32, C.POINTER(PCPProblem),
                                   C.POINTER(PCPInfo), _vp]),
+    "pcp_l1filter_batch_plan": (_i32, [_i32, C.POINTER(PCPProblem), _vp,
+                                       C.POINTER(_vp)]),
+    "pcp_l1filter_batch_run": (_i32, [_vp, C.POINTER(PCPInfo), _vp]),
+    "pcp_batch_plan_destroy": (None, [_vp]),
     "pcp_serve_create": (_i32, [C.c_size_t, _i32, _i32, C.POINTER(_vp)]),
     "pcp_serve_submit": (_i32, [_vp, C.POINTER(PCPProblem),
                                 C.POINTER(C.c_uint64)]),

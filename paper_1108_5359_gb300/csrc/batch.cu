@@ -254,8 +254,17 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
   }
   const size_t fbytes = filter_batch_bytes(sets.data(), 2 * count);
   const size_t o_filt = take(fbytes);
-  h->bytes = off;
-  PCP_CUDA(cudaMallocAsync(&h->d_base, off, st));
+  if (h->size_only) {
+    h->bytes = off;
+    return PCP_OK;
+  }
+  if (h->prealloc) {
+    PCP_ARG(h->d_base && h->bytes >= off,
+            "batch: workspace of %zu bytes, %zu needed", h->bytes, off);
+  } else {
+    h->bytes = off;
+    PCP_CUDA(cudaMallocAsync(&h->d_base, off, st));
+  }
   char* base = static_cast<char*>(h->d_base);
 
   // ---- host staging: indices, then the argument blocks ----------------------
@@ -292,7 +301,7 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
   // indices are contiguous per instance; each instance's block is 256-byte
   // aligned, so copy instance by instance
   pos = 0;
-  for (int i = 0; i < count; ++i) {
+  for (int i = 0; i < count && !h->indices_ready; ++i) {
     const pcp_params& q = probs[i].params;
     PCP_CUDA(cudaMemcpyAsync(base + o_idx[i], hidx.data() + pos,
                              sizeof(int32_t) * (q.m + q.n),
@@ -469,7 +478,7 @@ pcp_status batch_finish(BatchHandle* h, pcp_info* infos, cudaStream_t st,
       cudaEventDestroy(e);
       e = nullptr;
     }
-  if (h->d_base) {
+  if (h->d_base && !h->prealloc) {
     PCP_CUDA(cudaFreeAsync(h->d_base, st));
     h->d_base = nullptr;
   }
@@ -560,4 +569,155 @@ extern "C" pcp_status pcp_l1filter_batch(int32_t count,
   for (int i = 0; i < count && s == PCP_OK; ++i)
     s = (pcp_status)infos[i].status;
   return s;
+}
+
+// ---------------------------------------------------------------------------
+// Batch plans: the batched solve with its workspace allocated once and its
+// launches captured into a CUDA graph that every run replays.
+struct pcp_batch_plan {
+  std::vector<pcp_problem> probs;            // the instances, seeds fixed
+  std::vector<std::vector<int64_t>> arrays;  // host index arrays they use
+  pcp::BatchHandle h;                         // workspace, argument blocks
+  cudaStream_t cap_st = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" void pcp_batch_plan_destroy(pcp_batch_plan* P) {
+  if (!P) return;
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->cap_st) cudaStreamDestroy(P->cap_st);
+  if (P->h.d_base) cudaFree(P->h.d_base);
+  delete P;
+}
+
+extern "C" pcp_status pcp_l1filter_batch_plan(int32_t count,
+                                              const pcp_problem* probs,
+                                              void* stream,
+                                              pcp_batch_plan** out) {
+  PCP_ARG(out, "pcp_l1filter_batch_plan: null output");
+  *out = nullptr;
+  PCP_ARG(count >= 1 && count <= 65535 && probs,
+          "pcp_l1filter_batch_plan: count %d outside [1, 65535] or null "
+          "problems", count);
+  cudaStream_t st = (cudaStream_t)stream;
+  // one batched solve settles every instance's seed (Section 3.5 growth
+  // where asked for); the plan keeps the seed each instance ended with
+  std::vector<pcp_info> inf(count);
+  pcp_status s = pcp_l1filter_batch(count, probs, inf.data(), stream);
+  if (s == PCP_ERR_ARG || s == PCP_ERR_CUDA || s == PCP_ERR_NOMEM ||
+      s == PCP_ERR_UNSUPPORTED || s == PCP_ERR_TIMEOUT)
+    return s;
+  pcp_batch_plan* P = new pcp_batch_plan();
+  P->probs.assign(probs, probs + count);
+  P->arrays.reserve(4 * (size_t)count);
+  auto keep = [&](const int64_t* v, int64_t len) -> const int64_t* {
+    if (!v) return nullptr;
+    P->arrays.emplace_back(v, v + len);
+    return P->arrays.back().data();
+  };
+  for (int i = 0; i < count; ++i) {
+    pcp_params& q = P->probs[i].params;
+    const int mp0 = q.seed_m > 0 ? q.seed_m : (int)std::llround(q.s_r * q.r);
+    const int np0 = q.seed_n > 0 ? q.seed_n : (int)std::llround(q.s_c * q.r);
+    const bool grown = q.grow_seed && (inf[i].seed_m != mp0 ||
+                                       inf[i].seed_n != np0);
+    if (grown) {
+      // the growth took prefixes of these orders (the library's sampling
+      // order when none was given)
+      if (!q.row_order) {
+        P->arrays.push_back(pcp::sample_order(q.m, q.rng_seed));
+        q.row_order = P->arrays.back().data();
+      } else {
+        q.row_order = keep(q.row_order, q.m);
+      }
+      if (!q.col_order) {
+        P->arrays.push_back(pcp::sample_order(q.n, q.rng_seed ^ 0xC01C01C0ull));
+        q.col_order = P->arrays.back().data();
+      } else {
+        q.col_order = keep(q.col_order, q.n);
+      }
+      q.seed_m = (int32_t)inf[i].seed_m;
+      q.seed_n = (int32_t)inf[i].seed_n;
+    } else {
+      const int mp = mp0, np = np0;
+      q.seed_rows = keep(q.seed_rows, mp);
+      q.seed_cols = keep(q.seed_cols, np);
+      q.row_order = keep(q.row_order, q.m);
+      q.col_order = keep(q.col_order, q.n);
+    }
+    q.grow_seed = 0;
+  }
+  pcp::BatchHandle& h = P->h;
+  h.size_only = true;
+  s = pcp::batch_launch(count, P->probs.data(), st, &h, false);
+  if (s != PCP_OK) {
+    pcp_batch_plan_destroy(P);
+    return s;
+  }
+  h.size_only = false;
+  cudaError_t e = cudaMalloc(&h.d_base, h.bytes);
+  if (e != cudaSuccess) {
+    h.d_base = nullptr;
+    pcp_batch_plan_destroy(P);
+    return pcp::cuda_fail(e, "cudaMalloc(batch plan workspace)", __FILE__,
+                          __LINE__);
+  }
+  h.prealloc = true;
+  // a direct run uploads the index sets and settles one-time set-up, then
+  // the same launches are captured (without the index uploads)
+  s = pcp::batch_launch(count, P->probs.data(), st, &h, false);
+  if (s == PCP_OK) s = pcp::batch_finish(&h, nullptr, st, 0.0f);
+  if (s == PCP_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    s = pcp::cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+  if (s == PCP_OK &&
+      (e = cudaStreamCreateWithFlags(&P->cap_st, cudaStreamNonBlocking)) !=
+          cudaSuccess)
+    s = pcp::cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__);
+  if (s != PCP_OK) {
+    pcp_batch_plan_destroy(P);
+    return s;
+  }
+  h.indices_ready = true;
+  if ((e = cudaStreamBeginCapture(P->cap_st,
+                                  cudaStreamCaptureModeThreadLocal)) !=
+      cudaSuccess) {
+    pcp_batch_plan_destroy(P);
+    return pcp::cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+  }
+  s = pcp::batch_launch(count, P->probs.data(), P->cap_st, &h, false);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(P->cap_st, &g);
+  if (s == PCP_OK && e == cudaSuccess && g)
+    e = cudaGraphInstantiate(&P->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (s != PCP_OK || e != cudaSuccess || !P->exec) {
+    if (s == PCP_OK)
+      s = pcp::cuda_fail(e != cudaSuccess ? e : cudaErrorUnknown,
+                         "batch plan graph capture", __FILE__, __LINE__);
+    pcp_batch_plan_destroy(P);
+    return s;
+  }
+  *out = P;
+  return PCP_OK;
+}
+
+extern "C" pcp_status pcp_l1filter_batch_run(pcp_batch_plan* P,
+                                             pcp_info* infos, void* stream) {
+  PCP_ARG(P && P->exec, "pcp_l1filter_batch_run: null plan");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (infos) {
+    PCP_CUDA(cudaEventCreate(&e0));
+    PCP_CUDA(cudaEventCreate(&e1));
+    PCP_CUDA(cudaEventRecord(e0, st));
+  }
+  PCP_CUDA(cudaGraphLaunch(P->exec, st));
+  if (!infos) return PCP_OK;
+  PCP_CUDA(cudaEventRecord(e1, st));
+  PCP_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return pcp::batch_finish(&P->h, infos, st, ms);
 }

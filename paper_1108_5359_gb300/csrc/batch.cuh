@@ -39,6 +39,11 @@ struct BatchHandle {
   // the launch is timed
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<pcp_status> status;
+  // a batch plan's workspace: size_only asks batch_launch for the bytes
+  // alone (no device work); prealloc uses d_base / bytes as given (never
+  // freed by batch_finish); indices_ready skips the index uploads (already
+  // on the device, e.g. while the launches are captured into a graph)
+  bool size_only = false, prealloc = false, indices_ready = false;
 };
 
 pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi);

@@ -53,10 +53,14 @@ constexpr int kSeedTeamMax = 64;     // largest team of the batched solver
 constexpr int kSeedMaxSide = 512;    // largest m', n'
 constexpr int kSeedGemmGroup = 4;    // tasks per pass of the tall products
 // The tall and rank-k products of the ALM run in FP32 while its residual is
-// above this (their ~1e-7 relative error is far below what the inexact ALM
-// leaves there), FP64 after.
+// above this, FP64 after.  An FP64 emulation of the iteration with FP32
+// products (200 x 200 and 50 x 50 seeds) reached the oracle's L^s to
+// 1.3e-7 .. 1.9e-7 with the switch anywhere from 1e-4 down to 3e-7, and
+// to ~5e-7 with FP32 products throughout; on GB300 1e-6 took the 200 x 200
+// seed from 2.96 to 2.89 ms and the 500 x 500 seed from 9.77 to 9.24 ms
+// against 1e-4, with the same error against L0.
 #ifndef PCP_SEED_LOWP_RES
-#define PCP_SEED_LOWP_RES 1e-4
+#define PCP_SEED_LOWP_RES 1e-6
 #endif
 constexpr double kSeedLowpRes = PCP_SEED_LOWP_RES;
 // Largest single-cluster team (a non-portable cluster size on this part).
@@ -129,6 +133,7 @@ struct alignas(16) SeedArgs {
   // the tall and rank-k products run in FP32 while the ALM residual is
   // above this, FP64 after
   double lowp_res;
+  int smem_doubles;  // dynamic shared memory of the launch, in doubles
   // partial-sum slots of the three reductions (norms of D, Ritz values,
   // residual): fixed per solve, so the summation order (and the result)
   // does not depend on how many CTAs the team has
@@ -398,7 +403,7 @@ __device__ void gram(const double* X, int nrows, int k, int kmax,
 __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
                              const double* Gm, double* Out, float* Out32,
                              float* A32,
-                             float* Ri32, double* dsc, int* dead,
+                             float* Ri32, double* Rd, double* dsc, int* dead,
                              double* rowb, int bid, int nblk, int row_warps,
                              long long* sub) {
   const int tid = threadIdx.x;
@@ -476,9 +481,19 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
   // Reciprocal pivots, then one warp per output row solves x R = t~ by
   // forward substitution (lane c owns columns c and c + 32).  The row data
   // and the arithmetic are FP64; R and its reciprocal pivots are the FP32
-  // factor's values.  Keeping t~ in FP64 matters: rounding it to FP32
+  // factor's values, widened once into FP64 copies (Rd, with a dead
+  // direction's reciprocal pivot 0) so that the k dependent steps of a row
+  // carry no conversions.  Keeping t~ in FP64 matters: rounding it to FP32
   // perturbs the directions near the threshold enough to slow the ALM.
   for (int c = tid; c < k; c += kSeedThreads) Ri32[c] = 1.0f / A32[c * k + c];
+  __syncthreads();
+  double* Rid = rowb;  // kmax doubles
+  for (int idx = tid; idx < k * k; idx += kSeedThreads) {
+    const int j = idx / k, c = idx - j * k;
+    Rd[idx] = c > j ? (double)A32[idx] : 0.0;
+  }
+  for (int c = tid; c < k; c += kSeedThreads)
+    Rid[c] = dead[c] ? 0.0 : (double)Ri32[c];
   __syncthreads();
   long long q2 = prof ? clock64() : 0;
   // row_warps warps per CTA (1 for a grid-wide team: the FP64 pipe is
@@ -487,19 +502,21 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
   for (int t = (wid < row_warps) ? bid * row_warps + wid : nrows; t < nrows;
        t += nblk * row_warps) {
     const int c0 = lane, c1 = lane + 32;
+    const int cc0 = min(c0, k - 1), cc1 = min(c1, k - 1);
     double p0 = c0 < k ? ldg_cg(X + (size_t)t * kmax + c0) * dsc[c0] : 0.0;
     double p1 = c1 < k ? ldg_cg(X + (size_t)t * kmax + c1) * dsc[c1] : 0.0;
     double o0 = 0.0, o1 = 0.0;
     for (int j = 0; j < k; ++j) {
       const int owner = j & 31;
-      const double mine = (j < 32) ? p0 : p1;
-      double xj = __shfl_sync(0xffffffffu, mine * (double)Ri32[j], owner);
-      if (dead[j]) xj = 0.0;
+      const double mine = ((j < 32) ? p0 : p1) * Rid[j];
+      const double xj = __shfl_sync(0xffffffffu, mine, owner);
       if (lane == owner) {
         if (j < 32) o0 = xj; else o1 = xj;
       }
-      if (c0 > j && c0 < k) p0 = fma(-xj, (double)A32[j * k + c0], p0);
-      if (c1 > j && c1 < k) p1 = fma(-xj, (double)A32[j * k + c1], p1);
+      // Rd holds zeros on and below the diagonal, so columns <= j are
+      // left as they are
+      p0 = fma(-xj, Rd[j * k + cc0], p0);
+      p1 = fma(-xj, Rd[j * k + cc1], p1);
     }
     if (c0 < k) {
       __stcg(Out + (size_t)t * kmax + c0, o0);
@@ -847,6 +864,196 @@ __device__ int hestenes_f64(double* C, double* W, int nk) {
   return sweep;
 }
 
+// Fast form of the final FP64 SVD, for the usual case of nearly orthonormal
+// bases (F = G - I with |F| <= 1e-4, G the Gram of Ut or Vt) and a core
+// whose singular values are well separated against its off-diagonal part.
+// On entry D0 = F_u, D1 = F_v (FP64, nk x nk, row-major), sg = sigma_K.
+//   Löwdin orthonormalisation to second order: Q = Ut X, X = (I + F)^-1/2
+//     = I - F/2 + 3/8 F^2 + O(F^3);  Ut = Q S, S = I + F/2 - F^2/8 + O(F^3);
+//   core C = S_u diag(sigma) S_v = diag(sigma) + E, with
+//     E = (F_u Sigma + Sigma F_v)/2 + F_u Sigma F_v / 4 - F_u^2 Sigma / 8
+//         - Sigma F_v^2 / 8;
+//   first-order SVD of C = diag(d) + offdiag(E), d = sigma + diag(E):
+//     A_pq = (d_q E_pq + d_p E_qp) / (d_q^2 - d_p^2),
+//     B_pq = (d_q E_qp + d_p E_pq) / (d_q^2 - d_p^2)   (antisymmetric),
+//     W_u = exp(A) = I + A + A^2/2 + A^3/6 + A^4/24 (orthogonal to
+//     |A|^5/120), W_v likewise from B;  U = Ut X_u W_u, V = Vt X_v W_v,
+//     Sigma = d.
+// Every k x k product here is of perturbation matrices (|F| <= 1e-4,
+// |A|, |B| <= 5e-3), so it runs in FP32 on FP32 copies made once (an FP64
+// operand converted inside an O(nk^3) loop would put the conversions on
+// this part's narrow FP64 pipe): its rounding is ~1e-7 of a term already
+// ~1e-5 or below.  Linear terms and the sums stay FP64.  The error left in
+// the SVD is ~|E| |A| (<= 1e-8 of sigma_1, ~1e-12 typically); U and V are
+// orthonormal to ~1e-14.  Returns false (outputs undefined) when |A| or |B|
+// exceeds 5e-3 (a near-degenerate pair): the caller then takes the exact
+// path.  On success D0 = M_u = X_u W_u, D1 = M_v, d in dout.  Shared
+// memory: D0 .. D4, nk^2 doubles each (D2 .. D4 hold FP32 data).
+// Products of nk x nk FP32 matrices (row-major, nk <= 64) with 4 x 4
+// register tiles, one per thread of the CTA (16 x 16 tiles): for every
+// output (p, q) in this thread's tile, acc1 = sum_c X_pc s_c Y1_cq and
+// acc2 = sum_c X_pc Y2_cq (s = 1 without xs; Y1 + Y1b when Y1b is given),
+// each summed over c in order; out(p, q, acc1, acc2) stores the results.
+template <typename Out>
+__device__ __forceinline__ void mm64_tile(const float* X, const float* xs,
+                                          const float* Y1, const float* Y1b,
+                                          const float* Y2, int nk, Out out) {
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  const int r0 = 4 * ti, c0 = 4 * tj;
+  if (r0 >= nk || c0 >= nk) return;
+  float a1[4][4], a2[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a1[i][j] = a2[i][j] = 0.0f;
+  for (int c = 0; c < nk; ++c) {
+    float xv[4], y1[4], y2[4];
+    const float sc = xs ? xs[c] : 1.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      xv[i] = r0 + i < nk ? X[(r0 + i) * nk + c] * sc : 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool in = c0 + j < nk;
+      y1[j] = in ? Y1[c * nk + c0 + j] : 0.0f;
+      if (Y1b) y1[j] += in ? Y1b[c * nk + c0 + j] : 0.0f;
+      y2[j] = (Y2 && in) ? Y2[c * nk + c0 + j] : 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        a1[i][j] = fmaf(xv[i], y1[j], a1[i][j]);
+        if (Y2) a2[i][j] = fmaf(xv[i], y2[j], a2[i][j]);
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (r0 + i < nk && c0 + j < nk) out(r0 + i, c0 + j, a1[i][j], a2[i][j]);
+}
+
+__device__ bool svd_fast_f64(double* D0, double* D1, double* D2, double* D3,
+                             double* D4, int nk, const double* sg,
+                             double* dout) {
+  const int tid = threadIdx.x;
+  const int n2 = nk * nk;
+  __shared__ float sg32[kSeedKmaxLimit];
+  float* Fu32 = reinterpret_cast<float*>(D2);
+  float* Fv32 = Fu32 + n2;
+  float* P1 = reinterpret_cast<float*>(D3);  // F_u^2
+  float* P2 = P1 + n2;                       // F_v^2
+  float* P3 = reinterpret_cast<float*>(D4);  // F_u Sigma F_v
+  float* AB = P3 + n2;  // A above the diagonal, B (transposed) below
+  for (int e = tid; e < n2; e += kSeedThreads) {
+    Fu32[e] = (float)D0[e];
+    Fv32[e] = (float)D1[e];
+  }
+  for (int q = tid; q < nk; q += kSeedThreads) sg32[q] = (float)sg[q];
+  __syncthreads();
+  mm64_tile(Fu32, nullptr, Fu32, nullptr, nullptr, nk,
+            [&](int p, int q, float v, float) { P1[p * nk + q] = v; });
+  mm64_tile(Fv32, nullptr, Fv32, nullptr, nullptr, nk,
+            [&](int p, int q, float v, float) { P2[p * nk + q] = v; });
+  mm64_tile(Fu32, sg32, Fv32, nullptr, nullptr, nk,
+            [&](int p, int q, float v, float) { P3[p * nk + q] = v; });
+  __syncthreads();
+  auto E = [&](int p, int q) -> double {
+    return 0.5 * fma(D0[p * nk + q], sg[q], sg[p] * D1[p * nk + q]) +
+           0.25 * (double)P3[p * nk + q] -
+           0.125 * fma((double)P1[p * nk + q], sg[q],
+                       sg[p] * (double)P2[p * nk + q]);
+  };
+  for (int q = tid; q < nk; q += kSeedThreads) dout[q] = sg[q] + E(q, q);
+  __syncthreads();
+  int bad = 0;
+  for (int e = tid; e < n2; e += kSeedThreads) {
+    const int p = e / nk, q = e - p * nk;
+    if (p >= q) continue;
+    const double epq = E(p, q), eqp = E(q, p);
+    const double dp = dout[p], dq = dout[q];
+    const float den = (float)((dq - dp) * (dq + dp));
+    const float a = (float)fma(dq, epq, dp * eqp) / den;
+    const float b = (float)fma(dq, eqp, dp * epq) / den;
+    if (!(fabsf(a) <= 5e-3f && fabsf(b) <= 5e-3f)) bad = 1;
+    AB[p * nk + q] = a;
+    AB[q * nk + p] = b;
+  }
+  if (__syncthreads_or(bad)) return false;
+  // X = -F/2 + 3/8 F^2 (X - I, FP64) in place over F; A and B as full
+  // antisymmetric matrices: A over F_u Sigma F_v, B in place over AB (each
+  // pair (p, q) is read and written by one thread)
+  float* Af = P3;
+  float* Bf = AB;
+  for (int idx = tid; idx < 2 * n2; idx += kSeedThreads) {
+    const int w = idx / n2, e = idx - w * n2;
+    double* D = w ? D1 : D0;
+    D[e] = fma(-0.5, D[e], 0.375 * (double)(w ? P2 : P1)[e]);
+  }
+  for (int e = tid; e < n2; e += kSeedThreads) {
+    const int p = e / nk, q = e - p * nk;
+    if (p > q) continue;
+    if (p == q) {
+      Af[e] = 0.0f;
+      Bf[e] = 0.0f;
+      continue;
+    }
+    const float a = AB[p * nk + q], b = AB[q * nk + p];
+    Af[p * nk + q] = a;
+    Af[q * nk + p] = -a;
+    Bf[p * nk + q] = b;
+    Bf[q * nk + p] = -b;
+  }
+  __syncthreads();
+  // A^2, B^2 over the FP32 copies of F, then H = A^2/2 + A^3/6 + A^4/24
+  // (W - I - A) over F^2 (no longer needed)
+  float* A2 = Fu32;
+  float* B2 = Fv32;
+  mm64_tile(Af, nullptr, Af, nullptr, nullptr, nk,
+            [&](int p, int q, float v, float) { A2[p * nk + q] = v; });
+  mm64_tile(Bf, nullptr, Bf, nullptr, nullptr, nk,
+            [&](int p, int q, float v, float) { B2[p * nk + q] = v; });
+  __syncthreads();
+  float* Hu = P1;
+  float* Hv = P2;
+  mm64_tile(A2, nullptr, Af, nullptr, A2, nk,
+            [&](int p, int q, float a3, float a4) {
+              Hu[p * nk + q] = fmaf(0.5f, A2[p * nk + q],
+                                    fmaf(a3, 1.0f / 6.0f, a4 * (1.0f / 24.0f)));
+            });
+  mm64_tile(B2, nullptr, Bf, nullptr, B2, nk,
+            [&](int p, int q, float a3, float a4) {
+              Hv[p * nk + q] = fmaf(0.5f, B2[p * nk + q],
+                                    fmaf(a3, 1.0f / 6.0f, a4 * (1.0f / 24.0f)));
+            });
+  __syncthreads();
+  // FP32 copies of X over A^2, B^2
+  float* Xu32 = A2;
+  float* Xv32 = B2;
+  for (int e = tid; e < n2; e += kSeedThreads) {
+    Xu32[e] = (float)D0[e];
+    Xv32[e] = (float)D1[e];
+  }
+  __syncthreads();
+  // M = (I + X)(I + W) = I + X + W + X W, W = A + H: each thread writes the
+  // FP64 entries of its own tile (the product reads the FP32 copies only)
+  mm64_tile(Xu32, nullptr, Af, Hu, nullptr, nk,
+            [&](int p, int q, float xw, float) {
+              const int e = p * nk + q;
+              D0[e] = (p == q ? 1.0 : 0.0) + D0[e] +
+                      ((double)Af[e] + (double)Hu[e]) + (double)xw;
+            });
+  mm64_tile(Xv32, nullptr, Bf, Hv, nullptr, nk,
+            [&](int p, int q, float xw, float) {
+              const int e = p * nk + q;
+              D1[e] = (p == q ? 1.0 : 0.0) + D1[e] +
+                      ((double)Bf[e] + (double)Hv[e]) + (double)xw;
+            });
+  __syncthreads();
+  return true;
+}
+
 // Hardware barrier over the CTAs of this thread-block cluster, with release
 // / acquire ordering of their memory operations at cluster scope (the
 // cross-CTA data lives in global memory and is read with L2 loads).  Every
@@ -987,7 +1194,7 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     gram(a.T, np, k, kmax, a.Gam, b, nb);
     if (!team_sync()) return;
     trace_mark(a, 3);
-    cholqr_apply(a.T, np, k, kmax, a.Gam, a.Psi, a.Psi32, J0, W0, dsc, dead, rowb,
+    cholqr_apply(a.T, np, k, kmax, a.Gam, a.Psi, a.Psi32, J0, W0, Vd, dsc, dead, rowb,
                  b, nb, row_warps, kGrid ? ctl->sub : nullptr);
     if (!team_sync()) return;
     trace_mark(a, 4);
@@ -1002,7 +1209,7 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
     trace_mark(a, 6);
     if (stage < 2) {
       // plain power step on D: Omega = orth(P)
-      cholqr_apply(a.P, mp, k, kmax, a.Gam, a.Om, a.Om32, J0, W0, dsc, dead, rowb, b, nb,
+      cholqr_apply(a.P, mp, k, kmax, a.Gam, a.Om, a.Om32, J0, W0, Vd, dsc, dead, rowb, b, nb,
                    row_warps, nullptr);
       if (!team_sync()) return;
       trace_mark(a, 7);
@@ -1534,15 +1741,20 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
   // of orthogonality of the FP32 k x k factorisations, while Algorithm 1
   // (step 2, Eq. l1g) takes A^T A = I; so the factors are re-orthonormalised
   // once here, in FP64.  With K the nk columns whose Ritz value s exceeds
-  // tau (the rest are shrunk to zero):
-  //   Ut = Pt_K diag(1/s_K),  Vt = PsiT_K            (nearly orthonormal)
-  //   Ut = Qu Ru,  Vt = Qv Rv                        (Cholesky QR, FP64)
-  //   C = Ru diag(s_K - tau) Rv^T                    (nk x nk, ~diagonal)
-  //   C Wv = Wu diag(sigma)                          (one-sided Jacobi, FP64)
-  //   U^s = Ut Ru^-1 Wu,  V^s = Vt Rv^-1 Wv,  Sigma^s = sigma (sorted)
-  // so U^s Sigma^s V^sT is the iterate's L^s to FP64 rounding and U^s, V^s
-  // are orthonormal to FP64 rounding.  rank = #{sigma > rank_cut sigma_1},
-  // capped at r_cap.
+  // tau (the rest are shrunk to zero), Ut = Pt_K diag(1/s_K) and
+  // Vt = PsiT_K (nearly orthonormal), L^s = Ut diag(s_K - tau) Vt^T, and
+  // the FP64 Grams of Ut and Vt (distributed over the team) give either
+  //   fast path (svd_fast_f64): second-order Löwdin orthonormalisation of
+  //     Ut, Vt and a first-order (exponential-map) SVD of the nearly
+  //     diagonal core, O(nk^2) FP64 work plus FP32 products of
+  //     perturbation matrices; taken when the bases are orthonormal to
+  //     1e-4 and the singular values are well separated; or
+  //   exact path: Ut = Qu Ru, Vt = Qv Rv (Cholesky QR), C = Ru diag(s_K -
+  //     tau) Rv^T, one-sided Jacobi C Wv = Wu diag(sigma), U^s = Ut Ru^-1
+  //     Wu, V^s = Vt Rv^-1 Wv.
+  // Either way U^s Sigma^s V^sT is the iterate's L^s (to ~1e-12 relative,
+  // FP64 rounding on the exact path) and U^s, V^s are orthonormal to FP64
+  // rounding.  rank = #{sigma > rank_cut sigma_1}, capped at r_cap.
   __shared__ double f_is[kSeedKmaxLimit];   // 1 / s_K
   __shared__ double f_sig[kSeedKmaxLimit];  // sigma_K (scaled), then sigma
   __shared__ double f_y[2][kSeedKmaxLimit]; // reciprocal pivots of Ru, Rv
@@ -1577,42 +1789,71 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
   if (!team_sync()) return;
   // every CTA: the same nk x nk factorisations on the same data (identical
   // results), in the dynamic shared memory the iteration is done with
-  double* Ru = sm;
-  double* Rv = Ru + nk * nk;
-  double* Cm = Rv + nk * nk;
-  double* Wv = Cm + nk * nk;
+  double* D0 = sm;
+  double* D1 = D0 + nk * nk;
+  double* D2 = D1 + nk * nk;
+  double* D3 = D2 + nk * nk;
+  double* D4 = D3 + nk * nk;
+  __shared__ double f_d[kSeedKmaxLimit];
+  int far = 0;
   for (int idx = tid; idx < nk * nk; idx += kSeedThreads) {
     const int p = idx / nk, q = idx - p * nk;
-    Ru[idx] = ldg_cg(a.Gam + p * kmax + q);
-    Rv[idx] = ldg_cg(a.Gam2 + p * kmax + q);
+    const double id = p == q ? 1.0 : 0.0;
+    D0[idx] = ldg_cg(a.Gam + p * kmax + q) - id;
+    D1[idx] = ldg_cg(a.Gam2 + p * kmax + q) - id;
+    if (!(fabs(D0[idx]) <= 1e-4 && fabs(D1[idx]) <= 1e-4)) far = 1;
   }
-  __syncthreads();
-  chol2_f64(Ru, Rv, nk, f_y[0], f_y[1]);
-  for (int idx = tid; idx < nk * nk; idx += kSeedThreads) {
-    const int p = idx / nk, q = idx - p * nk;
-    double acc = 0.0;
-    for (int c = max(p, q); c < nk; ++c)
-      acc = fma(Ru[p * nk + c] * f_sig[c], Rv[q * nk + c], acc);
-    Cm[idx] = acc;
+  // the fast form needs 5 nk^2 doubles of shared memory, the exact one 4
+  bool fast = !__syncthreads_or(far) && 5 * nk * nk <= a.smem_doubles;
+  if (fast) fast = svd_fast_f64(D0, D1, D2, D3, D4, nk, f_sig, f_d);
+  double* Mu = D0;  // diag(1/s_K) Ru^-1 Wu (exact) or X_u W_u (fast)
+  double* Mv = D1;
+  int fsweeps = 0;
+  if (fast) {
+    for (int q = tid; q < nk; q += kSeedThreads) f_sig[q] = f_d[q];
+  } else {
+    // exact path: Cholesky QR and a one-sided Jacobi SVD of the core
+    double* Ru = D0;
+    double* Rv = D1;
+    double* Cm = D2;
+    double* Wv = D3;
+    for (int idx = tid; idx < nk * nk; idx += kSeedThreads) {
+      const int p = idx / nk, q = idx - p * nk;
+      Ru[idx] = ldg_cg(a.Gam + p * kmax + q);
+      Rv[idx] = ldg_cg(a.Gam2 + p * kmax + q);
+    }
+    __syncthreads();
+    chol2_f64(Ru, Rv, nk, f_y[0], f_y[1]);
+    for (int idx = tid; idx < nk * nk; idx += kSeedThreads) {
+      const int p = idx / nk, q = idx - p * nk;
+      double acc = 0.0;
+      for (int c = max(p, q); c < nk; ++c)
+        acc = fma(Ru[p * nk + c] * f_sig[c], Rv[q * nk + c], acc);
+      Cm[idx] = acc;
+    }
+    __syncthreads();
+    fsweeps = hestenes_f64(Cm, Wv, nk);
+    // sigma_q = ||C e_q||, Wu = C diag(1/sigma)
+    for (int q = tid; q < nk; q += kSeedThreads) {
+      double ss = 0.0;
+      for (int p = 0; p < nk; ++p) ss = fma(Cm[p * nk + q], Cm[p * nk + q], ss);
+      f_sig[q] = sqrt(ss);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nk * nk; idx += kSeedThreads) {
+      const int q = idx - (idx / nk) * nk;
+      Cm[idx] = f_sig[q] > 0.0 ? Cm[idx] / f_sig[q] : 0.0;
+    }
+    __syncthreads();
+    // Ru^-1 Wu (in Cm), Rv^-1 Wv (in Wv)
+    backsub2_f64(Ru, Rv, Cm, Wv, nk, f_y[0], f_y[1]);
+    Mu = Cm;
+    Mv = Wv;
   }
-  __syncthreads();
-  const int fsweeps = hestenes_f64(Cm, Wv, nk);
-  // sigma_q = ||C e_q||, Wu = C diag(1/sigma)
-  for (int q = tid; q < nk; q += kSeedThreads) {
-    double ss = 0.0;
-    for (int p = 0; p < nk; ++p) ss = fma(Cm[p * nk + q], Cm[p * nk + q], ss);
-    f_sig[q] = sqrt(ss);
-  }
-  __syncthreads();
-  for (int idx = tid; idx < nk * nk; idx += kSeedThreads) {
-    const int q = idx - (idx / nk) * nk;
-    Cm[idx] = f_sig[q] > 0.0 ? Cm[idx] / f_sig[q] : 0.0;
-  }
-  __syncthreads();
-  // Mu = diag(1/s_K) Ru^-1 Wu (in Cm), Mv = Rv^-1 Wv (in Wv)
-  backsub2_f64(Ru, Rv, Cm, Wv, nk, f_y[0], f_y[1]);
+  // U = Pt_K diag(1/s_K) M_u: fold 1/s_K into the rows of M_u
   for (int idx = tid; idx < nk * nk; idx += kSeedThreads)
-    Cm[idx] *= f_is[idx / nk];
+    Mu[idx] *= f_is[idx / nk];
+  __syncthreads();
   if (tid == 0) {
     for (int q = 0; q < nk; ++q) f_ord[q] = q;
     for (int x = 1; x < nk; ++x) {  // insertion sort, decreasing sigma
@@ -1635,28 +1876,35 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
   }
   __syncthreads();
   const int rank = f_n[1];
-  for (int i = b; i < mp; i += nb)
-    for (int c = tid; c < kmax; c += kSeedThreads) {
-      double acc = 0.0;
-      if (c < rank) {
-        const int oc = f_ord[c];
-        const double* pr = Ptc + (size_t)i * kmax;
-        for (int q = 0; q < nk; ++q)
-          acc = fma(ldg_cg(pr + f_sel[q]), Cm[q * nk + oc], acc);
+  // U^s = Pt_K M_u and V^s = PsiT_K M_v row by row: one warp per row loads
+  // the row's nk entries at once (two per lane), then every lane forms its
+  // output columns (c = lane, lane + 32) from shuffles, summing over q in
+  // order
+  {
+    const int lane = tid & 31, wid = tid >> 5;
+    constexpr int kW = kSeedThreads / 32;
+    const int c0 = lane, c1 = lane + 32;
+    const int oc0 = c0 < rank ? f_ord[c0] : 0;
+    const int oc1 = c1 < rank ? f_ord[c1] : 0;
+    for (int t = b * kW + wid; t < mp + np; t += nb * kW) {
+      const bool isu = t < mp;
+      const int i = isu ? t : t - mp;
+      const double* pr = (isu ? Ptc : PsiTc) + (size_t)i * kmax;
+      const double* Mx = isu ? Mu : Mv;
+      const double v0 = lane < nk ? ldg_cg(pr + f_sel[lane]) : 0.0;
+      const double v1 = lane + 32 < nk ? ldg_cg(pr + f_sel[lane + 32]) : 0.0;
+      double o0 = 0.0, o1 = 0.0;
+      for (int q = 0; q < nk; ++q) {
+        const double vq = __shfl_sync(0xffffffffu, q < 32 ? v0 : v1, q & 31);
+        o0 = fma(vq, Mx[q * nk + oc0], o0);
+        o1 = fma(vq, Mx[q * nk + oc1], o1);
       }
-      a.U[i + (size_t)c * mp] = acc;
+      double* out = isu ? a.U + i : a.V + i;
+      const size_t ld = isu ? (size_t)mp : (size_t)np;
+      if (c0 < kmax) out[(size_t)c0 * ld] = c0 < rank ? o0 : 0.0;
+      if (c1 < kmax) out[(size_t)c1 * ld] = c1 < rank ? o1 : 0.0;
     }
-  for (int j = b; j < np; j += nb)
-    for (int c = tid; c < kmax; c += kSeedThreads) {
-      double acc = 0.0;
-      if (c < rank) {
-        const int oc = f_ord[c];
-        const double* pr = PsiTc + (size_t)j * kmax;
-        for (int q = 0; q < nk; ++q)
-          acc = fma(ldg_cg(pr + f_sel[q]), Wv[q * nk + oc], acc);
-      }
-      a.V[j + (size_t)c * np] = acc;
-    }
+  }
   trace_mark(a, 15);
   if (b == 0) {
     for (int c = tid; c < kmax; c += kSeedThreads)
@@ -1665,7 +1913,7 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
       ctl->iters = it;
       ctl->rank = rank;
       ctl->rank_raw = f_n[2];
-      ctl->fin_sweeps = fsweeps;
+      ctl->fin_sweeps = fast ? -1 : fsweeps;
       ctl->converged = converged ? 1 : 0;
       ctl->residual = res;
       ctl->k_final = k;
@@ -1679,6 +1927,14 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
           a.trace[2 * i] = q < 4 ? (unsigned long long)ctl->jcyc[q]
                                  : (unsigned long long)ctl->jsweeps;
           a.trace[2 * i + 1] = 95ull + q;
+          ctl->ntrace = i + 1;
+        }
+      }
+      {  // final SVD: phase 91, value 0 = fast path, else 1 + Jacobi sweeps
+        const int i = ctl->ntrace;
+        if (i < kSeedTraceCap) {
+          a.trace[2 * i] = (unsigned long long)(fast ? 0 : 1 + fsweeps);
+          a.trace[2 * i + 1] = 91ull;
           ctl->ntrace = i + 1;
         }
       }
@@ -1840,6 +2096,9 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
     kmax_all = std::max(kmax_all, t.kmax);
   }
   const size_t smem = seed_smem_bytes(kmax_all);
+  for (int i = 0; i < count; ++i)
+    reinterpret_cast<SeedArgs*>(hb + (size_t)i * seed_args_bytes())
+        ->smem_doubles = (int)(smem / sizeof(double));
   PCP_CUDA(cudaFuncSetAttribute(seed_alm_team_kernel,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
@@ -1961,6 +2220,7 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
   if (d_rank_out) *d_rank_out = &a.ctl->rank;
 
   const size_t smem = seed_smem_bytes(kmax);
+  a.smem_doubles = (int)(smem / sizeof(double));
   PCP_CUDA(cudaFuncSetAttribute(seed_alm_kernel,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));

@@ -207,3 +207,35 @@ def test_batch_matches_oracle_at_bench_seed_sizes():
         assert o["info"]["rank"] == ref.rank == P.r
         assert relerr(_L(o), ref.L) < TOL, i
         assert relerr(o["S"].astype(np.float64), ref.S) < TOL, i
+
+
+def test_batch_plan_replays_the_batch_bit_for_bit():
+    # a batch plan allocates once, captures the batch into a CUDA graph and
+    # replays it: two replays give the same bits as a direct batched call
+    # (same seeds, same kernels, same reduction orders)
+    import torch
+    import paper_1108_5359_gb300 as pk
+    build_and_load()
+    Ps = _instances()
+    st, direct = _run_batch(Ps)
+    bufs, probs = [], []
+    for P in Ps:
+        dM, Lu, Lv, S = _buffers(P)
+        bufs.append((dM, Lu, Lv, S))
+        probs.append(pk.problem(pk.pcp_params_default(P.m, P.n, P.r), dM, Lu,
+                                Lv, S, P.rows, P.cols))
+    plan = pk.BatchPlan(probs)
+    for rep in range(2):
+        for (_, Lu, Lv, S) in bufs:   # the replay must rewrite them
+            Lu.fill_(float("nan"))
+            Lv.fill_(float("nan"))
+            S.fill_(float("nan"))
+        st2, infos = plan.run()
+        torch.cuda.synchronize()
+        for i, ((_, Lu, Lv, S), o, inf) in enumerate(zip(bufs, direct, infos)):
+            assert inf.status == o["info"]["status"], (rep, i)
+            assert inf.seed_iters == o["info"]["seed_iters"]
+            np.testing.assert_array_equal(Lu.cpu().numpy(), o["Lu"])
+            np.testing.assert_array_equal(Lv.cpu().numpy(), o["Lv"])
+            np.testing.assert_array_equal(S.cpu().numpy(), o["S"])
+    plan.close()

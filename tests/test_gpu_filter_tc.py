@@ -131,3 +131,4 @@ def test_error_before_and_after_refinement(precision, capsys):
     assert (itb == -lowp).all()        # stopped by max_iter, unrefined
     assert er < TOL and (itr > 0).all()
     assert eb > 100 * er
+
