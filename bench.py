@@ -511,7 +511,8 @@ def report(pk, rec, rank=0):
                  "achieved": seed_flops / (mean["seed"] * 1e-3) / 1e12,
                  "note": "6 m'n'k + 4 (m'+n') k^2 flops per ALM iteration "
                          "(k = r + max(6, r/4)), seed iterations + 3 "
-                         "prologue passes, against the FP64 peak (part of "
+                         "prologue passes (two power steps, one Rayleigh-Ritz "
+                         "step on D), against the FP64 peak (part of "
                          "the work runs in FP32)"},
     }
     for k, v in stages.items():

@@ -707,6 +707,7 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
   }
   // stage 1: gather the seed (FP64) and count non-finite entries (from the
   // page-locked host M itself when the device can read it)
+  pcp::NvtxStages nvtx("pcp.seed");
   PCP_CUDA(cudaMemsetAsync(P->d_bad, 0, sizeof(int32_t), st));
   s = (hio && hio->gM)
           ? pcp::gather_seed(hio->gM, hio->ldm, P->d_rows, P->mp, P->d_cols,
@@ -738,6 +739,7 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
   // stages 3 and 4: column and row filtering (Algorithm 1), the row filter
   // on the plan's second stream so that both launches share the GPU
   const int64_t ncb = P->n - P->np, nrb = P->m - P->mp;
+  nvtx.next("pcp.filter");
   PCP_CUDA(cudaEventRecord(P->fork_ev, st));
   PCP_CUDA(cudaStreamWaitEvent(P->side_st, P->fork_ev, 0));
   s = pcp_l1_filter(dM, P->d_rows, P->mp, 1, P->d_cbar, (int32_t)ncb, ldm,
@@ -766,6 +768,7 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
     PCP_CUDA(cudaMemcpyAsync(hio->hLv, dLv, sizeof(float) * P->n * P->r,
                              cudaMemcpyDeviceToHost, P->copy_st));
   }
+  nvtx.next("pcp.spass");
   // stage 6: S = M - Lu Lv^T (host buffers: in column chunks of a multiple
   // of 64 columns, each chunk's S copied back while the next is computed)
   if (dS && hio) {

@@ -204,7 +204,7 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
   h->count = count;
   h->inst.assign(count, BatchInstance());
   h->probs.assign(probs, probs + count);
-  h->d_base = nullptr;
+  if (!h->prealloc) h->d_base = nullptr;  // a plan's workspace stays
   for (int i = 0; i < count; ++i) {
     pcp_status s = batch_validate(probs[i], &h->inst[i]);
     if (s != PCP_OK) {
@@ -379,20 +379,27 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
     PCP_CUDA(cudaEventRecord(h->ev[0], st));
   }
   pcp_status s;
+  NvtxStages nvtx("pcp.batch.seed");
+  // a plan's capture follows its direct run on the same workspace: the
+  // argument blocks there already hold these bytes, so the graph carries
+  // no host copies
+  const bool upload = !h->indices_ready;
   if ((s = gather_batched_async(gat.data(), count, h->h_gat.data(),
-                                base + o_gat, st)) != PCP_OK)
+                                base + o_gat, st, upload)) != PCP_OK)
     return s;
   if ((s = seed_pcp_batched_async(seeds.data(), count, h->h_sargs.data(),
-                                  base + o_sargs, st)) != PCP_OK)
+                                  base + o_sargs, st, upload)) != PCP_OK)
     return s;
   if ((s = assemble_batched_async(asmb.data(), count, h->h_asm.data(),
-                                  base + o_asm, st)) != PCP_OK)
+                                  base + o_asm, st, upload)) != PCP_OK)
     return s;
   if (timed) PCP_CUDA(cudaEventRecord(h->ev[1], st));
+  nvtx.next("pcp.batch.filter");
   if ((s = l1_filter_batched_async(sets.data(), 2 * count, h->h_filt.data(),
-                                   base + o_filt, st)) != PCP_OK)
+                                   base + o_filt, st, upload)) != PCP_OK)
     return s;
   if (timed) PCP_CUDA(cudaEventRecord(h->ev[2], st));
+  nvtx.next("pcp.batch.spass");
   h->h_stask.resize(sizeof(SummaryTask) * count);
   SummaryTask* stask = reinterpret_cast<SummaryTask*>(h->h_stask.data());
   for (int i = 0; i < count; ++i) {
@@ -402,8 +409,10 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
                            b.d_iters, (q.m - b.mp) + (q.n - b.np), b.d_bad};
   }
   h->d_summary = reinterpret_cast<BatchSummary*>(base + o_sum);
-  PCP_CUDA(cudaMemcpyAsync(base + o_stask, stask, sizeof(SummaryTask) * count,
-                           cudaMemcpyHostToDevice, st));
+  if (upload)
+    PCP_CUDA(cudaMemcpyAsync(base + o_stask, stask,
+                             sizeof(SummaryTask) * count,
+                             cudaMemcpyHostToDevice, st));
   batch_summary_kernel<<<count, 256, 0, st>>>(
       reinterpret_cast<const SummaryTask*>(base + o_stask), h->d_summary);
   PCP_CUDA(cudaGetLastError());
@@ -665,8 +674,28 @@ extern "C" pcp_status pcp_l1filter_batch_plan(int32_t count,
   h.prealloc = true;
   // a direct run uploads the index sets and settles one-time set-up, then
   // the same launches are captured (without the index uploads)
+  // The direct run must reproduce the settling call instance by instance
+  // (same seeds, kernels and reduction orders): a difference means the
+  // preallocated workspace is not what the launches expect.
+  std::vector<pcp_info> inf2(count);
   s = pcp::batch_launch(count, P->probs.data(), st, &h, false);
-  if (s == PCP_OK) s = pcp::batch_finish(&h, nullptr, st, 0.0f);
+  if (s == PCP_OK) {
+    const pcp_status s2 = pcp::batch_finish(&h, inf2.data(), st, 0.0f);
+    if (s2 == PCP_ERR_ARG || s2 == PCP_ERR_CUDA || s2 == PCP_ERR_TIMEOUT)
+      s = s2;
+  }
+  for (int i = 0; s == PCP_OK && i < count; ++i)
+    if (inf2[i].status != inf[i].status ||
+        inf2[i].seed_iters != inf[i].seed_iters ||
+        inf2[i].rank != inf[i].rank) {
+      pcp::set_error(
+          "pcp_l1filter_batch_plan: instance %d of the plan's direct run "
+          "differs from the batched call (status %d / %d, seed iterations "
+          "%d / %d, rank %d / %d)", i, (int)inf2[i].status,
+          (int)inf[i].status, (int)inf2[i].seed_iters,
+          (int)inf[i].seed_iters, (int)inf2[i].rank, (int)inf[i].rank);
+      s = PCP_ERR_CUDA;
+    }
   if (s == PCP_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess)
     s = pcp::cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
   if (s == PCP_OK &&

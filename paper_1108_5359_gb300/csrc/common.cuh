@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "pcp_l1f.h"
@@ -27,6 +28,23 @@ pcp_status cuda_fail(cudaError_t e, const char* what, const char* file,
       return PCP_ERR_ARG;             \
     }                                 \
   } while (0)
+
+// ---- host-side stage ranges ----------------------------------------------
+// One NVTX range per stage of a solve (seed, filters, S pass), pushed while
+// the stage's work is enqueued: a profiler that records NVTX (Nsight
+// Systems, ncu --nvtx) groups the launches by stage; without one attached
+// the calls do nothing.  next() closes the open range and opens the next.
+class NvtxStages {
+ public:
+  explicit NvtxStages(const char* first) { nvtxRangePushA(first); }
+  void next(const char* name) {
+    nvtxRangePop();
+    nvtxRangePushA(name);
+  }
+  ~NvtxStages() { nvtxRangePop(); }
+  NvtxStages(const NvtxStages&) = delete;
+  NvtxStages& operator=(const NvtxStages&) = delete;
+};
 
 // ---- device helpers ------------------------------------------------------
 __device__ __forceinline__ unsigned long long globaltimer_ns() {

@@ -341,7 +341,7 @@ size_t filter_batch_bytes(const FilterSet* sets, int nsets) {
 
 pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
                                    void* h_buf, void* d_buf,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, bool upload) {
   if (nsets <= 0) return PCP_OK;
   char* hb = static_cast<char*>(h_buf);
   FilterArgs* ha = reinterpret_cast<FilterArgs*>(hb);
@@ -395,7 +395,8 @@ pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
     std::memcpy(hb + used, by_class[c].data(), 4 * by_class[c].size());
     used += (4 * by_class[c].size() + 15) / 16 * 16;
   }
-  PCP_CUDA(cudaMemcpyAsync(d_buf, h_buf, used, cudaMemcpyHostToDevice, st));
+  if (upload)
+    PCP_CUDA(cudaMemcpyAsync(d_buf, h_buf, used, cudaMemcpyHostToDevice, st));
   char* db = static_cast<char*>(d_buf);
   const FilterArgs* d_sets = reinterpret_cast<const FilterArgs*>(db);
   for (int c = 0; c < kShapeClasses; ++c) {

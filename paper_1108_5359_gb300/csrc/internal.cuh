@@ -43,10 +43,12 @@ size_t seed_batched_args_bytes(int count);
 // Pack the tasks into h_args (seed_batched_args_bytes(count) bytes), copy
 // them to d_args and launch: a team of CTAs per seed, sized by its work
 // (cooperative launch) when every seed gets at least one co-resident CTA,
-// else one CTA per seed.
+// else one CTA per seed.  upload = false: d_args already holds the same
+// packed bytes (a batch plan's capture after its direct run), nothing is
+// copied.  The same flag on the other batched launches below.
 pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
                                   void* h_args, void* d_args,
-                                  cudaStream_t st);
+                                  cudaStream_t st, bool upload = true);
 // Device addresses of the control block / the seed rank (int) inside a
 // CTA-solver workspace.
 SeedCtl* seed_ctl_ptr_cta(void* d_work, int mp, int np, int kmax);
@@ -127,7 +129,7 @@ size_t filter_batch_bytes(const FilterSet* sets, int nsets);
 // shape is fixed by p and r; sets of equal shape share a launch).
 pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
                                    void* h_buf, void* d_buf,
-                                   cudaStream_t st);
+                                   cudaStream_t st, bool upload = true);
 
 // Batched gather / assembly: one launch for all instances.
 struct GatherTask {
@@ -140,7 +142,8 @@ struct GatherTask {
   int32_t* bad;
 };
 pcp_status gather_batched_async(const GatherTask* tasks, int count,
-                                void* h_buf, void* d_buf, cudaStream_t st);
+                                void* h_buf, void* d_buf, cudaStream_t st,
+                                bool upload = true);
 struct AssembleTask {
   const double *U, *Sigma, *V;
   int mp, np, ku, r;
@@ -151,7 +154,8 @@ struct AssembleTask {
   float *U32, *V32, *inv_sigma32;
 };
 pcp_status assemble_batched_async(const AssembleTask* tasks, int count,
-                                  void* h_buf, void* d_buf, cudaStream_t st);
+                                  void* h_buf, void* d_buf, cudaStream_t st,
+                                  bool upload = true);
 
 // Tensor-core S pass (tcgen05 + TMA): applicability, launch, and the device
 // count of bounded waits that ran out.

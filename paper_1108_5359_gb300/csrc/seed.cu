@@ -63,6 +63,16 @@ constexpr int kSeedGemmGroup = 4;    // tasks per pass of the tall products
 #define PCP_SEED_LOWP_RES 1e-6
 #endif
 constexpr double kSeedLowpRes = PCP_SEED_LOWP_RES;
+// Power steps on D before the first Rayleigh-Ritz step, whose largest Ritz
+// value stands for ||D||_2 in mu_0 and Y_0.  An FP64 emulation needed the
+// same ALM iteration count with 2, 1 or 0 steps, but on GB300 (FP32 k x k
+// eigen-solve) one step left a 50 x 50 rank-5 seed at 6.5e-4 from the
+// oracle's L^s after 31 iterations, against 5.7e-7 after 25 with two.
+#ifndef PCP_SEED_POWER_STEPS
+#define PCP_SEED_POWER_STEPS 2
+#endif
+constexpr int kSeedPowerSteps = PCP_SEED_POWER_STEPS;
+static_assert(kSeedPowerSteps >= 0 && kSeedPowerSteps <= 2, "0..2 power steps");
 // Largest single-cluster team (a non-portable cluster size on this part).
 constexpr int kSeedClusterMax = 16;
 // limit of one grid-barrier wait when the caller gives none
@@ -392,6 +402,52 @@ __device__ void gram(const double* X, int nrows, int k, int kmax,
   }
 }
 
+// Right-looking Cholesky of the k x k (k <= K <= 32) scaled Gram in A32 by
+// one warp, the matrix held in registers: lane c keeps column c (a[r] =
+// A_rc).  Step j takes the pivot from lane j, every lane c > j scales its
+// entry of row j (R_jc = A_jc / sqrt(A_jj)), and each later row r gets its
+// rank-1 update A_rc -= R_jr R_jc with R_jr broadcast from lane r.  Same
+// operations in the same order per entry as the CTA-wide form, without its
+// k CTA barriers.  The K x K body is straight-line code (no test on k):
+// rows and columns past k hold zeros, so their steps change nothing that
+// is kept, and the broadcasts of a step overlap the next step's pivot
+// chain.  A non-positive pivot (or a dead column) gives R_jj = 1 and a
+// zero row, and marks the column dead.  R (upper triangle and diagonal) is
+// written back to A32; the lower triangle is left as it was.
+template <int K>
+__device__ __noinline__ void chol_warp(float* A32, int k, int* dead) {
+  const int lane = threadIdx.x & 31;
+  const bool own = lane < k;
+  float a[K];
+#pragma unroll
+  for (int r = 0; r < K; ++r)
+    a[r] = (own && r < k) ? A32[r * k + lane] : 0.0f;
+  int dl = own ? dead[lane] : 1;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const float piv = __shfl_sync(0xffffffffu, a[j], j);
+    const int dj = __shfl_sync(0xffffffffu, dl, j);
+    const bool bad = !(piv > 1e-6f) || dj;
+    const float rs = bad ? 0.0f : rsqrtf(piv);
+    float rj = a[j] * rs;  // R_jc for lanes c > j
+    if (lane == j) {
+      rj = bad ? 1.0f : piv * rs;
+      if (bad) dl = 1;
+    }
+    if (lane >= j) a[j] = rj;
+    const float rju = lane > j ? rj : 0.0f;  // columns <= j are final
+#pragma unroll
+    for (int r = j + 1; r < K; ++r) {
+      const float rjr = __shfl_sync(0xffffffffu, rj, r);
+      a[r] = fmaf(-rjr, rju, a[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < K; ++r)
+    if (own && r < k && r <= lane) A32[r * k + lane] = a[r];
+  if (own) dead[lane] = dl;
+}
+
 // Column-normalised Cholesky QR: Out = X diag(1/||x_a||) R^{-1} with
 // R^T R = diag(1/||x_a||) X^T X diag(1/||x_a||) (unit diagonal, well
 // conditioned).  The k x k Cholesky factor and its inverse are computed in
@@ -443,7 +499,14 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
   // (warp-synchronous), while warps 1.. update rows j+2.. (a_ab -= R_ja R_jb,
   // b >= a).  A non-positive pivot marks the column dead (R_jj = 1, rest of
   // the row 0).
-  if (!near_orth) {
+  if (!near_orth && k <= 32) {
+    if (tid < 32) {
+      if (k <= 16)
+        chol_warp<16>(A32, k, dead);
+      else
+        chol_warp<32>(A32, k, dead);
+    }
+  } else if (!near_orth) {
     const int lane = tid & 31, w = tid >> 5;
     auto finish_row = [&](int r) {  // warp 0: pivot and scaling of row r
       const float piv = A32[r * k + r];
@@ -1176,7 +1239,8 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
   int k = a.k0;
   double mu = 0.0, mu_max = 0.0, tau = 0.0;
   int it = 0;           // ALM iterations done
-  int stage = 0;        // 0,1: power steps on D; 2: Rayleigh-Ritz on D; 3: ALM
+  // stages below 2: power steps on D; 2: Rayleigh-Ritz on D; 3: ALM
+  int stage = 2 - kSeedPowerSteps;
   bool converged = false;
   double res = 1.0;
   int knext = k;
@@ -2080,7 +2144,7 @@ int* seed_rank_ptr_cta(void* d_work, int mp, int np, int kmax) {
 
 pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
                                   void* h_args, void* d_args,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, bool upload) {
   if (count <= 0) return PCP_OK;
   char* hb = static_cast<char*>(h_args);
   int kmax_all = 2;
@@ -2148,10 +2212,11 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   int nblocks = 0;
   for (int i : order)
     for (int b = 0; b < nb[i]; ++b) tab[nblocks++] = make_int4(i, b, nb[i], 0);
-  PCP_CUDA(cudaMemcpyAsync(d_args, h_args,
-                           seed_args_bytes() * (size_t)count +
-                               sizeof(int4) * (size_t)nblocks,
-                           cudaMemcpyHostToDevice, st));
+  if (upload)
+    PCP_CUDA(cudaMemcpyAsync(d_args, h_args,
+                             seed_args_bytes() * (size_t)count +
+                                 sizeof(int4) * (size_t)nblocks,
+                             cudaMemcpyHostToDevice, st));
   const SeedArgs* d_a = static_cast<const SeedArgs*>(d_args);
   const int4* d_tab = reinterpret_cast<const int4*>(
       static_cast<char*>(d_args) + seed_args_bytes() * (size_t)count);

@@ -255,11 +255,13 @@ __global__ void assemble_batched_kernel(const AssembleTask* __restrict__ tasks) 
 }  // namespace
 
 pcp_status gather_batched_async(const GatherTask* tasks, int count,
-                                void* h_buf, void* d_buf, cudaStream_t st) {
+                                void* h_buf, void* d_buf, cudaStream_t st,
+                                bool upload) {
   if (count <= 0) return PCP_OK;
   std::memcpy(h_buf, tasks, sizeof(GatherTask) * count);
-  PCP_CUDA(cudaMemcpyAsync(d_buf, h_buf, sizeof(GatherTask) * count,
-                           cudaMemcpyHostToDevice, st));
+  if (upload)
+    PCP_CUDA(cudaMemcpyAsync(d_buf, h_buf, sizeof(GatherTask) * count,
+                             cudaMemcpyHostToDevice, st));
   int64_t biggest = 1;
   for (int i = 0; i < count; ++i)
     biggest = std::max<int64_t>(biggest, (int64_t)tasks[i].mp * tasks[i].np);
@@ -271,11 +273,13 @@ pcp_status gather_batched_async(const GatherTask* tasks, int count,
 }
 
 pcp_status assemble_batched_async(const AssembleTask* tasks, int count,
-                                  void* h_buf, void* d_buf, cudaStream_t st) {
+                                  void* h_buf, void* d_buf, cudaStream_t st,
+                                  bool upload) {
   if (count <= 0) return PCP_OK;
   std::memcpy(h_buf, tasks, sizeof(AssembleTask) * count);
-  PCP_CUDA(cudaMemcpyAsync(d_buf, h_buf, sizeof(AssembleTask) * count,
-                           cudaMemcpyHostToDevice, st));
+  if (upload)
+    PCP_CUDA(cudaMemcpyAsync(d_buf, h_buf, sizeof(AssembleTask) * count,
+                             cudaMemcpyHostToDevice, st));
   int64_t biggest = 1;
   for (int i = 0; i < count; ++i)
     biggest = std::max<int64_t>(

@@ -230,7 +230,9 @@ def test_batch_plan_replays_the_batch_bit_for_bit():
             Lu.fill_(float("nan"))
             Lv.fill_(float("nan"))
             S.fill_(float("nan"))
-        st2, infos = plan.run()
+        # statuses are compared, not required to be 0: an instance whose
+        # seed fails Eq. rank_test fails it in both forms
+        st2, infos = plan.run(raise_on_error=False)
         torch.cuda.synchronize()
         for i, ((_, Lu, Lv, S), o, inf) in enumerate(zip(bufs, direct, infos)):
             assert inf.status == o["info"]["status"], (rep, i)
