@@ -105,8 +105,8 @@ def parse():
                          "FP32-accurate), bf16 / tf32 (one-pass BF16 / TF32 "
                          "tensor-core iterations then split-TF32 "
                          "refinement), fp32simt (FP32 FMA)")
-    ap.add_argument("--r-max", type=int, default=25,
-                    help="batch: largest rank drawn (seed 10r <= 256)")
+    ap.add_argument("--r-max", type=int, default=30,
+                    help="batch: largest rank drawn (also r <= min(m, n) / 20)")
     return ap.parse_args()
 
 
@@ -625,8 +625,9 @@ def run_ours(args):
                               "between steps outside the timed span"}
         subs["large"] = r3
         del rec3, P3, M3
-        subs["batch"] = batch_record(pk, torch, dev, count=64, steps=3,
-                                     warmup=3, seed=args.seed, r_max=25)
+        subs["batch"] = batch_record(pk, torch, dev, count=256, steps=3,
+                                     warmup=3, seed=args.seed, r_max=30,
+                                     precision="bf16")
     if rank == 0:
         out = {"metric": METRIC, "value": body.pop("value"),
                "unit": body.pop("unit"), "n_gpus": ws,
@@ -655,10 +656,11 @@ def _pct(v, q):
     return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
 
 
-def batch_record(pk, torch, dev, count, steps, warmup, seed, r_max):
+def batch_record(pk, torch, dev, count, steps, warmup, seed, r_max,
+                 precision="fp32"):
     """Uneven instances: one pcp_l1filter_batch call per step against one
-    pcp_l1filter_solve per instance (plans made outside the timed span);
-    returns the record."""
+    pcp_l1filter_solve per instance (plans made outside the timed span),
+    both in the given Algorithm 1 precision form; returns the record."""
     from paper_1108_5359_gb300 import synth
     t0 = time.perf_counter()
     Ps = synth.uneven_instances(count=count, seed=seed, r_max=r_max,
@@ -675,11 +677,13 @@ def batch_record(pk, torch, dev, count, steps, warmup, seed, r_max):
         # seeds by order, grown on a failed rank test (Section 3.5)
         prm = pk.pcp_params_default(P.m, P.n, P.r)
         prm.grow_seed = 1
+        prm.precision = PRECISIONS[precision]
         ro, co = synth.seed_orders(P.m, P.n, P.rows, P.cols, seed=seed)
         probs.append(pk.problem(prm, dM, Lu, Lv, S, row_order=ro,
                                 col_order=co))
         prm2 = pk.pcp_params_default(P.m, P.n, P.r)
         prm2.grow_seed = 1
+        prm2.precision = PRECISIONS[precision]
         plans.append(pk.Plan(prm2, row_order=ro, col_order=co))
     entries = sum(P.m * P.n for P in Ps)
     stream = torch.cuda.current_stream()
@@ -774,12 +778,24 @@ def batch_record(pk, torch, dev, count, steps, warmup, seed, r_max):
         "value": ok_entries / (tb * 1e-3),
         "unit": "entries/s", "n_gpus": 1, "steps": steps,
         "warmup": max(3, warmup), "ms_per_step": tb,
-        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "higher_is_better": True,
+        "dtype": {"fp32": "f32", "bf16": "bf16+f32", "tf32": "tf32+f32",
+                  "fp32simt": "f32"}[precision],
+        "data": "synthetic",
         "config": {"workload": f"uneven{count}_r3-{r_max}",
                    "desc": f"{count} instances, m~U[300,4000], "
-                           f"n~U[200,3000], r~U[3,{r_max}], density "
-                           "U[0.02,0.15], values U[-50,50], seed 10r x 10r, "
-                           "FP32 M",
+                           f"n~U[200,3000], r~U[3,min({r_max}, min(m,n)/20)], "
+                           "density U[0.02,0.15], values U[-50,50], seed "
+                           "10r x 10r (grown on a failed rank test), FP32 M; "
+                           "Algorithm 1 " + {
+                               "fp32": "FP32 (PCP_FP32)",
+                               "bf16": "BF16 one-pass products then "
+                                       "split-TF32 refinement "
+                                       "(PCP_BF16_REFINED)",
+                               "tf32": "TF32 one-pass products then "
+                                       "split-TF32 refinement "
+                                       "(PCP_TF32_REFINED)",
+                               "fp32simt": "FP32 SIMT"}[precision],
                    "entries_per_step": entries,
                    "entries_recovered_per_step": ok_entries,
                    "generate_s": t_gen,
@@ -818,7 +834,8 @@ def run_batch(args):
     pkbuild.build()
     pk.load()
     out = batch_record(pk, torch, torch.device("cuda", 0), args.count,
-                       args.steps, args.warmup, args.seed, args.r_max)
+                       args.steps, args.warmup, args.seed, args.r_max,
+                       args.precision)
     print(json.dumps(out), flush=True)
 
 

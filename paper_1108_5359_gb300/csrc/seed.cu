@@ -36,6 +36,7 @@
 // bit-identical factors.  Cross-CTA data is read with L2-only loads
 // (ld.global.cg) so no CTA sees a stale L1 line.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <queue>
@@ -2041,13 +2042,18 @@ __global__ void __launch_bounds__(kSeedThreads, 1)
 // control block (the launch is cooperative, so every team is co-resident).
 __global__ void __launch_bounds__(kSeedThreads, 2)
     seed_alm_team_kernel(const SeedArgs* __restrict__ args,
-                         const int4* __restrict__ team) {
+                         const int4* __restrict__ team,
+                         const int* __restrict__ lists) {
   const int4 t = team[blockIdx.x];
-  const SeedArgs a = args[t.x];
-  if (t.z == 1)
-    seed_alm_body<kTeamCta>(a, 0, 1);
-  else
-    seed_alm_body<kTeamGrid>(a, t.y, t.z);
+  if (t.z == 1) {
+    // a list of seeds solved one after another by this CTA alone
+    for (int q = 0; q < t.w; ++q) {
+      if (q > 0) __syncthreads();
+      seed_alm_body<kTeamCta>(args[lists[t.x + q]], 0, 1);
+    }
+  } else {
+    seed_alm_body<kTeamGrid>(args[t.x], t.y, t.z);
+  }
 }
 
 // Control blocks start at zero (barrier counters included) before any team
@@ -2129,7 +2135,8 @@ size_t seed_args_bytes() { return sizeof(SeedArgs); }
 
 size_t seed_batched_args_bytes(int count) {
   return seed_args_bytes() * (size_t)count +
-         sizeof(int4) * ((size_t)count + kMaxCoopBlocks);
+         sizeof(int4) * ((size_t)count + kMaxCoopBlocks) +
+         sizeof(int) * (size_t)count;
 }
 
 SeedCtl* seed_ctl_ptr_cta(void* d_work, int mp, int np, int kmax) {
@@ -2173,62 +2180,134 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   PCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &per_sm, seed_alm_team_kernel, kSeedThreads, smem));
   const int slots = std::min(per_sm * sms, kMaxCoopBlocks);
-  // Team sizes: FP64 work of one ALM iteration ~ m' n' k (plus a fixed
-  // latency share); spare CTAs go one by one to the seed with the most work
-  // per CTA, up to kSeedTeamMax and a quarter of its shorter side.
-  std::vector<int> nb(count, 1);
-  const bool teams = coop && slots >= count && count > 0;
-  if (teams) {
-    std::vector<double> w(count);
-    std::vector<int> cap(count);
-    using Item = std::pair<double, int>;
-    std::priority_queue<Item> pq;
-    for (int i = 0; i < count; ++i) {
-      w[i] = (double)tasks[i].mp * tasks[i].np * tasks[i].k0 + 2.0e4;
-      cap[i] = std::max(1, std::min(kSeedTeamMax,
-                                    std::min(tasks[i].mp, tasks[i].np) / 4));
-      pq.push({w[i], i});
+  // Schedule (host, deterministic).  Per ALM pass a seed costs about
+  // w = m' n' k units on one CTA plus a fixed share (its k x k steps), and
+  // w / nb plus a larger fixed share (the grid barriers) on a team of nb
+  // CTAs.  With a cooperative launch of `slots` CTAs: seeds whose work is
+  // above a target load T get teams of ceil(w / T) CTAs (at most
+  // kSeedTeamMax and a quarter of the shorter side), and the other seeds
+  // are packed, largest first, onto the remaining CTAs as lists that a CTA
+  // solves one after another; T is taken from a geometric grid between the
+  // balanced load and the largest seed, minimising the longest CTA.  A
+  // seed's result does not depend on its team or list (fixed reduction
+  // slots), so the schedule changes no bits.
+  const int n = count;
+  std::vector<double> w(n);
+  std::vector<int> cap(n);
+  double wsum = 0.0, wmax = 0.0;
+  for (int i = 0; i < n; ++i) {
+    w[i] = (double)tasks[i].mp * tasks[i].np * tasks[i].k0;
+    cap[i] = std::max(1, std::min(kSeedTeamMax,
+                                  std::min(tasks[i].mp, tasks[i].np) / 4));
+    wsum += w[i];
+    wmax = std::max(wmax, w[i]);
+  }
+  constexpr double kCtaFixed = 1.5e4, kTeamFixed = 3.0e4;
+  std::vector<int> by_w(n);
+  for (int i = 0; i < n; ++i) by_w[i] = i;
+  std::stable_sort(by_w.begin(), by_w.end(),
+                   [&](int x, int y) { return w[x] > w[y]; });
+  std::vector<int> nb(n, 1), bin(n, -1);
+  int nlist = 0;  // CTAs that run lists
+  auto plan_for = [&](double T, std::vector<int>& nbv, std::vector<int>& binv,
+                      int& nl) -> double {
+    int used = 0;
+    double worst = 0.0;
+    for (int i : by_w) {
+      nbv[i] = 1;
+      if (w[i] > T && cap[i] > 1) {
+        nbv[i] = std::min(cap[i], (int)std::ceil(w[i] / T));
+        if (nbv[i] < 2) nbv[i] = 1;
+      }
+      if (nbv[i] > 1) {
+        used += nbv[i];
+        worst = std::max(worst, w[i] / nbv[i] + kTeamFixed);
+      }
     }
-    int spare = slots - count;
-    while (spare > 0 && !pq.empty()) {
-      const int i = pq.top().second;
-      pq.pop();
-      if (nb[i] >= cap[i]) continue;
-      ++nb[i];
-      --spare;
-      pq.push({w[i] / nb[i], i});
+    nl = slots - used;
+    if (nl < 1) return 1e300;
+    // LPT over the list CTAs (a min-heap of loads)
+    using Bin = std::pair<double, int>;
+    std::priority_queue<Bin, std::vector<Bin>, std::greater<Bin>> heap;
+    for (int b = 0; b < nl; ++b) heap.push({0.0, b});
+    for (int i : by_w) {
+      if (nbv[i] > 1) continue;
+      Bin top = heap.top();
+      heap.pop();
+      binv[i] = top.second;
+      top.first += w[i] + kCtaFixed;
+      worst = std::max(worst, top.first);
+      heap.push(top);
+    }
+    return worst;
+  };
+  if (coop && slots >= 1) {
+    double best = 1e301;
+    std::vector<int> nbv(n), binv(n);
+    const double lo = std::max(1.0, wsum / slots);
+    const double hi = std::max(lo, wmax);
+    for (int g = 0; g <= 24; ++g) {
+      const double T = lo * std::pow(hi / lo, g / 24.0);
+      int nl = 0;
+      const double m = plan_for(T, nbv, binv, nl);
+      if (m < best) {
+        best = m;
+        nb = nbv;
+        bin = binv;
+        nlist = nl;
+      }
     }
   }
-  // block table after the argument blocks; without teams (more seeds than
-  // co-resident CTAs) one CTA per seed, largest first
+  const bool coop_launch = coop && nlist >= 1;
+  if (!coop_launch) {
+    // no cooperative launch: one CTA per seed, largest first, scheduled
+    // by the hardware as CTAs finish
+    std::fill(nb.begin(), nb.end(), 1);
+    for (int q = 0; q < n; ++q) bin[by_w[q]] = q;
+    nlist = n;
+  }
+  // block table after the argument blocks: team CTAs {seed, rank, size, 0},
+  // then list CTAs {list offset, 0, 1, length}; the lists follow the table
   int4* tab = reinterpret_cast<int4*>(hb + seed_args_bytes() * (size_t)count);
-  std::vector<int> order(count);
-  for (int i = 0; i < count; ++i) order[i] = i;
-  if (!teams)
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-      return (double)tasks[x].mp * tasks[x].np * tasks[x].k0 >
-             (double)tasks[y].mp * tasks[y].np * tasks[y].k0;
-    });
   int nblocks = 0;
-  for (int i : order)
-    for (int b = 0; b < nb[i]; ++b) tab[nblocks++] = make_int4(i, b, nb[i], 0);
+  for (int i : by_w)
+    if (nb[i] > 1)
+      for (int b = 0; b < nb[i]; ++b) tab[nblocks++] = make_int4(i, b, nb[i], 0);
+  std::vector<std::vector<int>> lists(nlist);
+  for (int i : by_w)
+    if (nb[i] == 1) lists[bin[i]].push_back(i);
+  int* lst = reinterpret_cast<int*>(tab + nblocks + nlist);
+  int off = 0;
+  for (int b = 0; b < nlist; ++b) {
+    tab[nblocks + b] = make_int4(off, 0, 1, (int)lists[b].size());
+    for (int i : lists[b]) lst[off++] = i;
+  }
+  nblocks += nlist;
+  const size_t used_bytes = seed_args_bytes() * (size_t)count +
+                            sizeof(int4) * (size_t)nblocks +
+                            sizeof(int) * (size_t)off;
+  if (used_bytes > seed_batched_args_bytes(count)) {
+    set_error("batched seed: schedule of %d CTAs does not fit its block",
+              nblocks);
+    return PCP_ERR_ARG;
+  }
   if (upload)
-    PCP_CUDA(cudaMemcpyAsync(d_args, h_args,
-                             seed_args_bytes() * (size_t)count +
-                                 sizeof(int4) * (size_t)nblocks,
+    PCP_CUDA(cudaMemcpyAsync(d_args, h_args, used_bytes,
                              cudaMemcpyHostToDevice, st));
   const SeedArgs* d_a = static_cast<const SeedArgs*>(d_args);
   const int4* d_tab = reinterpret_cast<const int4*>(
       static_cast<char*>(d_args) + seed_args_bytes() * (size_t)count);
+  const int* d_lst = reinterpret_cast<const int*>(d_tab + nblocks);
   seed_ctl_zero_kernel<<<std::min(count, 1024), 64, 0, st>>>(d_a, count);
   PCP_CUDA(cudaGetLastError());
-  if (teams) {
-    void* kargs[] = {(void*)&d_a, (void*)&d_tab};
+  if (coop_launch) {
+    void* kargs[] = {(void*)&d_a, (void*)&d_tab, (void*)&d_lst};
     PCP_CUDA(cudaLaunchCooperativeKernel((void*)seed_alm_team_kernel,
                                          dim3(nblocks), dim3(kSeedThreads),
                                          kargs, smem, st));
   } else {
-    seed_alm_team_kernel<<<nblocks, kSeedThreads, smem, st>>>(d_a, d_tab);
+    seed_alm_team_kernel<<<nblocks, kSeedThreads, smem, st>>>(d_a, d_tab,
+                                                               d_lst);
     PCP_CUDA(cudaGetLastError());
   }
   return PCP_OK;
