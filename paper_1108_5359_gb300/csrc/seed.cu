@@ -1455,39 +1455,52 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
       if (b == 0 && tid == 0) ctl->jcyc[2] += clock64() - tj1;
     }
     trace_mark(a, 8);
-    // ---- rotate: Pt = P V, PsiT = Psi V, partial column sums of Pt^2 --------
-    // Thread (c, part) owns column c of this CTA's rows i = b + (part + s *
-    // nparts) * nb; partial sums of Pt^2 are reduced over parts in a fixed
-    // order, so the result does not depend on timing.
+    // ---- rotate: Pt = P V, PsiT = Psi V, slot column sums of Pt^2 ---------
+    // Thread (c, part) computes column c of the rows it takes; the sums of
+    // Pt^2 per partial-sum slot follow in a fixed order (below), so they do
+    // not depend on timing or on the team's size.
     {
       const int nparts = kSeedThreads / k;
       const int c = tid % k, part = tid / k;
-      for (int v = b; v < nv; v += nb) {
-        double csq = 0.0;
-        if (part < nparts) {
-          for (int i = v + part * nv; i < mp; i += nv * nparts) {
-            const double* pr = a.P + (size_t)i * kmax;
-            double s0 = 0.0, s1 = 0.0;
-            int q = 0;
-            for (; q + 1 < k; q += 2) {
-              s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
-              s1 = fma(ldg_cg(pr + q + 1), Vd[(q + 1) * k + c], s1);
-            }
-            if (q < k) s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
-            const double sv = s0 + s1;
-            __stcg(a.Pt + (size_t)i * kmax + c, sv);
+      // The rows of all the slots this CTA owns are rotated in parallel
+      // (slot v holds rows v, v + nv, ...); after one CTA barrier each
+      // slot's column sums of Pt^2 are formed from the stored rows in a
+      // fixed order: per part q the rows v + (q + s nparts) nv in turn, then
+      // the parts in order, so the sums do not depend on the team's size.
+      const int myslots = (nv - b + nb - 1) / nb;
+      const int rps = (mp + nv - 1) / nv;  // rows per slot, at most
+      if (part < nparts) {
+        for (int ri = part; ri < myslots * rps; ri += nparts) {
+          const int ls = ri % myslots, t = ri / myslots;
+          const int i = b + ls * nb + t * nv;
+          if (i >= mp) continue;
+          const double* pr = a.P + (size_t)i * kmax;
+          double s0 = 0.0, s1 = 0.0;
+          int q = 0;
+          for (; q + 1 < k; q += 2) {
+            s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
+            s1 = fma(ldg_cg(pr + q + 1), Vd[(q + 1) * k + c], s1);
+          }
+          if (q < k) s0 = fma(ldg_cg(pr + q), Vd[q * k + c], s0);
+          __stcg(a.Pt + (size_t)i * kmax + c, s0 + s1);
+        }
+      }
+      __syncthreads();
+      for (int idx = tid; idx < myslots * k; idx += kSeedThreads) {
+        const int ls = idx / k, cc = idx - ls * k;
+        const int v = b + ls * nb;
+        double s2 = 0.0;
+        for (int q = 0; q < nparts; ++q) {
+          double csq = 0.0;
+          for (int i = v + q * nv; i < mp; i += nv * nparts) {
+            const double sv = ldg_cg(a.Pt + (size_t)i * kmax + cc);
             csq = fma(sv, sv, csq);
           }
-          red[part * k + c] = csq;
+          s2 += csq;
         }
-        __syncthreads();
-        if (tid < k) {
-          double s2 = 0.0;
-          for (int q = 0; q < nparts; ++q) s2 += red[q * k + tid];
-          __stcg(a.colsq + (size_t)v * kmax + tid, s2);
-        }
-        __syncthreads();
+        __stcg(a.colsq + (size_t)v * kmax + cc, s2);
       }
+      __syncthreads();
       if (part < nparts) {
         for (int j = b + part * nb; j < np; j += nb * nparts) {
           const double* pr = a.Psi + (size_t)j * kmax;
@@ -1700,7 +1713,7 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
       float* Qf = Pf + TT * kp;
       const int tcn = (np + TT - 1) / TT;
       const int ntile = ((mp + TT - 1) / TT) * tcn;
-      for (int v = b; v < nv; v += nb) {
+      for (int v = b, ls = 0; v < nv; v += nb, ++ls) {
         double zz = 0.0;
         for (int tile = v; tile < ntile; tile += nv) {
           const int i0 = (tile / tcn) * TT, j0 = (tile % tcn) * TT;
@@ -1761,12 +1774,13 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
           }
           __syncthreads();
         }
-        zz = block_reduce_sum(zz, red);
-        if (tid == 0) __stcg(a.part + 4 * v + 2, zz);
+        // a slot's warp sums wait in shared memory (xs is free here)
+        const double wz = warp_sum(zz);
+        if ((tid & 31) == 0) xs[ls * (kSeedThreads / 32) + (tid >> 5)] = wz;
       }
     } else {
       // narrow subspace: one column at a time
-      for (int v = b; v < nv; v += nb) {
+      for (int v = b, ls = 0; v < nv; v += nb, ++ls) {
         double zz = 0.0;
         for (int j = v; j < np; j += nv) {
           for (int c = tid; c < k; c += kSeedThreads)
@@ -1786,9 +1800,20 @@ __device__ void seed_alm_body(const SeedArgs& a, const int b, const int nb) {
           }
           __syncthreads();
         }
-        zz = block_reduce_sum(zz, red);
-        if (tid == 0) __stcg(a.part + 4 * v + 2, zz);
+        // a slot's warp sums wait in shared memory (xs is free here)
+        const double wz = warp_sum(zz);
+        if ((tid & 31) == 0) xs[ls * (kSeedThreads / 32) + (tid >> 5)] = wz;
       }
+    }
+    // slot sums of ||Z||^2: the warp sums added in warp order, the same
+    // arithmetic as a block reduction per slot, one CTA barrier in all
+    __syncthreads();
+    for (int ls = tid, nls = (nv - b + nb - 1) / nb; ls < nls;
+         ls += kSeedThreads) {
+      double zs = 0.0;
+      for (int q = 0; q < kSeedThreads / 32; ++q)
+        zs += xs[ls * (kSeedThreads / 32) + q];
+      __stcg(a.part + 4 * (b + ls * nb) + 2, zs);
     }
     if (prof_alm) ctl->sub[7] += clock64() - pa0;  // elementwise update
     ++it;
