@@ -2205,48 +2205,51 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   PCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &per_sm, seed_alm_team_kernel, kSeedThreads, smem));
   const int slots = std::min(per_sm * sms, kMaxCoopBlocks);
-  // Schedule (host, deterministic).  Per ALM pass a seed costs about
-  // w = m' n' k units on one CTA plus a fixed share (its k x k steps), and
-  // w / nb plus a larger fixed share (the grid barriers) on a team of nb
-  // CTAs.  With a cooperative launch of `slots` CTAs: seeds whose work is
-  // above a target load T get teams of ceil(w / T) CTAs (at most
-  // kSeedTeamMax and a quarter of the shorter side), and the other seeds
-  // are packed, largest first, onto the remaining CTAs as lists that a CTA
-  // solves one after another; T is taken from a geometric grid between the
-  // balanced load and the largest seed, minimising the longest CTA.  A
-  // seed's result does not depend on its team or list (fixed reduction
-  // slots), so the schedule changes no bits.
+  // Schedule (host, deterministic).  Cost of one ALM pass on one CTA,
+  // fitted on GB300 to single-seed runs (60 x 60 .. 300 x 300 seeds, one
+  // CTA: 0.38 .. 3.7 ms per pass): c(w) = 300 + 0.076 w^0.72 us with
+  // w = m' n' k; a team of nb CTAs (grid barrier) runs about nb^0.87 times
+  // faster (measured 1.9 / 3.6 / 6.6 / 11.1 at 2 / 4 / 8 / 16 CTAs on the
+  // 300 x 300 seed).  With a cooperative launch of `slots` CTAs: seeds whose
+  // one-CTA cost is above a target T get the smallest team that brings
+  // them under T (at most kSeedTeamMax CTAs and a quarter of the shorter
+  // side), and the other seeds are packed, largest first, onto the
+  // remaining CTAs as lists that a CTA solves one after another; T is
+  // taken from a geometric grid between the balanced load and the largest
+  // seed, minimising the longest CTA.  A seed's result does not depend on
+  // its team or list (fixed reduction slots), so the schedule changes no
+  // bits.
   const int n = count;
-  std::vector<double> w(n);
+  std::vector<double> c1(n);
   std::vector<int> cap(n);
-  double wsum = 0.0, wmax = 0.0;
+  double csum = 0.0, cmax = 0.0;
   for (int i = 0; i < n; ++i) {
-    w[i] = (double)tasks[i].mp * tasks[i].np * tasks[i].k0;
+    const double w = (double)tasks[i].mp * tasks[i].np * tasks[i].k0;
+    c1[i] = 300.0 + 0.076 * std::pow(w, 0.72);
     cap[i] = std::max(1, std::min(kSeedTeamMax,
                                   std::min(tasks[i].mp, tasks[i].np) / 4));
-    wsum += w[i];
-    wmax = std::max(wmax, w[i]);
+    csum += c1[i];
+    cmax = std::max(cmax, c1[i]);
   }
-  constexpr double kCtaFixed = 1.5e4, kTeamFixed = 3.0e4;
-  std::vector<int> by_w(n);
-  for (int i = 0; i < n; ++i) by_w[i] = i;
-  std::stable_sort(by_w.begin(), by_w.end(),
-                   [&](int x, int y) { return w[x] > w[y]; });
+  constexpr double kTeamExp = 0.87;
+  std::vector<int> by_c(n);
+  for (int i = 0; i < n; ++i) by_c[i] = i;
+  std::stable_sort(by_c.begin(), by_c.end(),
+                   [&](int x, int y) { return c1[x] > c1[y]; });
   std::vector<int> nb(n, 1), bin(n, -1);
   int nlist = 0;  // CTAs that run lists
   auto plan_for = [&](double T, std::vector<int>& nbv, std::vector<int>& binv,
                       int& nl) -> double {
     int used = 0;
     double worst = 0.0;
-    for (int i : by_w) {
+    for (int i : by_c) {
       nbv[i] = 1;
-      if (w[i] > T && cap[i] > 1) {
-        nbv[i] = std::min(cap[i], (int)std::ceil(w[i] / T));
-        if (nbv[i] < 2) nbv[i] = 1;
-      }
-      if (nbv[i] > 1) {
+      if (c1[i] > T && cap[i] > 1) {
+        const int want =
+            (int)std::ceil(std::pow(c1[i] / T, 1.0 / kTeamExp) - 1e-9);
+        nbv[i] = std::min(cap[i], std::max(2, want));
         used += nbv[i];
-        worst = std::max(worst, w[i] / nbv[i] + kTeamFixed);
+        worst = std::max(worst, c1[i] / std::pow((double)nbv[i], kTeamExp));
       }
     }
     nl = slots - used;
@@ -2255,12 +2258,12 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
     using Bin = std::pair<double, int>;
     std::priority_queue<Bin, std::vector<Bin>, std::greater<Bin>> heap;
     for (int b = 0; b < nl; ++b) heap.push({0.0, b});
-    for (int i : by_w) {
+    for (int i : by_c) {
       if (nbv[i] > 1) continue;
       Bin top = heap.top();
       heap.pop();
       binv[i] = top.second;
-      top.first += w[i] + kCtaFixed;
+      top.first += c1[i];
       worst = std::max(worst, top.first);
       heap.push(top);
     }
@@ -2269,10 +2272,10 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   if (coop && slots >= 1) {
     double best = 1e301;
     std::vector<int> nbv(n), binv(n);
-    const double lo = std::max(1.0, wsum / slots);
-    const double hi = std::max(lo, wmax);
-    for (int g = 0; g <= 24; ++g) {
-      const double T = lo * std::pow(hi / lo, g / 24.0);
+    const double lo = std::max(1.0, 0.5 * csum / slots);
+    const double hi = std::max(lo, cmax);
+    for (int g = 0; g <= 40; ++g) {
+      const double T = lo * std::pow(hi / lo, g / 40.0);
       int nl = 0;
       const double m = plan_for(T, nbv, binv, nl);
       if (m < best) {
@@ -2288,18 +2291,18 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
     // no cooperative launch: one CTA per seed, largest first, scheduled
     // by the hardware as CTAs finish
     std::fill(nb.begin(), nb.end(), 1);
-    for (int q = 0; q < n; ++q) bin[by_w[q]] = q;
+    for (int q = 0; q < n; ++q) bin[by_c[q]] = q;
     nlist = n;
   }
   // block table after the argument blocks: team CTAs {seed, rank, size, 0},
   // then list CTAs {list offset, 0, 1, length}; the lists follow the table
   int4* tab = reinterpret_cast<int4*>(hb + seed_args_bytes() * (size_t)count);
   int nblocks = 0;
-  for (int i : by_w)
+  for (int i : by_c)
     if (nb[i] > 1)
       for (int b = 0; b < nb[i]; ++b) tab[nblocks++] = make_int4(i, b, nb[i], 0);
   std::vector<std::vector<int>> lists(nlist);
-  for (int i : by_w)
+  for (int i : by_c)
     if (nb[i] == 1) lists[bin[i]].push_back(i);
   int* lst = reinterpret_cast<int*>(tab + nblocks + nlist);
   int off = 0;
