@@ -983,6 +983,30 @@ def run_serve(args):
                       "p50_ms": _pct(lp, 0.5), "p99_ms": _pct(lp, 0.99),
                       "ok": sp.count(0)},
         }
+    # error per request kind (reported, not gated): one solve of each kind
+    # through its plan, L = Lu Lv^T and S against the generated L0 and S0
+    # (relative Frobenius, FP64 on the device, in column blocks)
+    accuracy = []
+    stream = torch.cuda.current_stream()
+    for k, P in enumerate(Ps):
+        Lu, Lv, S = views(0, P)
+        st, inf, _, _ = pk.pcp_l1filter_solve(
+            plans[k], dMs[k], Lu, Lv, S, info=True, stream=stream,
+            raise_on_error=False)
+        dl = nl = ds = ns = 0.0
+        for j0 in range(0, P.n, 128):
+            j1 = min(P.n, j0 + 128)
+            L0b = torch.from_numpy(np.ascontiguousarray(P.L0[:, j0:j1])).to(dev)
+            S0b = torch.from_numpy(np.ascontiguousarray(P.S0[:, j0:j1])).to(dev)
+            Lb = Lu.double() @ Lv[j0:j1].double().t()
+            dl += float(((Lb - L0b) ** 2).sum())
+            nl += float((L0b ** 2).sum())
+            ds += float(((S[:, j0:j1].double() - S0b) ** 2).sum())
+            ns += float((S0b ** 2).sum())
+        accuracy.append({"n": P.n, "r": P.r, "status": int(st),
+                         "seed": [int(inf.seed_m), int(inf.seed_n)],
+                         "relerr_L_vs_L0": (dl / nl) ** 0.5,
+                         "relerr_S_vs_S0": (ds / ns) ** 0.5})
     for pl in plans:
         pl.close()
     out = {
@@ -997,6 +1021,7 @@ def run_serve(args):
         "latency_ms": {"p50": res["poisson"]["served"]["p50_ms"],
                        "p99": res["poisson"]["served"]["p99_ms"]},
         "results": res,
+        "accuracy_per_kind": accuracy,
     }
     print(json.dumps(out), flush=True)
 

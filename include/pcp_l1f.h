@@ -27,7 +27,11 @@
  *   - Errors are returned as pcp_status; nothing aborts or traps.  The
  *     message of the last error on the calling thread is available from
  *     pcp_last_error().  On an error no output is guaranteed.
- *   - Floating point: M, S and the L factors are FP32; the seed PCP is FP64.
+ *   - Floating point: M, S and the L factors are FP32.  The seed PCP keeps
+ *     its ALM state (S, Y, G), the Ritz values and the final skinny SVD of
+ *     L^s in FP64 (U^s, V^s orthonormal to FP64 rounding); inside the ALM
+ *     the k x k Cholesky and Jacobi steps are FP32 and, while the residual
+ *     is above 1e-6, so are the tall and rank-k products.
  */
 #ifndef PCP_L1F_H
 #define PCP_L1F_H

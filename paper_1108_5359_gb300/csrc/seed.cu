@@ -2212,7 +2212,7 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   // faster (measured 1.9 / 3.6 / 6.6 / 11.1 at 2 / 4 / 8 / 16 CTAs on the
   // 300 x 300 seed).  With a cooperative launch of `slots` CTAs: seeds whose
   // one-CTA cost is above a target T get the smallest team that brings
-  // them under T (at most kSeedTeamMax CTAs and a quarter of the shorter
+  // them under T (at most kSeedTeamMax CTAs, and a quarter of the shorter
   // side), and the other seeds are packed, largest first, onto the
   // remaining CTAs as lists that a CTA solves one after another; T is
   // taken from a geometric grid between the balanced load and the largest
@@ -2226,8 +2226,13 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   for (int i = 0; i < n; ++i) {
     const double w = (double)tasks[i].mp * tasks[i].np * tasks[i].k0;
     c1[i] = 300.0 + 0.076 * std::pow(w, 0.72);
+    // a quarter of the shorter side, or more when the batch leaves CTAs
+    // idle: a small seed's phases are latency bound, and each CTA of a
+    // larger team takes fewer of the rows, entries and tasks in turn
+    // (one 20 x 20 seed: 1.79 ms on 5 CTAs, 1.31 ms on the 152-CTA grid)
     cap[i] = std::max(1, std::min(kSeedTeamMax,
-                                  std::min(tasks[i].mp, tasks[i].np) / 4));
+                                  std::max(std::min(tasks[i].mp, tasks[i].np) / 4,
+                                           slots / std::max(1, count))));
     csum += c1[i];
     cmax = std::max(cmax, c1[i]);
   }
