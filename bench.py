@@ -64,6 +64,12 @@ TRAFFIC = {
     ("c3_20000_r50", "spass", "spass_tc_kernel"): (
         2895202000, "profiles/spass_tc_kernel_c2_5000_r20.md: 8000^2 capture "
         "(463.2 MB) scaled by the entry count (x 6.25)"),
+    # Algorithm 1: both launches of one solve (column and row filter)
+    ("c2_5000_r20", "filter", "adm_tc_kernel"): (
+        72495872, "profiles/adm_tc_kernel_c2_5000_r20.md"),
+    ("c3_20000_r50", "filter", "adm_tc_kernel"): (
+        604521216, "profiles/adm_tc_kernel_bf16_c3_8000_r50.md: 8000^2 "
+        "capture (232.5 MB) scaled by the problem count (x 2.6)"),
 }
 PRECISIONS = {"fp32": 0, "bf16": 1, "tf32": 2, "fp32simt": 5}
 
