@@ -374,32 +374,6 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
   h->h_asm.resize(sizeof(AssembleTask) * count);
   h->h_sargs.resize(seed_batched_args_bytes(count));
   h->h_filt.resize(fbytes);
-  if (timed) {
-    for (cudaEvent_t& e : h->ev) PCP_CUDA(cudaEventCreate(&e));
-    PCP_CUDA(cudaEventRecord(h->ev[0], st));
-  }
-  pcp_status s;
-  NvtxStages nvtx("pcp.batch.seed");
-  // a plan's capture follows its direct run on the same workspace: the
-  // argument blocks there already hold these bytes, so the graph carries
-  // no host copies
-  const bool upload = !h->indices_ready;
-  if ((s = gather_batched_async(gat.data(), count, h->h_gat.data(),
-                                base + o_gat, st, upload)) != PCP_OK)
-    return s;
-  if ((s = seed_pcp_batched_async(seeds.data(), count, h->h_sargs.data(),
-                                  base + o_sargs, st, upload)) != PCP_OK)
-    return s;
-  if ((s = assemble_batched_async(asmb.data(), count, h->h_asm.data(),
-                                  base + o_asm, st, upload)) != PCP_OK)
-    return s;
-  if (timed) PCP_CUDA(cudaEventRecord(h->ev[1], st));
-  nvtx.next("pcp.batch.filter");
-  if ((s = l1_filter_batched_async(sets.data(), 2 * count, h->h_filt.data(),
-                                   base + o_filt, st, upload)) != PCP_OK)
-    return s;
-  if (timed) PCP_CUDA(cudaEventRecord(h->ev[2], st));
-  nvtx.next("pcp.batch.spass");
   h->h_stask.resize(sizeof(SummaryTask) * count);
   SummaryTask* stask = reinterpret_cast<SummaryTask*>(h->h_stask.data());
   for (int i = 0; i < count; ++i) {
@@ -409,10 +383,51 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
                            b.d_iters, (q.m - b.mp) + (q.n - b.np), b.d_bad};
   }
   h->d_summary = reinterpret_cast<BatchSummary*>(base + o_sum);
-  if (upload)
+  pcp_status s;
+  // Every argument block is copied before the first launch: a copy from
+  // pageable host memory issued behind a running kernel would hold the
+  // calling thread until that kernel ends (the server's scheduler thread
+  // among them).  A plan's capture follows its direct run on the same
+  // workspace: the blocks there already hold these bytes, so the graph
+  // carries no host copies.
+  if (!h->indices_ready) {
+    if ((s = gather_batched_async(gat.data(), count, h->h_gat.data(),
+                                  base + o_gat, st, true, false)) != PCP_OK ||
+        (s = seed_pcp_batched_async(seeds.data(), count, h->h_sargs.data(),
+                                    base + o_sargs, st, true, false)) !=
+            PCP_OK ||
+        (s = assemble_batched_async(asmb.data(), count, h->h_asm.data(),
+                                    base + o_asm, st, true, false)) !=
+            PCP_OK ||
+        (s = l1_filter_batched_async(sets.data(), 2 * count,
+                                     h->h_filt.data(), base + o_filt, st,
+                                     true, false)) != PCP_OK)
+      return s;
     PCP_CUDA(cudaMemcpyAsync(base + o_stask, stask,
                              sizeof(SummaryTask) * count,
                              cudaMemcpyHostToDevice, st));
+  }
+  if (timed) {
+    for (cudaEvent_t& e : h->ev) PCP_CUDA(cudaEventCreate(&e));
+    PCP_CUDA(cudaEventRecord(h->ev[0], st));
+  }
+  NvtxStages nvtx("pcp.batch.seed");
+  if ((s = gather_batched_async(gat.data(), count, h->h_gat.data(),
+                                base + o_gat, st, false)) != PCP_OK)
+    return s;
+  if ((s = seed_pcp_batched_async(seeds.data(), count, h->h_sargs.data(),
+                                  base + o_sargs, st, false)) != PCP_OK)
+    return s;
+  if ((s = assemble_batched_async(asmb.data(), count, h->h_asm.data(),
+                                  base + o_asm, st, false)) != PCP_OK)
+    return s;
+  if (timed) PCP_CUDA(cudaEventRecord(h->ev[1], st));
+  nvtx.next("pcp.batch.filter");
+  if ((s = l1_filter_batched_async(sets.data(), 2 * count, h->h_filt.data(),
+                                   base + o_filt, st, false)) != PCP_OK)
+    return s;
+  if (timed) PCP_CUDA(cudaEventRecord(h->ev[2], st));
+  nvtx.next("pcp.batch.spass");
   batch_summary_kernel<<<count, 256, 0, st>>>(
       reinterpret_cast<const SummaryTask*>(base + o_stask), h->d_summary);
   PCP_CUDA(cudaGetLastError());

@@ -341,7 +341,8 @@ size_t filter_batch_bytes(const FilterSet* sets, int nsets) {
 
 pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
                                    void* h_buf, void* d_buf,
-                                   cudaStream_t st, bool upload) {
+                                   cudaStream_t st, bool upload,
+                                   bool launch) {
   if (nsets <= 0) return PCP_OK;
   char* hb = static_cast<char*>(h_buf);
   FilterArgs* ha = reinterpret_cast<FilterArgs*>(hb);
@@ -397,6 +398,7 @@ pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
   }
   if (upload)
     PCP_CUDA(cudaMemcpyAsync(d_buf, h_buf, used, cudaMemcpyHostToDevice, st));
+  if (!launch) return PCP_OK;
   char* db = static_cast<char*>(d_buf);
   const FilterArgs* d_sets = reinterpret_cast<const FilterArgs*>(db);
   for (int c = 0; c < kShapeClasses; ++c) {

@@ -45,10 +45,14 @@ size_t seed_batched_args_bytes(int count);
 // (cooperative launch) when every seed gets at least one co-resident CTA,
 // else one CTA per seed.  upload = false: d_args already holds the same
 // packed bytes (a batch plan's capture after its direct run), nothing is
-// copied.  The same flag on the other batched launches below.
+// copied; launch = false: pack and copy only (the batched solve copies every
+// argument block before its first launch, so that no copy from pageable
+// host memory waits behind a running kernel).  The same flags on the other
+// batched launches below.
 pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
                                   void* h_args, void* d_args,
-                                  cudaStream_t st, bool upload = true);
+                                  cudaStream_t st, bool upload = true,
+                                  bool launch = true);
 // Device addresses of the control block / the seed rank (int) inside a
 // CTA-solver workspace.
 SeedCtl* seed_ctl_ptr_cta(void* d_work, int mp, int np, int kmax);
@@ -129,7 +133,8 @@ size_t filter_batch_bytes(const FilterSet* sets, int nsets);
 // shape is fixed by p and r; sets of equal shape share a launch).
 pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
                                    void* h_buf, void* d_buf,
-                                   cudaStream_t st, bool upload = true);
+                                   cudaStream_t st, bool upload = true,
+                                   bool launch = true);
 
 // Batched gather / assembly: one launch for all instances.
 struct GatherTask {
@@ -143,7 +148,7 @@ struct GatherTask {
 };
 pcp_status gather_batched_async(const GatherTask* tasks, int count,
                                 void* h_buf, void* d_buf, cudaStream_t st,
-                                bool upload = true);
+                                bool upload = true, bool launch = true);
 struct AssembleTask {
   const double *U, *Sigma, *V;
   int mp, np, ku, r;
@@ -155,7 +160,7 @@ struct AssembleTask {
 };
 pcp_status assemble_batched_async(const AssembleTask* tasks, int count,
                                   void* h_buf, void* d_buf, cudaStream_t st,
-                                  bool upload = true);
+                                  bool upload = true, bool launch = true);
 
 // Tensor-core S pass (tcgen05 + TMA): applicability, launch, and the device
 // count of bounded waits that ran out.

@@ -2176,7 +2176,7 @@ int* seed_rank_ptr_cta(void* d_work, int mp, int np, int kmax) {
 
 pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
                                   void* h_args, void* d_args,
-                                  cudaStream_t st, bool upload) {
+                                  cudaStream_t st, bool upload, bool launch) {
   if (count <= 0) return PCP_OK;
   char* hb = static_cast<char*>(h_args);
   int kmax_all = 2;
@@ -2327,6 +2327,7 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   if (upload)
     PCP_CUDA(cudaMemcpyAsync(d_args, h_args, used_bytes,
                              cudaMemcpyHostToDevice, st));
+  if (!launch) return PCP_OK;
   const SeedArgs* d_a = static_cast<const SeedArgs*>(d_args);
   const int4* d_tab = reinterpret_cast<const int4*>(
       static_cast<char*>(d_args) + seed_args_bytes() * (size_t)count);

@@ -256,12 +256,13 @@ __global__ void assemble_batched_kernel(const AssembleTask* __restrict__ tasks) 
 
 pcp_status gather_batched_async(const GatherTask* tasks, int count,
                                 void* h_buf, void* d_buf, cudaStream_t st,
-                                bool upload) {
+                                bool upload, bool launch) {
   if (count <= 0) return PCP_OK;
   std::memcpy(h_buf, tasks, sizeof(GatherTask) * count);
   if (upload)
     PCP_CUDA(cudaMemcpyAsync(d_buf, h_buf, sizeof(GatherTask) * count,
                              cudaMemcpyHostToDevice, st));
+  if (!launch) return PCP_OK;
   int64_t biggest = 1;
   for (int i = 0; i < count; ++i)
     biggest = std::max<int64_t>(biggest, (int64_t)tasks[i].mp * tasks[i].np);
@@ -274,12 +275,13 @@ pcp_status gather_batched_async(const GatherTask* tasks, int count,
 
 pcp_status assemble_batched_async(const AssembleTask* tasks, int count,
                                   void* h_buf, void* d_buf, cudaStream_t st,
-                                  bool upload) {
+                                  bool upload, bool launch) {
   if (count <= 0) return PCP_OK;
   std::memcpy(h_buf, tasks, sizeof(AssembleTask) * count);
   if (upload)
     PCP_CUDA(cudaMemcpyAsync(d_buf, h_buf, sizeof(AssembleTask) * count,
                              cudaMemcpyHostToDevice, st));
+  if (!launch) return PCP_OK;
   int64_t biggest = 1;
   for (int i = 0; i < count; ++i)
     biggest = std::max<int64_t>(
