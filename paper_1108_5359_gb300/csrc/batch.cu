@@ -159,7 +159,12 @@ pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi) {
   k0 = (k0 + 1) / 2 * 2;
   const int kcap = std::min(std::min(mp, np) / 2 * 2, 64);
   bi->k0 = std::min(k0, kcap);
-  bi->kmax = std::min(kcap, std::max(bi->k0 + 16, 2 * bi->k0) / 2 * 2);
+  // Room for one growth step of the subspace (k0 + max(8, k0 / 4)): a seed
+  // that passes Eq. rank_test keeps r' <= r < k0 values, and the batched
+  // seeds share one launch whose shared memory is sized by the largest
+  // kmax; at r = 30 this keeps it at ~78 KB (two CTAs per SM) instead of
+  // ~116 KB for kmax = 64 (one).
+  bi->kmax = std::min(kcap, (bi->k0 + std::max(8, bi->k0 / 4) + 1) / 2 * 2);
   bi->lam_seed = q.lambda_seed > 0
                      ? q.lambda_seed
                      : 1.0 / std::sqrt((double)std::max(mp, np));
