@@ -2309,13 +2309,18 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   std::vector<std::vector<int>> lists(nlist);
   for (int i : by_c)
     if (nb[i] == 1) lists[bin[i]].push_back(i);
-  int* lst = reinterpret_cast<int*>(tab + nblocks + nlist);
+  // only lists that hold a seed get a CTA: a small group (one served
+  // request) then occupies only the CTAs it uses, and the cooperative
+  // launch of another stream's group can be resident beside it
+  int nused = 0;
+  for (const auto& l : lists) nused += !l.empty();
+  int* lst = reinterpret_cast<int*>(tab + nblocks + nused);
   int off = 0;
-  for (int b = 0; b < nlist; ++b) {
-    tab[nblocks + b] = make_int4(off, 0, 1, (int)lists[b].size());
-    for (int i : lists[b]) lst[off++] = i;
+  for (const auto& l : lists) {
+    if (l.empty()) continue;
+    tab[nblocks++] = make_int4(off, 0, 1, (int)l.size());
+    for (int i : l) lst[off++] = i;
   }
-  nblocks += nlist;
   const size_t used_bytes = seed_args_bytes() * (size_t)count +
                             sizeof(int4) * (size_t)nblocks +
                             sizeof(int) * (size_t)off;
