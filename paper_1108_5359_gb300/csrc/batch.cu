@@ -43,6 +43,47 @@ std::vector<int64_t> sample(int64_t n, int64_t k, uint64_t seed) {
   return out;
 }
 
+// Index block of one instance, written on the device: the seed rows and
+// columns in their given order, then the other rows and columns in
+// ascending order.  src holds rows, cols and sorted copies of both; a
+// non-seed index i goes to position i - (number of seed indices below i).
+struct ComplementTask {
+  const int32_t* src;  // rows (mp), cols (np), sorted rows, sorted cols
+  int32_t* idx;        // rows, cols, rbar (m - mp), cbar (n - np)
+  int m, n, mp, np;
+};
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t* v, int len,
+                                               int x) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void complement_batched_kernel(
+    const ComplementTask* __restrict__ tasks) {
+  const ComplementTask t = tasks[blockIdx.y];
+  const int32_t* srows = t.src + t.mp + t.np;
+  const int32_t* scols = srows + t.mp;
+  int32_t* rbar = t.idx + t.mp + t.np;
+  int32_t* cbar = rbar + (t.m - t.mp);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < t.m + t.n;
+       e += gridDim.x * blockDim.x) {
+    if (e < t.mp + t.np) t.idx[e] = t.src[e];
+    if (e < t.m) {
+      const int c = lower_bound_i32(srows, t.mp, e);
+      if (c == t.mp || srows[c] != e) rbar[e - c] = e;
+    } else {
+      const int j = e - t.m;
+      const int c = lower_bound_i32(scols, t.np, j);
+      if (c == t.np || scols[c] != j) cbar[j - c] = j;
+    }
+  }
+}
+
 struct SummaryTask {
   const SeedCtl* ctl;
   const int32_t* iters;
@@ -194,6 +235,7 @@ size_t batch_footprint(const pcp_problem& pr, const BatchInstance& bi) {
   const int64_t nrb = q.m - bi.mp, ncb = q.n - bi.np;
   size_t b = 0;
   b += align256(sizeof(int32_t) * (q.m + q.n));                  // indices
+  b += sizeof(int32_t) * 2 * (bi.mp + bi.np) + 64;                // staged seeds
   b += align256(sizeof(double) * bi.mp * bi.np);                 // M^s
   b += align256(seed_workspace_bytes_cta(bi.mp, bi.np, bi.kmax));
   b += align256(sizeof(double) * (bi.mp + bi.np + 1) * bi.kmax); // U, S, V
@@ -227,12 +269,12 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
   std::vector<size_t> o_idx(count), o_Ms(count), o_work(count), o_U(count),
       o_Sig(count), o_V(count), o_U32(count), o_V32(count), o_isg(count),
       o_it(count);
-  int64_t idx_total = 0;
+  int64_t seed_total = 0;  // staged seed indices, 2 (m' + n') per instance
   for (int i = 0; i < count; ++i) {
     const pcp_params& q = probs[i].params;
     const BatchInstance& b = h->inst[i];
     o_idx[i] = take(sizeof(int32_t) * (q.m + q.n));
-    idx_total += q.m + q.n;
+    seed_total += 2 * (b.mp + b.np);
     o_Ms[i] = take(sizeof(double) * b.mp * b.np);
     o_work[i] = take(seed_workspace_bytes_cta(b.mp, b.np, b.kmax));
     o_U[i] = take(sizeof(double) * b.mp * b.kmax);
@@ -244,6 +286,8 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
     o_it[i] = take(sizeof(int32_t) * ((q.m - b.mp) + (q.n - b.np)));
   }
   const size_t o_bad = take(sizeof(int32_t) * count);
+  const size_t o_seeds = take(sizeof(int32_t) * (size_t)seed_total);
+  const size_t o_ctask = take(sizeof(ComplementTask) * count);
   const size_t o_sargs = take(seed_batched_args_bytes(count));
   const size_t o_gat = take(sizeof(GatherTask) * count);
   const size_t o_asm = take(sizeof(AssembleTask) * count);
@@ -272,9 +316,14 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
   }
   char* base = static_cast<char*>(h->d_base);
 
-  // ---- host staging: indices, then the argument blocks ----------------------
-  std::vector<int32_t> hidx((size_t)idx_total);
+  // ---- host staging: seed indices, then the argument blocks ---------------
+  // Only the seed rows and columns (and sorted copies) go to the device;
+  // complement_batched_kernel writes each instance's whole index block.
+  std::vector<int32_t> hseeds((size_t)seed_total);
+  h->h_ctask.resize(sizeof(ComplementTask) * count);
+  ComplementTask* ctask = reinterpret_cast<ComplementTask*>(h->h_ctask.data());
   int64_t pos = 0;
+  int64_t widest = 1;
   for (int i = 0; i < count; ++i) {
     const pcp_params& q = probs[i].params;
     BatchInstance& b = h->inst[i];
@@ -292,26 +341,32 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
                     : (q.col_order ? prefix(q.col_order, b.np)
                                    : sample(q.n, b.np,
                                             q.rng_seed ^ 0xC01C01C0ull));
-    b.rows = rows;
-    b.cols = cols;
-    std::vector<char> in_r(q.m, 0), in_c(q.n, 0);
-    int32_t* hp = hidx.data() + pos;
+    int32_t* hp = hseeds.data() + pos;
     int64_t o = 0;
-    for (int64_t v : rows) { hp[o++] = (int32_t)v; in_r[v] = 1; }
-    for (int64_t v : cols) { hp[o++] = (int32_t)v; in_c[v] = 1; }
-    for (int64_t v = 0; v < q.m; ++v) if (!in_r[v]) hp[o++] = (int32_t)v;
-    for (int64_t v = 0; v < q.n; ++v) if (!in_c[v]) hp[o++] = (int32_t)v;
-    pos += q.m + q.n;
+    for (int64_t v : rows) hp[o++] = (int32_t)v;
+    for (int64_t v : cols) hp[o++] = (int32_t)v;
+    std::vector<int64_t> srt(rows);
+    std::sort(srt.begin(), srt.end());
+    for (int64_t v : srt) hp[o++] = (int32_t)v;
+    srt.assign(cols.begin(), cols.end());
+    std::sort(srt.begin(), srt.end());
+    for (int64_t v : srt) hp[o++] = (int32_t)v;
+    b.rows = std::move(rows);
+    b.cols = std::move(cols);
+    ctask[i] = ComplementTask{
+        reinterpret_cast<const int32_t*>(base + o_seeds) + pos,
+        reinterpret_cast<int32_t*>(base + o_idx[i]), (int)q.m, (int)q.n, b.mp,
+        b.np};
+    widest = std::max<int64_t>(widest, q.m + q.n);
+    pos += o;
   }
-  // indices are contiguous per instance; each instance's block is 256-byte
-  // aligned, so copy instance by instance
-  pos = 0;
-  for (int i = 0; i < count && !h->indices_ready; ++i) {
-    const pcp_params& q = probs[i].params;
-    PCP_CUDA(cudaMemcpyAsync(base + o_idx[i], hidx.data() + pos,
-                             sizeof(int32_t) * (q.m + q.n),
+  if (!h->indices_ready) {
+    PCP_CUDA(cudaMemcpyAsync(base + o_seeds, hseeds.data(),
+                             sizeof(int32_t) * (size_t)seed_total,
                              cudaMemcpyHostToDevice, st));
-    pos += q.m + q.n;
+    PCP_CUDA(cudaMemcpyAsync(base + o_ctask, ctask,
+                             sizeof(ComplementTask) * count,
+                             cudaMemcpyHostToDevice, st));
   }
   PCP_CUDA(cudaMemsetAsync(base + o_bad, 0, sizeof(int32_t) * count, st));
 
@@ -417,6 +472,12 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
     PCP_CUDA(cudaEventRecord(h->ev[0], st));
   }
   NvtxStages nvtx("pcp.batch.seed");
+  if (!h->indices_ready) {
+    const int bx = (int)std::min<int64_t>((widest + 255) / 256, 64);
+    complement_batched_kernel<<<dim3(bx, count), 256, 0, st>>>(
+        reinterpret_cast<const ComplementTask*>(base + o_ctask));
+    PCP_CUDA(cudaGetLastError());
+  }
   if ((s = gather_batched_async(gat.data(), count, h->h_gat.data(),
                                 base + o_gat, st, false)) != PCP_OK)
     return s;

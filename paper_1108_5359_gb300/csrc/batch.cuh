@@ -33,7 +33,7 @@ struct BatchHandle {
   std::vector<pcp_problem> probs;
   void* d_base = nullptr;  // one stream-ordered allocation
   size_t bytes = 0;
-  std::vector<char> h_gat, h_asm, h_sargs, h_filt, h_stask;
+  std::vector<char> h_gat, h_asm, h_sargs, h_filt, h_stask, h_ctask;
   BatchSummary* d_summary = nullptr;
   // stage boundaries (start, seed done, filters done, S pass done) when
   // the launch is timed
