@@ -268,10 +268,16 @@ def relerr(a, b):
 # oracle timing (cpu_baseline and the reference arm)
 # -------------------------------------------------------------------------
 
-def oracle_solve(P, M32):
-    """One full FP64 oracle solve (Algorithm 2) of the workload; returns
-    (seconds, result)."""
+def oracle_solve(P, M32, fp32=False):
+    """One full oracle solve (Algorithm 2) of the workload; returns
+    (seconds, result).  fp32: the plain-FP32 variant (the same steps in
+    FP32 arithmetic, Algorithm 1's eps at 1e-6, which FP32 resolves)."""
     from oracle import l1filter
+    if fp32:
+        t0 = time.perf_counter()
+        res = l1filter.l1_filter_pcp(M32, P.rows, P.cols, r=P.r,
+                                     adm_kw=dict(eps=1e-6), dtype=np.float32)
+        return time.perf_counter() - t0, res
     M = M32.astype(np.float64)
     t0 = time.perf_counter()
     res = l1filter.l1_filter_pcp(M, P.rows, P.cols, r=P.r)
@@ -559,6 +565,21 @@ def report(pk, rec, rank=0):
             if rec["Lrec"] is not None:
                 parity["relerr_L_vs_oracle"] = relerr(rec["Lrec"], ref.L)
                 parity["relerr_S_vs_oracle"] = relerr(rec["Sh"], ref.S)
+            # the plain-FP32 NumPy variant, timed the same way
+            ts32, r32 = [], None
+            for _ in range(3):
+                t, r32 = oracle_solve(P, M32, fp32=True)
+                ts32.append(t)
+            cpu["fp32_variant"] = {
+                "value": mn / statistics.median(ts32), "unit": "entries/s",
+                "seconds": ts32,
+                "what": "the oracle's steps in FP32 (numpy float32), "
+                        "Algorithm 1 eps 1e-6; median of 3 full solves"}
+            if rec["Lrec"] is not None:
+                parity["relerr_L_vs_fp32_variant"] = relerr(
+                    rec["Lrec"], r32.L.astype(np.float64))
+                parity["relerr_L_fp32_variant_vs_oracle"] = relerr(
+                    r32.L.astype(np.float64), ref.L)
         else:
             frac = mode
             t_seed, t_rest = oracle_sample(P, M32, frac)

@@ -1,4 +1,6 @@
-"""Algorithm 1 (ADM for l1 regression) and Algorithm 2 (l1 filtering), FP64.
+"""Algorithm 1 (ADM for l1 regression) and Algorithm 2 (l1 filtering), FP64
+(the same steps in FP32 through ``dtype``: the plain-FP32 variant timed
+beside the oracle as a CPU baseline).
 
 Test infrastructure only (see ``oracle/__init__``).
 
@@ -55,23 +57,25 @@ class ADMResult:
 
 
 def adm_l1(X, A, eps=ADM_EPS, rho=ADM_RHO, beta0_scale=ADM_BETA0_SCALE,
-           beta_bar_ratio=ADM_BETA_BAR_RATIO, max_iter=ADM_MAX_ITER):
+           beta_bar_ratio=ADM_BETA_BAR_RATIO, max_iter=ADM_MAX_ITER,
+           dtype=np.float64):
     """Algorithm 1 on every column of X (p x N) with basis A (p x r).
 
     A must have orthonormal columns (A^T A = I), which is what lets step 2 be
-    a plain product with A^T.
+    a plain product with A^T.  ``dtype``: FP64 (the oracle) or FP32 (the
+    plain-FP32 variant, which needs an eps above FP32 resolution).
     """
-    X = np.asarray(X, dtype=np.float64)
-    A = np.asarray(A, dtype=np.float64)
+    X = np.asarray(X, dtype=dtype)
+    A = np.asarray(A, dtype=dtype)
     if X.ndim == 1:
         X = X[:, None]
     p, N = X.shape
     r = A.shape[1]
-    xinf = np.abs(X).max(axis=0) if p > 0 else np.zeros(N)
-    Z = np.zeros((r, N))
-    E = np.zeros((p, N))
-    Y = np.zeros((p, N))
-    AZ = np.zeros((p, N))
+    xinf = np.abs(X).max(axis=0) if p > 0 else np.zeros(N, dtype)
+    Z = np.zeros((r, N), dtype)
+    E = np.zeros((p, N), dtype)
+    Y = np.zeros((p, N), dtype)
+    AZ = np.zeros((p, N), dtype)
     active = xinf > 0
     safe = np.where(active, xinf, 1.0)
     beta = beta0_scale / safe
@@ -80,7 +84,8 @@ def adm_l1(X, A, eps=ADM_EPS, rho=ADM_RHO, beta0_scale=ADM_BETA0_SCALE,
     converged = ~active.copy()
     for _ in range(max_iter + 1):
         # loop condition: ||X - A Z_k - E_k||_inf / ||X||_inf >= eps
-        rel = np.abs(X - AZ - E).max(axis=0) / safe if p > 0 else np.zeros(N)
+        rel = (np.abs(X - AZ - E).max(axis=0) / safe if p > 0
+               else np.zeros(N, dtype))
         done = active & (rel < eps)
         converged |= done
         active &= ~done
@@ -91,7 +96,7 @@ def adm_l1(X, A, eps=ADM_EPS, rho=ADM_RHO, beta0_scale=ADM_BETA0_SCALE,
         c = active
         Xc, Yc, b = X[:, c], Y[:, c], beta[c]
         # Step 1
-        Ec = soft_threshold(Xc - AZ[:, c] + Yc / b, 1.0 / b)
+        Ec = soft_threshold(Xc - AZ[:, c] + Yc / b, 1.0 / b, dtype)
         # Step 2
         Zc = A.T @ (Xc - Ec + Yc / b)
         # Step 3
@@ -118,7 +123,7 @@ def rank_test(mp, np_, r_est, s_r=10.0, s_c=10.0):
     return (mp / r_est >= s_r) and (np_ / r_est >= s_c)
 
 
-def nystrom_factors(m, n, rows, cols, U, sigma, V, Pt, Qt):
+def nystrom_factors(m, n, rows, cols, U, sigma, V, Pt, Qt, dtype=np.float64):
     """Factors of L = Lu diag(W) Lv^T (Eq. l1s', Algorithm 2 step 5).
 
     Lu[I_s] = U^s Sigma^s, Lu[~I_s] = P~^T; Lv[J_s] = V^s Sigma^s,
@@ -128,8 +133,8 @@ def nystrom_factors(m, n, rows, cols, U, sigma, V, Pt, Qt):
     r = sigma.size
     rbar = np.setdiff1d(np.arange(m), rows)
     cbar = np.setdiff1d(np.arange(n), cols)
-    Lu = np.zeros((m, r))
-    Lv = np.zeros((n, r))
+    Lu = np.zeros((m, r), dtype)
+    Lv = np.zeros((n, r), dtype)
     Lu[rows] = U * sigma
     Lu[rbar] = Pt.T
     Lv[cols] = V * sigma
@@ -161,7 +166,7 @@ class L1FilterResult:
 
 def l1_filter_pcp(M, rows, cols, r=None, seed_tol=1e-7, lam_seed=None,
                   s_r=10.0, s_c=10.0, rank_cut=1e-6, adm_kw=None,
-                  seed_kw=None, form_L=True):
+                  seed_kw=None, form_L=True, dtype=np.float64):
     """Algorithm 2 on M (m x n) with seed rows I_s = rows, columns J_s = cols.
 
     ``r`` caps the rank kept from the seed (the target rank); None keeps the
@@ -170,8 +175,11 @@ def l1_filter_pcp(M, rows, cols, r=None, seed_tol=1e-7, lam_seed=None,
     only to about 1e-7 of its norm; components below 1e-6 of the largest are
     treated as zero (with a 1e-10 cut, two equally converged ALM iterates
     of a borderline seed can disagree on the rank).
+
+    ``dtype``: FP64 (the oracle) or FP32 (the plain-FP32 variant: the same
+    steps in FP32 arithmetic; pass adm_kw eps >= 1e-6, which FP32 resolves).
     """
-    M = np.asarray(M, dtype=np.float64)
+    M = np.asarray(M, dtype=dtype)
     m, n = M.shape
     rows = np.asarray(rows, dtype=np.int64)
     cols = np.asarray(cols, dtype=np.int64)
@@ -182,7 +190,7 @@ def l1_filter_pcp(M, rows, cols, r=None, seed_tol=1e-7, lam_seed=None,
     Ms = M[np.ix_(rows, cols)]
     if lam_seed is None:
         lam_seed = 1.0 / math.sqrt(max(mp, np_))
-    seed = inexact_alm_pcp(Ms, lam_seed, tol=seed_tol, **seed_kw)
+    seed = inexact_alm_pcp(Ms, lam_seed, tol=seed_tol, dtype=dtype, **seed_kw)
     rk_raw = numerical_rank(seed.sigma, rank_cut)
     rk = rk_raw if r is None else min(rk_raw, int(r))
     order = np.argsort(-seed.sigma)[:rk]
@@ -194,11 +202,12 @@ def l1_filter_pcp(M, rows, cols, r=None, seed_tol=1e-7, lam_seed=None,
     rbar = np.setdiff1d(np.arange(m), rows)
     cbar = np.setdiff1d(np.arange(n), cols)
     # step 3: column filtering, M^c = U^s Q~ + S^c (Eq. l1c')
-    col = adm_l1(M[np.ix_(rows, cbar)], U, **adm_kw)
+    col = adm_l1(M[np.ix_(rows, cbar)], U, dtype=dtype, **adm_kw)
     # step 4: row filtering, (M^r)^T = V^s P~ + (S^r)^T (Eq. l1r')
-    row = adm_l1(M[np.ix_(rbar, cols)].T, V, **adm_kw)
+    row = adm_l1(M[np.ix_(rbar, cols)].T, V, dtype=dtype, **adm_kw)
     # step 5: Nystrom representation (Eq. l1s')
-    Lu, Lv, W = nystrom_factors(m, n, rows, cols, U, sigma, V, row.Z, col.Z)
+    Lu, Lv, W = nystrom_factors(m, n, rows, cols, U, sigma, V, row.Z, col.Z,
+                                dtype)
     if form_L:
         L = (Lu * W) @ Lv.T
         S = M - L

@@ -1,4 +1,5 @@
-"""Soft shrinkage, singular value thresholding and inexact-ALM PCP (FP64).
+"""Soft shrinkage, singular value thresholding and inexact-ALM PCP (FP64;
+the same steps in FP32 through ``dtype`` for the plain-FP32 variant).
 
 Test infrastructure only (see ``oracle/__init__``).
 
@@ -25,24 +26,25 @@ import numpy as np
 __all__ = ["soft_threshold", "svt", "inexact_alm_pcp", "PCPResult"]
 
 
-def soft_threshold(x, eta):
+def soft_threshold(x, eta, dtype=np.float64):
     """S_eta(x) = sgn(x) * max(|x| - eta, 0), elementwise (Section 2).
 
     ``eta`` may be a scalar or broadcast against ``x``; sgn(0) = 0 so
-    S_eta(0) = 0.
+    S_eta(0) = 0.  ``dtype``: the arithmetic (FP64; FP32 for the plain-FP32
+    variant).
     """
-    x = np.asarray(x, dtype=np.float64)
+    x = np.asarray(x, dtype=dtype)
     return np.sign(x) * np.maximum(np.abs(x) - eta, 0.0)
 
 
-def svt(W, eta):
+def svt(W, eta, dtype=np.float64):
     """Singular value thresholding (Eq. SVT).
 
     Returns (A, U_+, s_+, Vt_+) with A = U S_eta(Sigma) V^T computed from a full
     LAPACK SVD of W, and the skinny factors of A restricted to the singular
     values that survive (sigma_i > eta), s_+ = sigma_i - eta.
     """
-    U, s, Vt = np.linalg.svd(np.asarray(W, dtype=np.float64),
+    U, s, Vt = np.linalg.svd(np.asarray(W, dtype=dtype),
                              full_matrices=False)
     keep = s > eta
     s_shr = s[keep] - eta
@@ -65,7 +67,7 @@ class PCPResult:
 
 
 def inexact_alm_pcp(D, lam, tol=1e-7, rho=1.5, mu_scale=1.25,
-                    mu_max_ratio=1e7, max_iter=1000):
+                    mu_max_ratio=1e7, max_iter=1000, dtype=np.float64):
     """Solve min ||L||_* + lam ||S||_1 s.t. D = L + S by inexact ALM.
 
     Steps per iteration k (the ADM of the cited solver, in the paper's
@@ -79,13 +81,17 @@ def inexact_alm_pcp(D, lam, tol=1e-7, rho=1.5, mu_scale=1.25,
     with S_0 = 0, Y_0 = D / max(||D||_2, ||D||_inf / lam),
     mu_0 = mu_scale / ||D||_2, mu_max = mu_max_ratio * mu_0, and stop when
     ||D - L - S||_F / ||D||_F <= tol.
+
+    ``dtype`` sets the arithmetic: FP64 (the oracle), or FP32 for the
+    plain-FP32 variant (same steps and constants).
     """
-    D = np.asarray(D, dtype=np.float64)
+    D = np.asarray(D, dtype=dtype)
     normF = np.linalg.norm(D, "fro")
     if normF == 0.0:
         z = np.zeros_like(D)
-        return PCPResult(z, z.copy(), np.zeros((D.shape[0], 0)),
-                         np.zeros(0), np.zeros((D.shape[1], 0)), 0, 0.0, True)
+        return PCPResult(z, z.copy(), np.zeros((D.shape[0], 0), dtype),
+                         np.zeros(0, dtype), np.zeros((D.shape[1], 0), dtype),
+                         0, 0.0, True)
     norm2 = np.linalg.norm(D, 2)
     norminf = np.abs(D).max() / lam
     Y = D / max(norm2, norminf)
@@ -93,16 +99,16 @@ def inexact_alm_pcp(D, lam, tol=1e-7, rho=1.5, mu_scale=1.25,
     mu_max = mu * mu_max_ratio
     S = np.zeros_like(D)
     L = np.zeros_like(D)
-    U = np.zeros((D.shape[0], 0))
-    s = np.zeros(0)
-    Vt = np.zeros((0, D.shape[1]))
+    U = np.zeros((D.shape[0], 0), dtype)
+    s = np.zeros(0, dtype)
+    Vt = np.zeros((0, D.shape[1]), dtype)
     it = 0
     res = 1.0
     converged = False
     while it < max_iter:
         it += 1
-        L, U, s, Vt = svt(D - S + Y / mu, 1.0 / mu)
-        S = soft_threshold(D - L + Y / mu, lam / mu)
+        L, U, s, Vt = svt(D - S + Y / mu, 1.0 / mu, dtype)
+        S = soft_threshold(D - L + Y / mu, lam / mu, dtype)
         Z = D - L - S
         Y = Y + mu * Z
         mu = min(rho * mu, mu_max)
