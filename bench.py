@@ -14,15 +14,20 @@ e2e          the same metric through the public API from pinned host
              memory: H2D of M, the solve, D2H of Lu, Lv and S per step;
 roofline     the dominant kernel of the step against MEASURED_PEAKS.json;
 cpu_baseline the FP64 oracle on the host cores (rank 0, N=1 only): the
-             median of three full solves of the same workload;
+             median of three full solves of the same workload, and the
+             plain-FP32 variant of the oracle timed the same way;
 gpu_launches the library's own kernel launches in the timed steps, as the
              library counts them (pcp_info.launches);
 large        (N=1) the same record for the 20000 x 20000 rank-50 solve in
              the BF16 + refinement form, its CPU baseline a stated sample;
-batch        (N=1) 64 uneven instances through pcp_l1filter_batch against
-             one pcp_l1filter_solve per instance, p50 / p99, and the same
-             batch replayed as a captured graph (pcp_l1filter_batch_plan /
-             pcp_l1filter_batch_run);
+batch        (N=1) 256 uneven instances (r up to 30, BF16 + refinement)
+             through pcp_l1filter_batch against one pcp_l1filter_solve per
+             instance, p50 / p99, and the same batch replayed as a captured
+             graph (pcp_l1filter_batch_plan / pcp_l1filter_batch_run);
+serve        (N=1) 256 video-like requests (76800 x U[200, 1000], rank
+             1-5) arriving at 50 / s (Poisson) and as a burst, the server
+             against one solve at a time: throughput, p50 / p99, and the
+             error against L0 / S0 per request kind;
 --impl reference  the oracle as the reference arm: one full FP64 oracle
              solve per step, nothing sampled or scaled.
 Multi-GPU: independent replicas (each rank solves its own instance; weak
@@ -85,7 +90,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the extra records of the default line (the "
-                         "20000^2 solve and the batched form)")
+                         "20000^2 solve, the batched form, the served "
+                         "video stream)")
     ap.add_argument("--small", action="store_true",
                     help="500x500 rank-5 workload (profiling / smoke)")
     ap.add_argument("--workload", choices=["single", "large", "batch",
@@ -637,7 +643,8 @@ def run_ours(args):
     del rec
     subs = {}
     # extra records on one GPU: the largest single-GPU configuration in its
-    # own precision form, and the batched form against per-instance solves
+    # own precision form, the batched form against per-instance solves, and
+    # the served video stream against one solve at a time
     if ws == 1 and not args.no_sub and not args.small and not large:
         P3, M3 = make_problem(args.seed, large=True)
         rec3 = measure_single(pk, torch, dev, P3, M3, LARGE, "bf16",
@@ -655,6 +662,7 @@ def run_ours(args):
         subs["batch"] = batch_record(pk, torch, dev, count=256, steps=3,
                                      warmup=3, seed=args.seed, r_max=30,
                                      precision="bf16")
+        subs["serve"] = serve_record(pk, torch, 256, 50.0, args.seed)
     if rank == 0:
         out = {"metric": METRIC, "value": body.pop("value"),
                "unit": body.pop("unit"), "n_gpus": ws,
@@ -867,16 +875,27 @@ def run_batch(args):
 
 
 def run_serve(args):
+    import torch
+    import paper_1108_5359_gb300 as pk
+    from paper_1108_5359_gb300 import build as pkbuild
+    pkbuild.build()
+    pk.load()
+    out = serve_record(pk, torch, args.count, args.rate, args.seed)
+    print(json.dumps(out), flush=True)
+
+
+def serve_record(pk, torch, n_requests, rate, seed):
     """Poisson arrivals of video-like solves (m = 320*240 frames, n ~
     U[200,1000], rank 1-5): the server (continuous batching) against one
     solve at a time in arrival order; latency = arrival to result on the
-    host."""
+    host.  Returns the record."""
     import threading
-    import torch
-    import paper_1108_5359_gb300 as pk
-    from paper_1108_5359_gb300 import build as pkbuild, synth
-    pkbuild.build()
-    pk.load()
+    from paper_1108_5359_gb300 import synth
+
+    class _A:  # the settings the body reads
+        pass
+    args = _A()
+    args.seed, args.count, args.rate = seed, n_requests, rate
     rng = np.random.default_rng(args.seed)
     kinds = 6
     t0 = time.perf_counter()
@@ -1050,7 +1069,11 @@ def run_serve(args):
         "results": res,
         "accuracy_per_kind": accuracy,
     }
-    print(json.dumps(out), flush=True)
+    for dM in dMs:
+        del dM
+    del out_sets, dMs
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
