@@ -414,15 +414,18 @@ __device__ void gram(const double* X, int nrows, int k, int kmax,
 // is kept, and the broadcasts of a step overlap the next step's pivot
 // chain.  A non-positive pivot (or a dead column) gives R_jj = 1 and a
 // zero row, and marks the column dead.  R (upper triangle and diagonal) is
-// written back to A32; the lower triangle is left as it was.
-template <int K>
-__device__ __noinline__ void chol_warp(float* A32, int k, int* dead) {
+// written back to A; the lower triangle is left as it was.  A: the block's
+// first entry, row stride lda; rs_out (optional): the reciprocal pivots
+// rs_j the rows were scaled by.
+template <int K, bool kRs>
+__device__ __noinline__ void chol_warp(float* A, int lda, int k, int* dead,
+                                       float* rs_out) {
   const int lane = threadIdx.x & 31;
   const bool own = lane < k;
   float a[K];
 #pragma unroll
   for (int r = 0; r < K; ++r)
-    a[r] = (own && r < k) ? A32[r * k + lane] : 0.0f;
+    a[r] = (own && r < k) ? A[r * lda + lane] : 0.0f;
   int dl = own ? dead[lane] : 1;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
@@ -434,6 +437,7 @@ __device__ __noinline__ void chol_warp(float* A32, int k, int* dead) {
     if (lane == j) {
       rj = bad ? 1.0f : piv * rs;
       if (bad) dl = 1;
+      if (kRs && j < k) rs_out[j] = rs;
     }
     if (lane >= j) a[j] = rj;
     const float rju = lane > j ? rj : 0.0f;  // columns <= j are final
@@ -445,8 +449,67 @@ __device__ __noinline__ void chol_warp(float* A32, int k, int* dead) {
   }
 #pragma unroll
   for (int r = 0; r < K; ++r)
-    if (own && r < k && r <= lane) A32[r * k + lane] = a[r];
+    if (own && r < k && r <= lane) A[r * lda + lane] = a[r];
   if (own) dead[lane] = dl;
+}
+
+// The same factorisation for 32 < k <= 64 in four steps, each entry taking
+// the same operations in the same order as the right-looking CTA-wide form
+// (so the same bits): one warp factors the leading 32 x 32 block (keeping
+// its reciprocal pivots in rs); a thread per column c >= 32 forms rows
+// 0..31 of R in turn, R_jc = (A_jc - sum_{i<j} R_ij R_ic) rs_j with the
+// terms in i order; the trailing block takes its 32 updates A_rc -=
+// R_ir R_ic in i order (upper triangle); one warp factors it.
+static_assert(kSeedKmaxLimit <= 64, "the Cholesky forms cover k <= 64");
+__device__ __noinline__ void chol_blocked64(float* A32, int k, int* dead,
+                                            float* rs) {
+  const int tid = threadIdx.x;
+  if (tid < 32) chol_warp<32, true>(A32, k, 32, dead, rs);
+  __syncthreads();
+  {
+    // rows 0..31 of columns c >= 32, right-looking in registers: warp w
+    // takes columns 32 + w + 8 q (q < 4), lane j holds row j of each; at
+    // step i lane i finalises R_ic = a_ic rs_i and broadcasts it, and every
+    // lane j > i takes its update a_jc -= R_ij R_ic (four independent
+    // chains per warp)
+    const int lane = tid & 31, w = tid >> 5;
+    constexpr int kQ = 4;
+    float v[kQ];
+    int cq[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+      cq[q] = 32 + w + (kSeedThreads / 32) * q;
+      v[q] = cq[q] < k ? A32[lane * k + cq[q]] : 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const float rsi = rs[i];
+      const float rij = lane > i ? A32[i * k + lane] : 0.0f;
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        if (lane == i) v[q] *= rsi;
+        const float ric = __shfl_sync(0xffffffffu, v[q], i);
+        if (lane > i) v[q] = fmaf(-rij, ric, v[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; ++q)
+      if (cq[q] < k) A32[lane * k + cq[q]] = v[q];
+  }
+  __syncthreads();
+  const int k2 = k - 32;
+  for (int idx = tid; idx < k2 * k2; idx += kSeedThreads) {
+    const int r = 32 + idx / k2, c = 32 + idx % k2;
+    if (c < r) continue;
+    float acc = A32[r * k + c];
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i)
+      acc = fmaf(-A32[i * k + r], A32[i * k + c], acc);
+    A32[r * k + c] = acc;
+  }
+  __syncthreads();
+  if (tid < 32)
+    chol_warp<32, false>(A32 + 32 * k + 32, k, k2, dead + 32, nullptr);
 }
 
 // Column-normalised Cholesky QR: Out = X diag(1/||x_a||) R^{-1} with
@@ -494,51 +557,20 @@ __device__ void cholqr_apply(const double* X, int nrows, int k, int kmax,
   // the k sequential pivot steps are skipped.
   const bool near_orth = !__syncthreads_or(coupled);
   long long q1 = prof ? clock64() : 0;
-  // Right-looking Cholesky, R in the upper triangle, one CTA barrier per
-  // step: at the start of step j row j is final (R_j. = a_j. / sqrt(a_jj));
-  // warp 0 updates row j+1 with it, takes that row's pivot and scales it
-  // (warp-synchronous), while warps 1.. update rows j+2.. (a_ab -= R_ja R_jb,
-  // b >= a).  A non-positive pivot marks the column dead (R_jj = 1, rest of
-  // the row 0).
-  if (!near_orth && k <= 32) {
-    if (tid < 32) {
-      if (k <= 16)
-        chol_warp<16>(A32, k, dead);
-      else
-        chol_warp<32>(A32, k, dead);
-    }
-  } else if (!near_orth) {
-    const int lane = tid & 31, w = tid >> 5;
-    auto finish_row = [&](int r) {  // warp 0: pivot and scaling of row r
-      const float piv = A32[r * k + r];
-      const bool bad = !(piv > 1e-6f) || dead[r];
-      const float rs = bad ? 0.0f : rsqrtf(piv);
-      for (int c = r + 1 + lane; c < k; c += 32) A32[r * k + c] *= rs;
-      __syncwarp();
-      if (lane == 0) {
-        A32[r * k + r] = bad ? 1.0f : piv * rs;
-        if (bad) dead[r] = 1;
+  // Right-looking Cholesky, R in the upper triangle (a non-positive pivot
+  // marks the column dead: R_jj = 1, rest of the row 0): one warp in
+  // registers for k <= 32, the blocked form above it (k <= 64, the
+  // subspace limit).
+  if (!near_orth) {
+    if (k <= 32) {
+      if (tid < 32) {
+        if (k <= 16)
+          chol_warp<16, false>(A32, k, k, dead, nullptr);
+        else
+          chol_warp<32, false>(A32, k, k, dead, nullptr);
       }
-    };
-    if (w == 0) finish_row(0);
-    for (int j = 0; j + 1 < k; ++j) {
-      __syncthreads();
-      if (w == 0) {
-        const int r = j + 1;
-        const float rjr = A32[j * k + r];
-        for (int c = r + lane; c < k; c += 32)
-          A32[r * k + c] -= rjr * A32[j * k + c];
-        __syncwarp();
-        finish_row(r);
-      } else {
-        const int t = tid - 32;  // 0 .. kSeedThreads - 33
-        constexpr int kRows = (kSeedThreads - 32) / 16;
-        for (int a = j + 2 + (t >> 4); a < k; a += kRows) {
-          const float rja = A32[j * k + a];
-          for (int c = a + (t & 15); c < k; c += 16)
-            A32[a * k + c] -= rja * A32[j * k + c];
-        }
-      }
+    } else {
+      chol_blocked64(A32, k, dead, Ri32);
     }
   }
   __syncthreads();
