@@ -891,15 +891,10 @@ def serve_record(pk, torch, n_requests, rate, seed):
     host.  Returns the record."""
     import threading
     from paper_1108_5359_gb300 import synth
-
-    class _A:  # the settings the body reads
-        pass
-    args = _A()
-    args.seed, args.count, args.rate = seed, n_requests, rate
-    rng = np.random.default_rng(args.seed)
+    rng = np.random.default_rng(seed)
     kinds = 6
     t0 = time.perf_counter()
-    Ps = [synth.video_like(int(rng.integers(200, 1001)), seed=args.seed + k)
+    Ps = [synth.video_like(int(rng.integers(200, 1001)), seed=seed + k)
           for k in range(kinds)]
     t_gen = time.perf_counter() - t0
     dev = torch.device("cuda", 0)
@@ -908,9 +903,9 @@ def serve_record(pk, torch, n_requests, rate, seed):
         dM = pk.colmajor(P.m, P.n, device=dev)
         dM.copy_(torch.from_numpy(P.M.astype(np.float32)))
         dMs.append(dM)
-    n_req = args.count
+    n_req = n_requests
     kind = [int(k) for k in rng.integers(0, kinds, size=n_req)]
-    gaps = rng.exponential(1.0 / args.rate, size=n_req)
+    gaps = rng.exponential(1.0 / rate, size=n_req)
     arrive = np.cumsum(gaps) - gaps[0]
     slots = 16
     mx = max(P.n for P in Ps)
@@ -927,7 +922,7 @@ def serve_record(pk, torch, n_requests, rate, seed):
         return (fu[:P.m * P.r].view(P.r, P.m).t(),
                 fv[:P.n * P.r].view(P.r, P.n).t(), S[:, :P.n])
 
-    orders = [synth.seed_orders(P.m, P.n, P.rows, P.cols, seed=args.seed)
+    orders = [synth.seed_orders(P.m, P.n, P.rows, P.cols, seed=seed)
               for P in Ps]
 
     def params_of(P):
@@ -1058,7 +1053,7 @@ def serve_record(pk, torch, n_requests, rate, seed):
     out = {
         "metric": METRIC, "workload": "serve",
         "value": res["burst"]["served"]["entries_per_s"], "unit": "entries/s",
-        "n_gpus": 1, "requests": n_req, "rate_req_s": args.rate,
+        "n_gpus": 1, "requests": n_req, "rate_req_s": rate,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "video_like_76800xU[200,1000]_r1-5",
                    "kinds": [{"n": P.n, "r": P.r} for P in Ps],
