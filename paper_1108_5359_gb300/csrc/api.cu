@@ -126,6 +126,9 @@ struct pcp_plan {
   std::vector<int64_t> given_rows, given_cols;
   std::vector<int64_t> row_order, col_order;  // seeds by order (prefixes)
   pcp_plan* child = nullptr;                   // grown seed (Section 3.5)
+  // the last solve on this plan stopped after the seed (a failed rank test
+  // checked before the filters), so its outputs were not written
+  bool stopped_after_seed = false;
   int64_t m, n;
   int r, mp, np, kmax, k0;
   double lam_seed, lam_full;
@@ -469,7 +472,8 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
                              float* dLu, float* dLv, float* dS, int64_t lds,
                              int64_t* h_seed_rows_out,
                              int64_t* h_seed_cols_out, pcp_info* info,
-                             void* stream, const HostIO* hio = nullptr);
+                             void* stream, const HostIO* hio = nullptr,
+                             bool rank_first = false);
 
 static pcp_status grow_loop(pcp_plan* P, const float* dM, int64_t ldm,
                             float* dLu, float* dLv, float* dS, int64_t lds,
@@ -557,7 +561,8 @@ extern "C" pcp_status pcp_l1filter_solve(pcp_plan* P, const float* dM,
         });
   }
   pcp_status st = solve_once(P, dM, ldm, dLu, dLv, dS, lds, h_seed_rows_out,
-                             h_seed_cols_out, info, stream);
+                             h_seed_cols_out, info, stream, nullptr,
+                             P && P->p.grow_seed);
   return grow_loop(P, dM, ldm, dLu, dLv, dS, lds, h_seed_rows_out,
                    h_seed_cols_out, info, stream, st);
 }
@@ -572,7 +577,7 @@ static pcp_status grow_loop(pcp_plan* P, const float* dM, int64_t ldm,
   // (s_r r') x (s_c r') (prefixes of the same orders) and the solve repeats,
   // until the test holds or the seed would pass half of a side.
   const pcp_params& q = P->p;
-  const pcp_plan* cur = P;
+  pcp_plan* cur = P;
   while (st == PCP_ERR_RANK_TEST) {
     const int rr = info->seed_rank_raw;
     const int gm = std::max(cur->mp, (int)std::llround(q.s_r * rr));
@@ -595,8 +600,16 @@ static pcp_status grow_loop(pcp_plan* P, const float* dM, int64_t ldm,
     cur = P->child;
     P->child->launches = P->launches;  // info->launches counts every attempt
     st = solve_once(P->child, dM, ldm, dLu, dLv, dS, lds, h_seed_rows_out,
-                    h_seed_cols_out, info, stream);
+                    h_seed_cols_out, info, stream, nullptr, true);
     P->launches = P->child->launches;
+  }
+  if (st == PCP_ERR_RANK_TEST && cur->stopped_after_seed) {
+    // growth gave up: the last seed's solve runs in full, so that the
+    // outputs are written as without growth
+    cur->launches = P->launches;
+    st = solve_once(cur, dM, ldm, dLu, dLv, dS, lds, h_seed_rows_out,
+                    h_seed_cols_out, info, stream, nullptr, false);
+    P->launches = cur->launches;
   }
   return st;
 }
@@ -676,7 +689,8 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
                              float* dLu, float* dLv, float* dS, int64_t lds,
                              int64_t* h_seed_rows_out,
                              int64_t* h_seed_cols_out, pcp_info* info,
-                             void* stream, const HostIO* hio) {
+                             void* stream, const HostIO* hio,
+                             bool rank_first) {
   PCP_ARG(P, "pcp_l1filter_solve: null plan");
   PCP_ARG(dM && dLu && dLv, "pcp_l1filter_solve: null pointer");
   PCP_ARG(ldm >= P->m, "pcp_l1filter_solve: ldm < m");
@@ -735,6 +749,45 @@ static pcp_status solve_once(pcp_plan* P, const float* dM, int64_t ldm,
   if (s != PCP_OK) return s;
   ++P->launches;
   if (timed) PCP_CUDA(cudaEventRecord(P->ev[1], st));
+  P->stopped_after_seed = false;
+  if (rank_first && timed && !hio) {
+    // Section 3.5 with seed growth on: the seed's rank decides whether this
+    // seed is kept, so it is read now and a seed that fails Eq. rank_test
+    // (and will grow) does not pay for the filters and the S pass
+    int rank = 0, iters = 0, conv = 0, err = 0, rank_raw = 0;
+    double resid = 0;
+    s = pcp::seed_read_ctl(P->d_seed_work, P->mp, P->np, P->kmax, st, &rank,
+                           &iters, &resid, &conv, &err, &rank_raw);
+    if (s != PCP_OK) return s;
+    int32_t bad = 0;
+    PCP_CUDA(cudaMemcpy(&bad, P->d_bad, sizeof(int32_t),
+                        cudaMemcpyDeviceToHost));
+    const bool ok = rank_raw >= 1 &&
+                    (double)P->mp / rank_raw >= q.s_r - 1e-9 &&
+                    (double)P->np / rank_raw >= q.s_c - 1e-9;
+    if (!err && !bad && conv && !ok) {
+      float t01 = 0.0f;
+      cudaEventElapsedTime(&t01, P->ev[0], P->ev[1]);
+      std::memset(info, 0, sizeof(*info));
+      info->rank = rank;
+      info->seed_iters = iters;
+      info->seed_residual = resid;
+      info->seed_m = P->mp;
+      info->seed_n = P->np;
+      info->seed_rank_raw = rank_raw;
+      info->lambda = P->lam_full;
+      info->rank_ok = 0;
+      info->status = (int32_t)PCP_ERR_RANK_TEST;
+      info->launches = P->launches;
+      info->seed_team = P->seed_team;
+      info->t_seed_ms = t01;
+      info->t_total_ms = t01;
+      P->stopped_after_seed = true;
+      pcp::set_error("rank test failed: seed rank %d for a %dx%d seed",
+                     rank_raw, P->mp, P->np);
+      return PCP_ERR_RANK_TEST;
+    }
+  }
   if (hio) PCP_CUDA(cudaStreamWaitEvent(st, cev[1], 0));  // all of M landed
   // stages 3 and 4: column and row filtering (Algorithm 1), the row filter
   // on the plan's second stream so that both launches share the GPU

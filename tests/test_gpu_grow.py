@@ -77,3 +77,26 @@ def test_growth_with_library_sampling():
     assert st == 0, info
     assert info["seed_m"] >= 50 and rows.size == info["seed_m"]
     assert relerr(L, L0) < TOL and relerr(S, S0) < TOL
+
+
+def test_growth_that_gives_up_still_writes_the_outputs():
+    # A full-rank Gaussian matrix: the first 30 x 30 seed's rank r' fails
+    # Eq. rank_test, and the rule would grow it past half a side, so the
+    # growth gives up.  With growth on, the rank is read before the filters
+    # (a seed that will grow skips them); when the growth gives up, the last
+    # seed is solved in full, so the call reports PCP_ERR_RANK_TEST with the
+    # same outputs as the solve without growth on the same seed.
+    rng = np.random.default_rng(5)
+    M = rng.standard_normal((300, 280))
+    ro, co = rng.permutation(300), rng.permutation(280)
+    st, info, rows, cols, L, S = _solve(M, 3, True, ro, co)
+    assert st == -5, info
+    assert info["seed_m"] == 30 and info["seed_n"] == 30
+    assert info["problems"] == 270 + 250      # the filters ran
+    assert np.isfinite(L).all() and np.isfinite(S).all()
+    st0, info0, rows0, cols0, L0n, S0n = _solve(M, 3, False, ro, co)
+    assert st0 == -5
+    np.testing.assert_array_equal(rows, rows0)
+    assert info0["seed_rank_raw"] == info["seed_rank_raw"]
+    np.testing.assert_array_equal(L, L0n)
+    np.testing.assert_array_equal(S, S0n)
