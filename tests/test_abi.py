@@ -86,6 +86,35 @@ def test_stage_entry_points_validate_sizes(lib):
     assert st == _abi.PCP_ERR_ARG
 
 
+def test_seed_entry_point_limits(lib):
+    # the seed stage's size limits are refused before any device work: sides
+    # in [2, 512], kmax even, <= 64 and <= the short side (+1 when it is
+    # odd), k0 even in [2, kmax]; a valid shape with null buffers is refused
+    # too
+    from paper_1108_5359_gb300 import _abi
+
+    def call(mp, np_, k0, kmax):
+        return lib.pcp_seed_pcp(None, mp, np_, 0.0, 1e-7, 1.5, 1.25, 1e7,
+                                10, k0, kmax, 1e-6, 0, None, None, None,
+                                None, None, None, None, None)
+
+    for mp, np_, k0, kmax, what in [(513, 100, 8, 8, "outside"),
+                                    (100, 513, 8, 8, "outside"),
+                                    (1, 100, 2, 2, "outside"),
+                                    (512, 512, 8, 66, "kmax"),
+                                    (512, 512, 8, 7, "kmax"),
+                                    (512, 7, 8, 10, "kmax"),
+                                    (512, 8, 8, 10, "kmax"),
+                                    (512, 512, 10, 8, "k0"),
+                                    (512, 512, 3, 8, "k0"),
+                                    (512, 512, 60, 64, "null"),
+                                    (512, 7, 8, 8, "null")]:
+        assert call(mp, np_, k0, kmax) == _abi.PCP_ERR_ARG, (mp, np_, kmax)
+        assert what in lib.pcp_last_error().decode()
+    assert lib.pcp_seed_workspace_bytes(512, 512, 64) > 0
+    assert lib.pcp_seed_workspace_bytes(0, 512, 64) == 0
+
+
 def test_batch_and_serve_validate_without_gpu(lib):
     from paper_1108_5359_gb300 import _abi
     assert lib.pcp_l1filter_batch(0, None, None, None) == _abi.PCP_OK
