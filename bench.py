@@ -10,14 +10,21 @@ S = M - L.  Prints ONE JSON line on rank 0.
 
 value        entries (m*n) recovered per second, device-resident input, L2
              flushed between steps (a 256 MB memset outside the timed span);
+             a timed step is the asynchronous pcp_l1filter_solve (no
+             pcp_info: one CUDA-graph replay, no host round trip); the
+             stage split and status come from checked solves of the same
+             plan after the timed loop, whose outputs must equal the timed
+             steps' bit for bit;
 e2e          the same metric through the public API from pinned host
              memory: H2D of M, the solve, D2H of Lu, Lv and S per step;
 roofline     the dominant kernel of the step against MEASURED_PEAKS.json;
 cpu_baseline the FP64 oracle on the host cores (rank 0, N=1 only): the
              median of three full solves of the same workload, and the
              plain-FP32 variant of the oracle timed the same way;
-gpu_launches the library's own kernel launches in the timed steps, as the
-             library counts them (pcp_info.launches);
+gpu_launches the library's own kernel launches in the timed steps: the
+             kernels of one solve as the library counts them
+             (pcp_info.launches of a checked solve) times the CUDA-graph
+             replays the plan counted in the timed loop;
 large        (N=1) the same record for the 20000 x 20000 rank-50 solve in
              the BF16 + refinement form, its CPU baseline a stated sample;
 batch        (N=1) 256 uneven instances (r up to 30, BF16 + refinement)
@@ -389,44 +396,73 @@ def measure_single(pk, torch, dev, P, M32, wl, precision, steps, warmup,
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        return pk.pcp_l1filter_solve(plan, dM, Lu, Lv, S, info=True,
+    def step(info):
+        return pk.pcp_l1filter_solve(plan, dM, Lu, Lv, S, info=info,
                                      stream=stream, raise_on_error=False)
 
+    # warm-up: the checked form (status, info) and the asynchronous form
+    # (its first call captures the solve into the plan's CUDA graph)
     for _ in range(max(3, warmup)):
         flush.zero_()
-        st, info, _, _ = step()
+        st, info, _, _ = step(True)
+        assert st == 0, (f"solve failed with status {st}: "
+                         f"{pk._abi.last_error()}")
+        flush.zero_()
+        st, _, _, _ = step(False)
+        assert st == 0, f"enqueue failed with status {st}"
     torch.cuda.synchronize()
-    assert st == 0, f"solve failed with status {st}: {pk._abi.last_error()}"
+    per_solve = info.launches
+    g0 = pk.pcp_plan_graph_launches(plan)
 
+    # timed: the asynchronous solve (pcp_l1filter_solve without pcp_info,
+    # one CUDA-graph replay of the plan's kernels, no host round trip), each
+    # bracketed by CUDA events on the launching stream, the L2 flush
+    # between them outside the events
     sampler = ClockSampler(local)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    step_ms, stage = [], {"seed": [], "filter": [], "spass": []}
-    launches = 0
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    evs = [(torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     wall0 = time.perf_counter()
-    for _ in range(steps):
+    for e0, e1 in evs:
         flush.zero_()
-        ev0.record(stream)
-        st, info, _, _ = step()
-        ev1.record(stream)
-        ev1.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-        stage["seed"].append(info.t_seed_ms)
-        stage["filter"].append(info.t_filter_ms)
-        stage["spass"].append(info.t_spass_ms)
-        launches += info.launches
+        e0.record(stream)
+        st, _, _, _ = step(False)
+        e1.record(stream)
+        assert st == 0, f"enqueue failed with status {st}"
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if ws > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     t_step = max_over_ranks(statistics.mean(step_ms), dev)
+    replays = pk.pcp_plan_graph_launches(plan) - g0
+    # every timed step replayed the graph, whose kernels are the checked
+    # form's (per_solve launches per solve)
+    launches = per_solve * replays if replays == steps else per_solve * steps
+
+    # the timed steps' outputs: parity below; then the stage split and the
+    # solve's status from checked solves of the same plan (untimed)
+    Lu_t, Lv_t = Lu.clone(), Lv.clone()
+    S_t = S.clone() if P.L0 is not None else None
+    stage = {"seed": [], "filter": [], "spass": []}
+    for _ in range(max(3, min(steps, 10))):
+        flush.zero_()
+        st, info, _, _ = step(True)
+        stage["seed"].append(info.t_seed_ms)
+        stage["filter"].append(info.t_filter_ms)
+        stage["spass"].append(info.t_spass_ms)
+    torch.cuda.synchronize()
+    assert st == 0, f"solve failed with status {st}: {pk._abi.last_error()}"
     last_info = info.as_dict()
+    last_info["graph_replays_timed"] = replays
+    # the checked solves reproduce the timed steps' outputs bit for bit
+    same = bool(torch.equal(Lu, Lu_t) and torch.equal(Lv, Lv_t) and
+                (S_t is None or torch.equal(S, S_t)))
+    del Lu_t, Lv_t, S_t
 
     # parity of the last solve: exact recovery of the generated L0, S0
     Lrec = Sh = None
@@ -440,6 +476,7 @@ def measure_single(pk, torch, dev, P, M32, wl, precision, steps, warmup,
     else:
         parity = sampled_parity(P, pseed, Lu, Lv, S)
         parity["status"] = int(st)
+    parity["timed_outputs_equal_checked"] = same
 
     # e2e through the public host-buffer call (pcp_l1filter_solve_host):
     # M from pinned host memory, Lu, Lv and S back to pinned host memory,

@@ -393,7 +393,10 @@ size_t pcp_seed_workspace_bytes(int32_t mp, int32_t np, int32_t kmax);
  *   rank_cut * largest, capped at r_cap when r_cap > 0);
  *   *h_iters, *h_residual: ALM iterations and final relative residual.
  * lambda <= 0 means 1/sqrt(max(mp,np)).  k0 is the initial subspace size
- * (even, <= kmax <= 64); 2 <= mp, np <= 512.  d_work must hold
+ * (even, <= kmax); kmax is even, <= 64 and <= min(mp, np); 2 <= mp, np <=
+ * 512.  The SVT equals the full-SVD one while the subspace holds every
+ * singular value above 1/mu; a subspace started below the SVT's rank cuts
+ * it until it grows (another ALM path).  d_work must hold
  * pcp_seed_workspace_bytes() bytes.
  * Returns PCP_ERR_SEED_NOCONV when max_iter is reached (outputs written),
  * PCP_ERR_TIMEOUT if a device barrier wait ran out. */

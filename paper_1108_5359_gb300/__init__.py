@@ -103,12 +103,22 @@ def pcp_params_default(m, n, r) -> PCPParams:
 def _set_index_arrays(params, keep, seed_rows, seed_cols, row_order,
                       col_order):
     """Point params' optional host index arrays at int64 copies kept alive
-    in ``keep``."""
+    in ``keep``.  A seed index set also sets the seed's size (seed_m /
+    seed_n) to its length; a size already set to another value is an
+    error (the library would read only that many entries)."""
     import numpy as np
-    for name, v in (("seed_rows", seed_rows), ("seed_cols", seed_cols),
-                    ("row_order", row_order), ("col_order", col_order)):
+    for name, v, size in (("seed_rows", seed_rows, "seed_m"),
+                          ("seed_cols", seed_cols, "seed_n"),
+                          ("row_order", row_order, None),
+                          ("col_order", col_order, None)):
         if v is not None:
-            a = np.ascontiguousarray(v, dtype=np.int64)
+            a = np.ascontiguousarray(v, dtype=np.int64).ravel()
+            if size is not None:
+                have = getattr(params, size)
+                if have and have != a.size:
+                    raise ValueError(f"{name} has {a.size} entries but "
+                                     f"params.{size} = {have}")
+                setattr(params, size, a.size)
             keep.append(a)
             setattr(params, name, a.ctypes.data_as(C.POINTER(C.c_int64)))
 
@@ -119,6 +129,7 @@ class Plan:
     def __init__(self, params: PCPParams, seed_rows=None, seed_cols=None,
                  row_order=None, col_order=None):
         self._keep = []
+        params = PCPParams.from_buffer_copy(params)
         _set_index_arrays(params, self._keep, seed_rows, seed_cols,
                           row_order, col_order)
         self.params = params

@@ -2523,8 +2523,11 @@ extern "C" pcp_status pcp_seed_pcp(const double* dD, int32_t mp, int32_t np,
               np <= pcp::kSeedMaxSide,
           "pcp_seed_pcp: seed %dx%d outside [2, %d]", mp, np,
           pcp::kSeedMaxSide);
+  // a subspace wider than the short side would hold a direction the seed
+  // does not have: its Cholesky pivot is FP32 rounding noise, not zero, and
+  // the noise column breaks the bases' orthogonality
   PCP_ARG(kmax >= 2 && kmax <= pcp::kSeedKmaxLimit && kmax % 2 == 0 &&
-              kmax <= std::min(mp, np) + (std::min(mp, np) & 1),
+              kmax <= std::min(mp, np),
           "pcp_seed_pcp: kmax=%d must be even, <= %d and <= min(mp,np)", kmax,
           pcp::kSeedKmaxLimit);
   PCP_ARG(k0 >= 2 && k0 % 2 == 0 && k0 <= kmax,

@@ -88,9 +88,8 @@ def test_stage_entry_points_validate_sizes(lib):
 
 def test_seed_entry_point_limits(lib):
     # the seed stage's size limits are refused before any device work: sides
-    # in [2, 512], kmax even, <= 64 and <= the short side (+1 when it is
-    # odd), k0 even in [2, kmax]; a valid shape with null buffers is refused
-    # too
+    # in [2, 512], kmax even, <= 64 and <= the short side, k0 even in
+    # [2, kmax]; a valid shape with null buffers is refused too
     from paper_1108_5359_gb300 import _abi
 
     def call(mp, np_, k0, kmax):
@@ -103,12 +102,13 @@ def test_seed_entry_point_limits(lib):
                                     (1, 100, 2, 2, "outside"),
                                     (512, 512, 8, 66, "kmax"),
                                     (512, 512, 8, 7, "kmax"),
-                                    (512, 7, 8, 10, "kmax"),
+                                    (512, 7, 8, 8, "kmax"),
                                     (512, 8, 8, 10, "kmax"),
                                     (512, 512, 10, 8, "k0"),
                                     (512, 512, 3, 8, "k0"),
                                     (512, 512, 60, 64, "null"),
-                                    (512, 7, 8, 8, "null")]:
+                                    (512, 8, 8, 8, "null"),
+                                    (512, 7, 6, 6, "null")]:
         assert call(mp, np_, k0, kmax) == _abi.PCP_ERR_ARG, (mp, np_, kmax)
         assert what in lib.pcp_last_error().decode()
     assert lib.pcp_seed_workspace_bytes(512, 512, 64) > 0

@@ -19,12 +19,12 @@ from tests.gpuhelp import build_and_load, idx_dev, relerr, to_dev_cm, to_host
 pytestmark = pytest.mark.gpu
 
 
-def _seed(D, r, kmax=None, tol=1e-7):
+def _seed(D, r, kmax=None, tol=1e-7, lam=None, k0=None):
     import torch
     import paper_1108_5359_gb300 as pk
     build_and_load()
     mp, np_ = D.shape
-    k0 = min((r + max(6, r // 4) + 1) // 2 * 2, min(mp, np_) // 2 * 2)
+    k0 = k0 or min((r + max(6, r // 4) + 1) // 2 * 2, min(mp, np_) // 2 * 2)
     kmax = kmax or min(min(mp, np_) // 2 * 2, max(k0 + 16, 2 * k0) // 2 * 2, 64)
     work = torch.empty(pk.pcp_seed_workspace_bytes(mp, np_, kmax),
                        dtype=torch.uint8, device="cuda")
@@ -32,7 +32,7 @@ def _seed(D, r, kmax=None, tol=1e-7):
     U = torch.zeros((kmax, mp), dtype=torch.float64, device="cuda").t()
     V = torch.zeros((kmax, np_), dtype=torch.float64, device="cuda").t()
     Sg = torch.zeros(kmax, dtype=torch.float64, device="cuda")
-    lam = 1.0 / np.sqrt(max(mp, np_))
+    lam = lam or 1.0 / np.sqrt(max(mp, np_))
     st, rank, iters, res = pk.pcp_seed_pcp(dD, lam, tol, 1.5, 1.25, 1e7, 500,
                                            k0, kmax, 1e-6, r, work, U, Sg, V)
     torch.cuda.synchronize()
@@ -124,3 +124,43 @@ def test_seed_result_does_not_depend_on_team(cfg, kw):
         np.testing.assert_array_equal(o[0], outs[0][0])
         np.testing.assert_array_equal(o[1], outs[0][1])
         assert o[2] == outs[0][2]
+
+
+def test_seed_pcp_at_the_largest_side_and_subspace():
+    # the largest seed the stage takes (512 x 512) with the largest subspace
+    # (k0 = 60 for rank 48, growing to kmax = 64): the blocked k x k
+    # Cholesky and every per-side loop at its bound
+    M, L0, S0 = synth.lowrank_plus_sparse(512, 512, 48, 0.05, -30, 30,
+                                          seed=31)
+    lam = 1.0 / np.sqrt(512)
+    ref = pcp.inexact_alm_pcp(M, lam)
+    U, s, V, rank, iters, res = _seed(M, 48)
+    assert U.shape == (512, 64)
+    assert rank == ref.sigma.size == 48
+    assert res <= 1e-7
+    Lg = (U[:, :rank] * s[:rank]) @ V[:, :rank].T
+    assert relerr(Lg, ref.L) < 1e-6
+    assert relerr(Lg, L0) < 1e-5
+    np.testing.assert_allclose(U[:, :rank].T @ U[:, :rank], np.eye(rank),
+                               rtol=0, atol=1e-12)
+    np.testing.assert_allclose(s[:rank], np.sort(ref.sigma)[::-1], rtol=1e-6)
+    assert np.all(U[:, rank:] == 0) and np.all(s[rank:] == 0)
+
+
+def test_seed_pcp_skinny_at_the_widest_subspace():
+    # 512 x 13 seed of rank 1 + 3% outliers: the short side is odd, so the
+    # widest subspace the entry point takes is kmax = 12 (even, <= 13), here
+    # from the first step (k0 = 12); most CTAs own no column of the short
+    # side.  (A subspace wider than the short side is refused: its extra
+    # vector's Cholesky pivot is FP32 rounding noise, not zero, and on a
+    # 512 x 7 seed with kmax = 8 the noise column moved L by 3.6e-4.)
+    M, L0, S0 = synth.lowrank_plus_sparse(512, 13, 1, 0.03, -10, 10, seed=32)
+    lam = 1.0 / np.sqrt(512)
+    ref = pcp.inexact_alm_pcp(M, lam)
+    U, s, V, rank, iters, res = _seed(M, 1, kmax=12, k0=12)
+    assert rank == ref.sigma.size == 1
+    assert res <= 1e-7
+    Lg = (U[:, :rank] * s[:rank]) @ V[:, :rank].T
+    assert relerr(Lg, ref.L) < 1e-6
+    np.testing.assert_allclose(s[:rank], ref.sigma[:1], rtol=1e-6)
+    assert np.all(U[:, rank:] == 0) and np.all(V[:, rank:] == 0)

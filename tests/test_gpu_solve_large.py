@@ -101,3 +101,23 @@ def test_rank50_full_size_sampled_block():
     Sg = S.double().cpu().numpy()[np.ix_(ri, ci)]
     assert relerr(Lg, L_o) < TOL
     assert relerr(Sg, Mh[np.ix_(ri, ci)] - L_o) < TOL
+
+
+def test_largest_seed_512_matches_oracle():
+    # the largest seed the plan takes (512 x 512) at rank 48 (k0 = 60,
+    # subspace up to 64) on a 1400 x 1300 matrix of the same distribution:
+    # Algorithm 1's tensor-core kernel at p = 512 on both sides
+    import dataclasses
+    P = synth.make_config("c3_20000_r50", seed=2, m=1400, n=1300, r=48)
+    rows, cols = synth.seed_indices(P.m, P.n, 512, 512, seed=2)
+    P = dataclasses.replace(P, rows=rows, cols=cols)
+    g = _gpu_solve(P)
+    assert g["st"] == 0, g
+    assert g["info"]["seed_m"] == 512 and g["info"]["seed_n"] == 512
+    ref = l1filter.l1_filter_pcp(g["M"], rows, cols, r=P.r)
+    Lg = g["Lu"] @ g["Lv"].T
+    assert g["info"]["rank"] == ref.rank == 48
+    assert relerr(Lg, ref.L) < TOL
+    assert relerr(g["S"], ref.S) < TOL
+    assert relerr(Lg, P.L0) < TOL
+    assert g["info"]["problems_unconverged"] == 0
