@@ -148,19 +148,23 @@ def test_seed_pcp_at_the_largest_side_and_subspace():
 
 
 def test_seed_pcp_skinny_at_the_widest_subspace():
-    # 512 x 13 seed of rank 1 + 3% outliers: the short side is odd, so the
-    # widest subspace the entry point takes is kmax = 12 (even, <= 13), here
-    # from the first step (k0 = 12); most CTAs own no column of the short
-    # side.  (A subspace wider than the short side is refused: its extra
-    # vector's Cholesky pivot is FP32 rounding noise, not zero, and on a
-    # 512 x 7 seed with kmax = 8 the noise column moved L by 3.6e-4.)
-    M, L0, S0 = synth.lowrank_plus_sparse(512, 13, 1, 0.03, -10, 10, seed=32)
+    # 512 x 41 seed of rank 2 + 3% outliers (exactly recovered by PCP): the
+    # short side is odd, so the widest subspace the entry point takes is
+    # kmax = 40 (even, <= 41), here from the first step (k0 = 40); most CTAs
+    # own no column of the short side.  (A subspace wider than the short
+    # side is refused: its extra vector's Cholesky pivot is FP32 rounding
+    # noise, not zero, and on a 512 x 7 seed with kmax = 8 the noise column
+    # moved L by 3.6e-4.)
+    M, L0, S0 = synth.lowrank_plus_sparse(512, 41, 2, 0.03, -10, 10, seed=32)
     lam = 1.0 / np.sqrt(512)
     ref = pcp.inexact_alm_pcp(M, lam)
-    U, s, V, rank, iters, res = _seed(M, 1, kmax=12, k0=12)
-    assert rank == ref.sigma.size == 1
+    U, s, V, rank, iters, res = _seed(M, 2, kmax=40, k0=40)
+    assert rank == ref.sigma.size == 2
     assert res <= 1e-7
     Lg = (U[:, :rank] * s[:rank]) @ V[:, :rank].T
     assert relerr(Lg, ref.L) < 1e-6
-    np.testing.assert_allclose(s[:rank], ref.sigma[:1], rtol=1e-6)
+    assert relerr(Lg, L0) < 1e-6
+    np.testing.assert_allclose(s[:rank], np.sort(ref.sigma)[::-1], rtol=1e-6)
+    np.testing.assert_allclose(V[:, :rank].T @ V[:, :rank], np.eye(rank),
+                               rtol=0, atol=1e-12)
     assert np.all(U[:, rank:] == 0) and np.all(V[:, rank:] == 0)
