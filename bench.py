@@ -76,6 +76,8 @@ TRAFFIC = {
     ("c3_20000_r50", "spass", "spass_tc_kernel"): (
         2895202000, "profiles/spass_tc_kernel_c2_5000_r20.md: 8000^2 capture "
         "(463.2 MB) scaled by the entry count (x 6.25)"),
+    ("c2_5000_r20", "seed", "seed_alm_kernel"): (
+        1119488, "profiles/seed_alm_kernel_c2_5000_r20.md (988.4 + 131.1 KB)"),
     # Algorithm 1: both launches of one solve (column and row filter)
     ("c2_5000_r20", "filter", "adm_tc_kernel"): (
         72495872, "profiles/adm_tc_kernel_c2_5000_r20.md"),
