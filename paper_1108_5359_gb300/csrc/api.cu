@@ -486,7 +486,7 @@ static pcp_status grow_loop(pcp_plan* P, const float* dM, int64_t ldm,
 // second with the same buffers is captured on the plan's capture stream and
 // instantiated, and later calls with the same buffers replay the graph on
 // the caller's stream.  A solve that cannot be captured (an index upload
-// that has to synchronise, or anything the driver refuses to capture) runs
+// that has to synchronise, or anything the CUDA driver refuses to capture) runs
 // directly and turns graphs off for the plan.
 template <typename Run>
 static pcp_status solve_async(pcp_plan* P, std::vector<uintptr_t> key,

@@ -160,7 +160,7 @@ def test_async_solves_replay_a_graph_with_the_same_results():
 
 def test_pageable_host_buffers_give_the_same_results():
     # pageable memory: the seed cannot read M in place and the copies are
-    # synchronous for the host; whether the driver captures them into the
+    # synchronous for the host; whether the CUDA driver captures them into the
     # graph (replays) or not (graphs off, -1), the results are the same
     import torch
     import paper_1108_5359_gb300 as pk
