@@ -2470,7 +2470,9 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
   // One CTA per SM, or one per column/row task (max(m', n')) when there are
   // fewer: a sweep on the 200 x 200 seed measured 3.58 ms at 152 CTAs
   // against 3.92 ms at 200 (48 SMs doubled up) and 3.9 ms at 304, and the
-  // 500 x 500 seed 11.0 ms at 152 against 11.1 ms at 304.  `ctas` > 0 asks
+  // 500 x 500 seed 11.0 ms at 152 against 11.1 ms at 304; with the current
+  // phases, 2.60 ms at 152 against 2.66-2.73 ms at 76-144 (200 x 200) and
+  // 7.24 ms against 7.58-9.55 ms (500 x 500).  `ctas` > 0 asks
   // for that many instead (within the co-resident limit of a cooperative
   // launch).  The partial-sum slots are fixed (kSeedGridSlots), so the
   // result does not depend on the grid size.
