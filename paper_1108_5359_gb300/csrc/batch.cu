@@ -89,16 +89,48 @@ struct SummaryTask {
   const int32_t* iters;
   int64_t nprob;
   const int32_t* bad;
+  int32_t* skip;      // written by batch_gate_kernel
+  int mp, np;         // seed size
+  int64_t m, n;
+  double s_r, s_c;
+  int gate;           // grow_seed on and the caller grows failed seeds
 };
+
+// Section 3.5 on the device, before the filters: an instance whose seed
+// failed Eq. rank_test and will grow to (s_r r') x (s_c r') skips its
+// filters (the same test and grown size as the host's, so the host grows
+// exactly the skipped instances; it runs again without the gate any
+// skipped instance it does not grow).
+__global__ void batch_gate_kernel(const SummaryTask* __restrict__ tasks,
+                                  int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const SummaryTask t = tasks[i];
+  int skip = 0;
+  if (t.gate) {
+    const int rr = t.ctl->rank_raw;
+    const bool rank_ok = rr >= 1 && (double)t.mp / rr >= t.s_r - 1e-9 &&
+                         (double)t.np / rr >= t.s_c - 1e-9;
+    if (t.ctl->converged && *t.bad == 0 && !rank_ok && rr >= 1) {
+      const long long gm = max((long long)t.mp, llround(t.s_r * rr));
+      const long long gn = max((long long)t.np, llround(t.s_c * rr));
+      skip = !(gm == t.mp && gn == t.np) && 2 * gm <= t.m && 2 * gn <= t.n &&
+             gm <= 512 && gn <= 512;
+    }
+  }
+  *t.skip = skip;
+}
 
 // Per-instance diagnostics reduced on the device, so that batch_finish
 // reads the whole batch with one copy.
 __global__ void batch_summary_kernel(const SummaryTask* __restrict__ tasks,
                                      BatchSummary* __restrict__ out) {
   const SummaryTask t = tasks[blockIdx.x];
+  const int skipped = *t.skip;
+  const int64_t nprob = skipped ? 0 : t.nprob;  // no filter ran
   int imax = 0;
   long long unconv = 0, isum = 0;
-  for (int64_t j = threadIdx.x; j < t.nprob; j += blockDim.x) {
+  for (int64_t j = threadIdx.x; j < nprob; j += blockDim.x) {
     const int v = t.iters[j];
     imax = max(imax, v < 0 ? -v : v);
     unconv += (v < 0);
@@ -134,6 +166,7 @@ __global__ void batch_summary_kernel(const SummaryTask* __restrict__ tasks,
     r.rank_raw = t.ctl->rank_raw;
     r.residual = t.ctl->residual;
     r.bad = *t.bad;
+    r.skipped = skipped;
     out[blockIdx.x] = r;
   }
 }
@@ -240,12 +273,13 @@ size_t batch_footprint(const pcp_problem& pr, const BatchInstance& bi) {
   b += align256(seed_workspace_bytes_cta(bi.mp, bi.np, bi.kmax));
   b += align256(sizeof(double) * (bi.mp + bi.np + 1) * bi.kmax); // U, S, V
   b += align256(sizeof(float) * ((bi.mp + bi.np) * q.r + q.r));  // FP32 copies
-  b += align256(sizeof(int32_t) * (nrb + ncb + 1));              // iters, bad
+  b += align256(sizeof(int32_t) * (nrb + ncb + 2));  // iters, bad, skip
   return b + 8192;  // share of the batch-wide argument blocks
 }
 
 pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
-                        BatchHandle* h, bool timed) {
+                        BatchHandle* h, bool timed,
+                        const unsigned char* grow_gate) {
   PCP_ARG(count >= 1 && count <= 65535,
           "batch: count %d outside [1, 65535]", count);
   h->count = count;
@@ -286,6 +320,7 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
     o_it[i] = take(sizeof(int32_t) * ((q.m - b.mp) + (q.n - b.np)));
   }
   const size_t o_bad = take(sizeof(int32_t) * count);
+  const size_t o_skip = take(sizeof(int32_t) * count);
   const size_t o_seeds = take(sizeof(int32_t) * (size_t)seed_total);
   const size_t o_ctask = take(sizeof(ComplementTask) * count);
   const size_t o_sargs = take(seed_batched_args_bytes(count));
@@ -427,6 +462,8 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
                                 q.filter_rho, q.beta0_scale,
                                 q.beta_bar_ratio, q.filter_max_iter,
                                 q.precision, q.lowp_iters};
+    sets[2 * i].skip = reinterpret_cast<const int32_t*>(base + o_skip) + i;
+    sets[2 * i + 1].skip = sets[2 * i].skip;
   }
   // host blocks for the argument copies must outlive the async copies; the
   // handle keeps them
@@ -440,7 +477,10 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
     const pcp_params& q = probs[i].params;
     const BatchInstance& b = h->inst[i];
     stask[i] = SummaryTask{seed_ctl_ptr_cta(b.d_work, b.mp, b.np, b.kmax),
-                           b.d_iters, (q.m - b.mp) + (q.n - b.np), b.d_bad};
+                           b.d_iters, (q.m - b.mp) + (q.n - b.np), b.d_bad,
+                           reinterpret_cast<int32_t*>(base + o_skip) + i,
+                           b.mp, b.np, q.m, q.n, q.s_r, q.s_c,
+                           (q.grow_seed && grow_gate && grow_gate[i]) ? 1 : 0};
   }
   h->d_summary = reinterpret_cast<BatchSummary*>(base + o_sum);
   pcp_status s;
@@ -487,6 +527,9 @@ pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
   if ((s = assemble_batched_async(asmb.data(), count, h->h_asm.data(),
                                   base + o_asm, st, false)) != PCP_OK)
     return s;
+  batch_gate_kernel<<<(count + 255) / 256, 256, 0, st>>>(
+      reinterpret_cast<const SummaryTask*>(base + o_stask), count);
+  PCP_CUDA(cudaGetLastError());
   if (timed) PCP_CUDA(cudaEventRecord(h->ev[1], st));
   nvtx.next("pcp.batch.filter");
   if ((s = l1_filter_batched_async(sets.data(), 2 * count, h->h_filt.data(),
@@ -522,6 +565,7 @@ pcp_status batch_finish(BatchHandle* h, pcp_info* infos, cudaStream_t st,
       for (int q = 0; q < 3; ++q)
         cudaEventElapsedTime(&stage_ms[q], h->ev[q], h->ev[q + 1]);
     h->status.clear();
+    h->skipped.assign(h->count, 0);
     for (int i = 0; i < h->count; ++i) {
       const pcp_params& q = h->probs[i].params;
       const BatchInstance& b = h->inst[i];
@@ -555,6 +599,7 @@ pcp_status batch_finish(BatchHandle* h, pcp_info* infos, cudaStream_t st,
       else if (!inf.rank_ok) si = PCP_ERR_RANK_TEST;
       else if (u.unconverged) si = PCP_ERR_FILTER_NOCONV;
       inf.status = (int32_t)si;
+      h->skipped[i] = u.skipped ? 1 : 0;
       if (si != PCP_OK && first == PCP_OK) {
         first = si;
         set_error("batch instance %d: status %d (rank %d, raw %d, iters %d)",
@@ -577,21 +622,24 @@ pcp_status batch_finish(BatchHandle* h, pcp_info* infos, cudaStream_t st,
 
 }  // namespace pcp
 
-extern "C" pcp_status pcp_l1filter_batch(int32_t count,
-                                         const pcp_problem* probs,
-                                         pcp_info* infos, void* stream) {
-  PCP_ARG(count >= 0, "pcp_l1filter_batch: count < 0");
-  if (count == 0) return PCP_OK;
-  PCP_ARG(probs, "pcp_l1filter_batch: null problems");
-  cudaStream_t st = (cudaStream_t)stream;
+namespace {
+
+// One round of the batched solve: launch, wait, and fill one pcp_info per
+// instance; with gate, instances whose seed fails Eq. rank_test and will
+// grow skip their filters (h->skipped marks them).
+pcp_status batch_round(int count, const pcp_problem* probs, pcp_info* infos,
+                       cudaStream_t st, bool gate, std::vector<char>* skipped,
+                       float* total_ms) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (infos) {
     PCP_CUDA(cudaEventCreate(&e0));
     PCP_CUDA(cudaEventCreate(&e1));
     PCP_CUDA(cudaEventRecord(e0, st));
   }
+  std::vector<unsigned char> g(gate ? count : 0, 1);
   pcp::BatchHandle h;
-  pcp_status s = pcp::batch_launch(count, probs, st, &h, infos != nullptr);
+  pcp_status s = pcp::batch_launch(count, probs, st, &h, infos != nullptr,
+                                   gate ? g.data() : nullptr);
   if (s != PCP_OK) {
     if (h.d_base) cudaFreeAsync(h.d_base, st);
     for (cudaEvent_t e : h.ev)
@@ -609,53 +657,90 @@ extern "C" pcp_status pcp_l1filter_batch(int32_t count,
     cudaEventDestroy(e1);
   }
   s = pcp::batch_finish(&h, infos, st, ms);
-  if (!infos) return s;
+  if (skipped) *skipped = h.skipped;
+  if (total_ms) *total_ms = ms;
+  return s;
+}
+
+}  // namespace
+
+extern "C" pcp_status pcp_l1filter_batch(int32_t count,
+                                         const pcp_problem* probs,
+                                         pcp_info* infos, void* stream) {
+  PCP_ARG(count >= 0, "pcp_l1filter_batch: count < 0");
+  if (count == 0) return PCP_OK;
+  PCP_ARG(probs, "pcp_l1filter_batch: null problems");
+  cudaStream_t st = (cudaStream_t)stream;
+  // Without infos nothing grows (Section 3.5 needs the seed's rank), so the
+  // filters are never gated off.
+  if (!infos)
+    return batch_round(count, probs, nullptr, st, false, nullptr, nullptr);
   // Section 3.5 for the instances that ask for it: a seed failing Eq.
   // rank_test grows to (s_r r') x (s_c r') along the same orders, and the
   // grown instances run again as one batch, until none is left to grow.
+  // Each round gates off the filters of the seeds that are about to grow.
+  std::vector<pcp_problem> cur(probs, probs + count);
   std::vector<std::vector<int64_t>> orders(2 * (size_t)count);
-  for (int round = 0; round < 16; ++round) {
-    std::vector<int> idx;
+  std::vector<int> act(count);
+  std::iota(act.begin(), act.end(), 0);
+  for (int round = 0; round < 17 && !act.empty(); ++round) {
     std::vector<pcp_problem> g;
-    for (int i = 0; i < count; ++i) {
-      const pcp_params& q = probs[i].params;
+    for (int i : act) g.push_back(cur[i]);
+    std::vector<pcp_info> gi(g.size());
+    std::vector<char> skipped;
+    // the last round grows nothing more, so its filters all run
+    const bool gate = round < 16;
+    pcp_status s = batch_round((int)g.size(), g.data(), gi.data(), st, gate,
+                               &skipped, nullptr);
+    if (s == PCP_ERR_ARG || s == PCP_ERR_CUDA || s == PCP_ERR_NOMEM ||
+        s == PCP_ERR_UNSUPPORTED)
+      return s;
+    std::vector<int> next, redo;
+    for (size_t u = 0; u < act.size(); ++u) {
+      const int i = act[u];
+      if (round > 0) gi[u].t_total_ms += infos[i].t_total_ms;
+      infos[i] = gi[u];
+      const pcp_params& q = cur[i].params;
       int gm = 0, gn = 0;
-      if (!q.grow_seed || infos[i].status != PCP_ERR_RANK_TEST ||
-          !pcp::grown_seed_size(q, infos[i], &gm, &gn))
+      const bool grows = q.grow_seed &&
+                         infos[i].status == PCP_ERR_RANK_TEST &&
+                         pcp::grown_seed_size(q, infos[i], &gm, &gn);
+      if (!grows) {
+        // a skipped instance the host does not grow runs again in full
+        if (u < skipped.size() && skipped[u]) redo.push_back(i);
         continue;
+      }
       if (orders[2 * i].empty()) {
-        orders[2 * i] = q.row_order
-                            ? std::vector<int64_t>(q.row_order, q.row_order + q.m)
-                            : pcp::sample_order(q.m, q.rng_seed);
+        orders[2 * i] =
+            q.row_order ? std::vector<int64_t>(q.row_order, q.row_order + q.m)
+                        : pcp::sample_order(q.m, q.rng_seed);
         orders[2 * i + 1] =
             q.col_order ? std::vector<int64_t>(q.col_order, q.col_order + q.n)
                         : pcp::sample_order(q.n, q.rng_seed ^ 0xC01C01C0ull);
       }
-      pcp_problem pr = probs[i];
-      pr.params.seed_m = gm;
-      pr.params.seed_n = gn;
-      pr.params.row_order = orders[2 * i].data();
-      pr.params.col_order = orders[2 * i + 1].data();
-      idx.push_back(i);
-      g.push_back(pr);
+      cur[i].params.seed_m = gm;
+      cur[i].params.seed_n = gn;
+      cur[i].params.row_order = orders[2 * i].data();
+      cur[i].params.col_order = orders[2 * i + 1].data();
+      next.push_back(i);
     }
-    if (g.empty()) break;
-    std::vector<pcp_info> gi(g.size());
-    pcp::BatchHandle h2;
-    s = pcp::batch_launch((int)g.size(), g.data(), st, &h2, true);
-    if (s != PCP_OK) {
-      if (h2.d_base) cudaFreeAsync(h2.d_base, st);
-      for (cudaEvent_t e : h2.ev)
-        if (e) cudaEventDestroy(e);
-      return s;
+    if (!redo.empty()) {
+      std::vector<pcp_problem> rp;
+      for (int i : redo) rp.push_back(cur[i]);
+      std::vector<pcp_info> ri(rp.size());
+      s = batch_round((int)rp.size(), rp.data(), ri.data(), st, false,
+                      nullptr, nullptr);
+      if (s == PCP_ERR_ARG || s == PCP_ERR_CUDA || s == PCP_ERR_NOMEM ||
+          s == PCP_ERR_UNSUPPORTED)
+        return s;
+      for (size_t u = 0; u < redo.size(); ++u) {
+        ri[u].t_total_ms += infos[redo[u]].t_total_ms;
+        infos[redo[u]] = ri[u];
+      }
     }
-    pcp::batch_finish(&h2, gi.data(), st, 0.0f);
-    for (size_t u = 0; u < idx.size(); ++u) {
-      gi[u].t_total_ms += infos[idx[u]].t_total_ms;
-      infos[idx[u]] = gi[u];
-    }
+    act.swap(next);
   }
-  s = PCP_OK;
+  pcp_status s = PCP_OK;
   for (int i = 0; i < count && s == PCP_OK; ++i)
     s = (pcp_status)infos[i].status;
   return s;

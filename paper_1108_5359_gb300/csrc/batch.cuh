@@ -25,6 +25,7 @@ struct BatchSummary {
   int rank, iters, converged, rank_raw, bad, iters_max;
   long long unconverged, iters_sum;
   double residual;
+  int skipped;  // filters skipped: the seed failed Eq. rank_test and grows
 };
 
 struct BatchHandle {
@@ -39,6 +40,7 @@ struct BatchHandle {
   // the launch is timed
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<pcp_status> status;
+  std::vector<char> skipped;  // per instance, from the summary
   // a batch plan's workspace: size_only asks batch_launch for the bytes
   // alone (no device work); prealloc uses d_base / bytes as given (never
   // freed by batch_finish); indices_ready skips the index uploads (already
@@ -55,9 +57,15 @@ bool grown_seed_size(const pcp_params& q, const pcp_info& inf, int* gm,
 // Device workspace one instance needs (its share of a batch).
 size_t batch_footprint(const pcp_problem& pr, const BatchInstance& bi);
 // Enqueue the whole batch on st (asynchronous; allocates with
-// cudaMallocAsync on st).
+// cudaMallocAsync on st).  grow_gate (per instance, may be null): the
+// caller grows a seed that fails Eq. rank_test (Section 3.5), so an
+// instance with grow_seed whose seed fails the test and has a grown size
+// skips its filters on the device (its outputs are left unwritten; the
+// summary marks it skipped, and a skipped instance the caller then does not
+// grow must be run again without the gate).
 pcp_status batch_launch(int count, const pcp_problem* probs, cudaStream_t st,
-                        BatchHandle* h, bool timed = false);
+                        BatchHandle* h, bool timed = false,
+                        const unsigned char* grow_gate = nullptr);
 // With infos: synchronise st, fill one pcp_info (and h->status) per
 // instance.  Always releases the workspace (stream-ordered).
 pcp_status batch_finish(BatchHandle* h, pcp_info* infos, cudaStream_t st,

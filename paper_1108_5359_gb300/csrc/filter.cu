@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     adm_f32_batched_kernel(const FilterArgs* __restrict__ sets,
                            const int32_t* __restrict__ tiles) {
   const FilterArgs a = sets[tiles[2 * blockIdx.x]];
+  if (a.skip != nullptr && *a.skip != 0) return;  // whole CTA, one set
   adm_f32_tile<SPT, RMAX>(a, tiles[2 * blockIdx.x + 1]);
 }
 
@@ -377,6 +378,7 @@ pcp_status l1_filter_batched_async(const FilterSet* sets, int nsets,
     a.lowp_iters = refined ? f.lowp_iters : 0;
     a.lowp_bf16 = f.precision == PCP_BF16_REFINED;
     a.iters_out = f.iters_out;
+    a.skip = f.skip;
     std::memcpy(ha + i, &a, sizeof(a));
     const int cls = simt ? shape_class(f.p, f.r)
                          : kSimtClasses + tc_shape_class(f.p, f.r);
@@ -458,6 +460,7 @@ extern "C" pcp_status pcp_l1_filter(
   if (N == 0) return PCP_OK;
   PCP_ARG(dM && d_pidx && d_qidx && dA && dZ, "pcp_l1_filter: null pointer");
   pcp::FilterArgs a;
+  a.skip = nullptr;
   a.M = dM;
   a.pidx = d_pidx;
   a.p = p;

@@ -552,6 +552,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<RB, NT>())
     adm_tc_batched_kernel(const FilterArgs* __restrict__ sets,
                           const int32_t* __restrict__ tiles) {
   const FilterArgs a = sets[tiles[2 * blockIdx.x]];
+  if (a.skip != nullptr && *a.skip != 0) return;  // whole CTA, one set
   if (a.lowp_bf16)
     adm_tc_tile<RB, NT, true>(a, tiles[2 * blockIdx.x + 1]);
   else

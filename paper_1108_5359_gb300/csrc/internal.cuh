@@ -88,6 +88,9 @@ struct FilterArgs {
   int lowp_iters;
   int lowp_bf16;  // the low-precision passes use BF16 (else one-pass TF32)
   int32_t* iters_out;
+  // batched form only: the set's problems are skipped when *skip != 0 (an
+  // instance whose seed failed Eq. rank_test and will grow); nullptr: never
+  const int32_t* skip;
 };
 
 // Tensor-core form of Algorithm 1 (filter_tc.cu): 16 problems per CTA,
@@ -123,6 +126,7 @@ struct FilterSet {
   int max_iter;
   int precision;   // pcp_precision
   int lowp_iters;  // PCP_TF32_REFINED
+  const int32_t* skip = nullptr;  // see FilterArgs::skip
 };
 // The FP32 SIMT kernel serves PCP_FP32_SIMT (p <= 256, r <= 32); every
 // other precision runs on the tensor-core kernel.

@@ -43,6 +43,10 @@ struct Request {
   pcp_status status = PCP_OK;
   pcp_info info;
   double t_submit = 0, t_done = 0;
+  // the filters of a seed that fails Eq. rank_test may be skipped on the
+  // device (it grows and comes back); a skipped request that is not
+  // requeued runs once more with this set, filters included
+  bool no_gate = false;
 };
 
 struct Flight {
@@ -50,6 +54,7 @@ struct Flight {
   int stream_slot = -1;
   cudaEvent_t start = nullptr, done = nullptr;
   std::vector<uint64_t> tickets;
+  std::vector<unsigned char> gate;  // per request: growth follows a failure
   size_t bytes = 0;
 };
 
@@ -82,8 +87,8 @@ void launch_group(pcp_server* S, Flight* f, std::vector<pcp_problem>& probs) {
   cudaEventCreate(&f->start);
   cudaEventCreate(&f->done);
   cudaEventRecord(f->start, st);
-  pcp_status s =
-      pcp::batch_launch((int)probs.size(), probs.data(), st, &f->h, true);
+  pcp_status s = pcp::batch_launch((int)probs.size(), probs.data(), st,
+                                   &f->h, true, f->gate.data());
   cudaEventRecord(f->done, st);
   if (s != PCP_OK) {
     // mark the whole group failed; the workspace (if any) is released when
@@ -133,25 +138,37 @@ void finish_group(pcp_server* S, Flight* f) {
     }
     // Section 3.5: a seed failing Eq. rank_test grows and the request goes
     // back to the head of the queue
-    pcp_params& q = r.prob.params;
+    const pcp_params& q = r.prob.params;
     int gm = 0, gn = 0;
     if (q.grow_seed && r.status == PCP_ERR_RANK_TEST &&
         pcp::grown_seed_size(q, r.info, &gm, &gn)) {
       if (r.rorder.empty()) r.rorder = pcp::sample_order(q.m, q.rng_seed);
       if (r.corder.empty())
         r.corder = pcp::sample_order(q.n, q.rng_seed ^ 0xC01C01C0ull);
-      q.seed_m = gm;
-      q.seed_n = gn;
-      q.row_order = r.rorder.data();
-      q.col_order = r.corder.data();
+      pcp_problem grown = r.prob;
+      grown.params.seed_m = gm;
+      grown.params.seed_n = gn;
+      grown.params.row_order = r.rorder.data();
+      grown.params.col_order = r.corder.data();
       pcp::BatchInstance bi;
-      if (pcp::batch_validate(r.prob, &bi) == PCP_OK) {
+      if (pcp::batch_validate(grown, &bi) == PCP_OK) {
+        r.prob = grown;
         r.bytes = pcp::batch_footprint(r.prob, bi);
         r.status = PCP_OK;
         r.state = kQueued;
         requeue.push_back(f->tickets[i]);
         continue;
       }
+    }
+    if (launch_status == PCP_OK && i < f->h.skipped.size() &&
+        f->h.skipped[i] && !r.no_gate) {
+      // its filters were skipped but it does not grow: run it again in full
+      // (the seed size is unchanged, so the footprint is too)
+      r.no_gate = true;
+      r.status = PCP_OK;
+      r.state = kQueued;
+      requeue.push_back(f->tickets[i]);
+      continue;
     }
     r.t_done = t;
     r.info.t_total_ms = (float)(t - r.t_submit);
@@ -206,6 +223,7 @@ void scheduler(pcp_server* S) {
         S->used_slots += 1;
         nf->bytes += r.bytes;
         nf->tickets.push_back(ticket);
+        nf->gate.push_back(r.no_gate ? 0 : 1);
         probs.push_back(r.prob);
       }
       if (probs.empty()) {

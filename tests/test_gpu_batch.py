@@ -275,3 +275,63 @@ def test_more_seeds_than_resident_ctas_bitwise():
         if ref.rank != P.r:
             continue
         assert relerr(_L(mix[i]), ref.L) < TOL, i
+
+
+def _grow_batch(M, r, grow, row_order=None, col_order=None, rows=None,
+                cols=None):
+    import torch
+    import paper_1108_5359_gb300 as pk
+    build_and_load()
+    m, n = M.shape
+    dM = to_dev_cm(M.astype(np.float32))
+    Lu = pk.colmajor(m, r, fill=0.0)
+    Lv = pk.colmajor(n, r, fill=0.0)
+    S = pk.colmajor(m, n, fill=0.0)
+    p = pk.pcp_params_default(m, n, r)
+    p.grow_seed = 1 if grow else 0
+    if rows is not None:
+        q = pk.problem(p, dM, Lu, Lv, S, rows, cols)
+    else:
+        q = pk.problem(p, dM, Lu, Lv, S, row_order=row_order,
+                       col_order=col_order)
+    st, infos = pk.pcp_l1filter_batch([q], raise_on_error=False)
+    torch.cuda.synchronize()
+    return st, infos[0].as_dict(), to_host(Lu), to_host(Lv), to_host(S)
+
+
+def test_growing_seed_skips_its_first_filters_and_matches_the_grown_batch():
+    # Section 3.5 in the batched form: the 50 x 50 seed fails Eq. rank_test
+    # and will grow, so its filters are skipped on the device; the grown
+    # round's outputs equal, bit for bit, a batch started at the grown seed
+    from tests.test_gpu_grow import _instance
+    M, L0, S0, ro, co = _instance(0)
+    st, info, Lu, Lv, S = _grow_batch(M, 5, True, ro, co)
+    assert st == 0 and info["seed_m"] > 50 and info["rank"] == 5
+    assert info["problems"] == (600 - info["seed_m"]) + (560 - info["seed_n"])
+    rows = np.sort(ro[:info["seed_m"]])
+    cols = np.sort(co[:info["seed_n"]])
+    st2, info2, Lu2, Lv2, S2 = _grow_batch(M, 5, False, rows=rows, cols=cols)
+    assert st2 == 0 and info2["seed_iters"] == info["seed_iters"]
+    np.testing.assert_array_equal(Lu, Lu2)
+    np.testing.assert_array_equal(Lv, Lv2)
+    np.testing.assert_array_equal(S, S2)
+    assert relerr(Lu.astype(np.float64) @ Lv.astype(np.float64).T, L0) < TOL
+
+
+def test_batch_growth_that_gives_up_still_writes_the_outputs():
+    # a full-rank Gaussian matrix: the 30 x 30 seed fails Eq. rank_test and
+    # the grown seed would pass half a side, so the growth gives up and the
+    # device must not skip the filters: PCP_ERR_RANK_TEST with the same
+    # outputs, bit for bit, as the batch without growth
+    rng = np.random.default_rng(5)
+    M = rng.standard_normal((300, 280))
+    ro, co = rng.permutation(300), rng.permutation(280)
+    st, info, Lu, Lv, S = _grow_batch(M, 3, True, ro, co)
+    assert st == -5 and info["seed_m"] == 30
+    assert info["problems"] == 270 + 250
+    st0, info0, Lu0, Lv0, S0 = _grow_batch(M, 3, False, ro, co)
+    assert st0 == -5
+    assert np.isfinite(Lu).all() and np.isfinite(S).all()
+    np.testing.assert_array_equal(Lu, Lu0)
+    np.testing.assert_array_equal(Lv, Lv0)
+    np.testing.assert_array_equal(S, S0)

@@ -152,3 +152,34 @@ def test_served_request_grows_its_seed():
     assert st == 0 and inf.seed_m > 50 and inf.rank == 5
     L = to_host(Lu) @ to_host(Lv).T
     assert relerr(L, L0) < TOL
+
+
+def test_served_growth_that_gives_up_still_writes_the_outputs():
+    # the growth of a full-rank Gaussian matrix's 30 x 30 seed gives up
+    # (Section 3.5): the served request ends with PCP_ERR_RANK_TEST and the
+    # outputs a batch of one without growth writes, bit for bit
+    import torch
+    import paper_1108_5359_gb300 as pk
+    build_and_load()
+    rng = np.random.default_rng(5)
+    M = rng.standard_normal((300, 280))
+    ro, co = rng.permutation(300), rng.permutation(280)
+    outs = []
+    for grow in (True, False):
+        dM = to_dev_cm(M.astype(np.float32))
+        bufs = (pk.colmajor(300, 3, fill=0.0), pk.colmajor(280, 3, fill=0.0),
+                pk.colmajor(300, 280, fill=0.0))
+        p = pk.pcp_params_default(300, 280, 3)
+        p.grow_seed = 1 if grow else 0
+        q = pk.problem(p, dM, *bufs, row_order=ro, col_order=co)
+        if grow:
+            srv = pk.Server(hbm_budget_bytes=1 << 30, max_slots=4, streams=2)
+            st, inf = srv.wait(srv.submit(q))
+            srv.close()
+        else:
+            st, infs = pk.pcp_l1filter_batch([q], raise_on_error=False)
+            torch.cuda.synchronize()
+        assert st == -5
+        outs.append(_host(bufs))
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
