@@ -2100,13 +2100,21 @@ __global__ void __launch_bounds__(kSeedThreads, 1)
 __global__ void __launch_bounds__(kSeedThreads, 2)
     seed_alm_team_kernel(const SeedArgs* __restrict__ args,
                          const int4* __restrict__ team,
-                         const int* __restrict__ lists) {
+                         int* __restrict__ lists) {
   const int4 t = team[blockIdx.x];
   if (t.z == 1) {
-    // a list of seeds solved one after another by this CTA alone
-    for (int q = 0; q < t.w; ++q) {
-      if (q > 0) __syncthreads();
-      seed_alm_body<kTeamCta>(args[lists[t.x + q]], 0, 1);
+    // the CTAs without a team take seeds one at a time, each alone, from
+    // one queue in decreasing order of predicted cost (lists[0]: the next
+    // entry, lists[1]: the length, then the seeds): a seed that runs longer
+    // than predicted holds one CTA while the others take the rest
+    __shared__ int s_q;
+    for (int round = 0;; ++round) {
+      if (round > 0) __syncthreads();  // the previous seed is done
+      if (threadIdx.x == 0) s_q = atomicAdd(lists, 1);
+      __syncthreads();
+      const int q = s_q;
+      if (q >= lists[1]) break;
+      seed_alm_body<kTeamCta>(args[lists[2 + q]], 0, 1);
     }
   } else {
     seed_alm_body<kTeamGrid>(args[t.x], t.y, t.z);
@@ -2114,9 +2122,10 @@ __global__ void __launch_bounds__(kSeedThreads, 2)
 }
 
 // Control blocks start at zero (barrier counters included) before any team
-// member runs.
+// member runs; so does the list queue's next-entry counter.
 __global__ void seed_ctl_zero_kernel(const SeedArgs* __restrict__ args,
-                                     int count) {
+                                     int count, int* queue) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *queue = 0;
   for (int i = blockIdx.x; i < count; i += gridDim.x) {
     int* c = reinterpret_cast<int*>(args[i].ctl);
     for (int w = threadIdx.x; w < (int)(sizeof(SeedCtl) / 4); w += blockDim.x)
@@ -2193,7 +2202,7 @@ size_t seed_args_bytes() { return sizeof(SeedArgs); }
 size_t seed_batched_args_bytes(int count) {
   return seed_args_bytes() * (size_t)count +
          sizeof(int4) * ((size_t)count + kMaxCoopBlocks) +
-         sizeof(int) * (size_t)count;
+         sizeof(int) * ((size_t)count + 2);
 }
 
 SeedCtl* seed_ctl_ptr_cta(void* d_work, int mp, int np, int kmax) {
@@ -2332,7 +2341,10 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
     nlist = n;
   }
   // block table after the argument blocks: team CTAs {seed, rank, size, 0},
-  // then list CTAs {list offset, 0, 1, length}; the lists follow the table
+  // then one entry {0, 0, 1, 0} per list CTA; the list queue follows the
+  // table: the next-entry counter (zeroed before each launch), the number
+  // of list seeds, and the list seeds, largest predicted cost first.  The
+  // plan above sizes the lists; on the device the list CTAs share them.
   int4* tab = reinterpret_cast<int4*>(hb + seed_args_bytes() * (size_t)count);
   int nblocks = 0;
   for (int i : by_c)
@@ -2348,14 +2360,14 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   for (const auto& l : lists) nused += !l.empty();
   int* lst = reinterpret_cast<int*>(tab + nblocks + nused);
   int off = 0;
-  for (const auto& l : lists) {
-    if (l.empty()) continue;
-    tab[nblocks++] = make_int4(off, 0, 1, (int)l.size());
-    for (int i : l) lst[off++] = i;
-  }
+  for (int b = 0; b < nused; ++b) tab[nblocks++] = make_int4(0, 0, 1, 0);
+  lst[0] = 0;
+  for (int i : by_c)
+    if (nb[i] == 1) lst[2 + off++] = i;
+  lst[1] = off;
   const size_t used_bytes = seed_args_bytes() * (size_t)count +
                             sizeof(int4) * (size_t)nblocks +
-                            sizeof(int) * (size_t)off;
+                            sizeof(int) * (size_t)(off + 2);
   if (used_bytes > seed_batched_args_bytes(count)) {
     set_error("batched seed: schedule of %d CTAs does not fit its block",
               nblocks);
@@ -2368,8 +2380,9 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   const SeedArgs* d_a = static_cast<const SeedArgs*>(d_args);
   const int4* d_tab = reinterpret_cast<const int4*>(
       static_cast<char*>(d_args) + seed_args_bytes() * (size_t)count);
-  const int* d_lst = reinterpret_cast<const int*>(d_tab + nblocks);
-  seed_ctl_zero_kernel<<<std::min(count, 1024), 64, 0, st>>>(d_a, count);
+  int* d_lst = const_cast<int*>(reinterpret_cast<const int*>(d_tab + nblocks));
+  seed_ctl_zero_kernel<<<std::min(count, 1024), 64, 0, st>>>(d_a, count,
+                                                              d_lst);
   PCP_CUDA(cudaGetLastError());
   if (coop_launch) {
     void* kargs[] = {(void*)&d_a, (void*)&d_tab, (void*)&d_lst};
