@@ -84,6 +84,14 @@ constexpr unsigned long long kSeedDefaultWaitNs = 2000000000ull;  // 2 s
 // 500 x 500 seed 11.19 / 10.63 / 11.80 ms; every slot costs each CTA a
 // k-vector read in the Ritz-value reduction).
 constexpr int kSeedGridSlots = 152;
+// A seed with fewer rows and columns than slots gets one slot per row (or
+// column) instead: a slot holds at least one row, and a small seed's CTAs
+// (one per row) each walk one slot per phase instead of several empty ones.
+// A function of the seed's size alone, so the result still does not depend
+// on the team.
+inline int seed_slots(int mp, int np, int cap) {
+  return std::max(1, std::min(cap, std::max(mp, np)));
+}
 
 struct SeedLayout {
   size_t ctl, part, colsq, S, Y, G, Gt, Om, P, Pt, T, Psi, PsiT, Gam, Gam2,
@@ -2170,7 +2178,7 @@ void fill_seed_args(SeedArgs& a, const SeedLayout& L, char* w,
   a.r_cap = r_cap;
   a.timeout_ns = timeout_ns > 0 ? timeout_ns : kSeedDefaultWaitNs;
   a.lowp_res = kSeedLowpRes;
-  a.nv = kSeedTeamMax;
+  a.nv = seed_slots(mp, np, kSeedTeamMax);
   a.ctl = reinterpret_cast<SeedCtl*>(w + L.ctl);
   a.part = reinterpret_cast<double*>(w + L.part);
   a.colsq = reinterpret_cast<double*>(w + L.colsq);
@@ -2466,7 +2474,7 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
     set_error("seed PCP: kernel does not fit on an SM (smem %zu)", smem);
     return PCP_ERR_UNSUPPORTED;
   }
-  a.nv = kSeedGridSlots;
+  a.nv = seed_slots(mp, np, kSeedGridSlots);
   PCP_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(SeedCtl), st));
   // One thread-block cluster of `ctas` CTAs (1 .. kSeedClusterMax) when
   // asked for and the device can hold it; the same slots, so the same bits.
