@@ -189,3 +189,25 @@ def test_table_written_by_the_tuning_run_is_well_formed():
     rows = re.findall(r"\{\s*([12])\s*,\s*([12])\s*,\s*([12])\s*,\s*([12])\s*\}",
                       text)
     assert len(rows) == 3
+
+
+def test_binding_sizes_the_seed_from_its_index_arrays(lib):
+    # a seed index set sets seed_m / seed_n to its length (the library reads
+    # that many entries); a size already set to another value is refused;
+    # the order arrays of seed growth do not size the seed
+    import numpy as np
+    import paper_1108_5359_gb300 as pk
+    p = pk.pcp_params_default(1000, 900, 5)
+    assert p.seed_m == 0 and p.seed_n == 0
+    keep = []
+    pk._set_index_arrays(p, keep, np.arange(64), np.arange(0, 120, 2),
+                         None, None)
+    assert (p.seed_m, p.seed_n) == (64, 60)
+    assert p.seed_rows[63] == 63 and p.seed_cols[59] == 118
+    q = pk.pcp_params_default(1000, 900, 5)
+    q.seed_m = 50
+    with pytest.raises(ValueError):
+        pk._set_index_arrays(q, [], np.arange(64), None, None, None)
+    g = pk.pcp_params_default(1000, 900, 5)
+    pk._set_index_arrays(g, [], None, None, np.arange(1000), np.arange(900))
+    assert (g.seed_m, g.seed_n) == (0, 0)
