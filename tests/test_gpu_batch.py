@@ -335,3 +335,47 @@ def test_batch_growth_that_gives_up_still_writes_the_outputs():
     np.testing.assert_array_equal(Lu, Lu0)
     np.testing.assert_array_equal(Lv, Lv0)
     np.testing.assert_array_equal(S, S0)
+
+
+def test_gated_growing_and_giving_up_instances_in_one_batch():
+    # one batch holding a seed that grows (its first filters gated off on
+    # the device), a seed whose growth gives up (filters kept) and a plain
+    # instance: each instance's outputs equal its batch of one, bit for bit
+    import torch
+    import paper_1108_5359_gb300 as pk
+    from tests.test_gpu_grow import _instance
+    build_and_load()
+    M1, _, _, ro1, co1 = _instance(0)
+    rng = np.random.default_rng(5)
+    M2 = rng.standard_normal((300, 280))
+    ro2, co2 = rng.permutation(300), rng.permutation(280)
+    P3 = synth.make_config("c1_500_r5", seed=3)
+    specs = [(M1, 5, dict(row_order=ro1, col_order=co1), True),
+             (M2, 3, dict(row_order=ro2, col_order=co2), True),
+             (P3.M, 5, dict(seed_rows=P3.rows, seed_cols=P3.cols), False)]
+
+    def make(spec):
+        M, r, idx, grow = spec
+        m, n = M.shape
+        dM = to_dev_cm(M.astype(np.float32))
+        bufs = (pk.colmajor(m, r, fill=0.0), pk.colmajor(n, r, fill=0.0),
+                pk.colmajor(m, n, fill=0.0))
+        p = pk.pcp_params_default(m, n, r)
+        p.grow_seed = 1 if grow else 0
+        return pk.problem(p, dM, *bufs, **idx), bufs, dM
+
+    made = [make(sp) for sp in specs]
+    st, infos = pk.pcp_l1filter_batch([q for q, _, _ in made],
+                                      raise_on_error=False)
+    torch.cuda.synchronize()
+    mix = [[to_host(b) for b in bufs] for _, bufs, _ in made]
+    assert [i.status for i in infos] == [0, -5, 0]
+    assert infos[0].seed_m > 50 and infos[1].seed_m == 30
+    for k, sp in enumerate(specs):
+        q, bufs, _ = make(sp)
+        st1, inf1 = pk.pcp_l1filter_batch([q], raise_on_error=False)
+        torch.cuda.synchronize()
+        assert inf1[0].status == infos[k].status
+        assert inf1[0].seed_m == infos[k].seed_m
+        for got, want in zip(mix[k], bufs):
+            np.testing.assert_array_equal(got, to_host(want))
