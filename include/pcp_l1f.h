@@ -136,8 +136,10 @@ typedef struct pcp_params {
                                device cannot hold it), more = a cooperative
                                grid of that many CTAs (software grid barrier,
                                up to the co-resident limit), 0 = the
-                               library's choice.  The result does not depend
-                               on it (fixed partial-sum slots). */
+                               library's choice (a cluster of 16 for seeds
+                               up to 64 x 64, else the grid).  The result
+                               does not depend on it (fixed partial-sum
+                               slots). */
   int64_t wait_timeout_ns;  /* limit of each bounded device wait of the seed
                                stage (its grid barrier), in ns; <= 0 means
                                2 s.  A wait that runs out ends the seed

@@ -2476,6 +2476,12 @@ pcp_status seed_pcp_async(const double* dD, int mp, int np, double lam,
   }
   a.nv = seed_slots(mp, np, kSeedGridSlots);
   PCP_CUDA(cudaMemsetAsync(a.ctl, 0, sizeof(SeedCtl), st));
+  // The library's choice for a seed of at most 64 rows and columns is one
+  // cluster of 16 CTAs: its phases are barrier-latency bound, and the
+  // hardware cluster barrier beats the grid's (20 x 20: 1.38 against 1.50
+  // ms on its grid of 20 CTAs, 30 x 30: 1.92 / 2.05, 50 x 50: 1.69 / 1.75,
+  // 60 x 60: 1.56 / 1.58); larger seeds need the FP64 pipes of every SM.
+  if (ctas == 0 && std::max(mp, np) <= 64) ctas = kSeedClusterMax;
   // One thread-block cluster of `ctas` CTAs (1 .. kSeedClusterMax) when
   // asked for and the device can hold it; the same slots, so the same bits.
   if (ctas >= 1 && ctas <= kSeedClusterMax) {
