@@ -111,12 +111,9 @@ __global__ void batch_gate_kernel(const SummaryTask* __restrict__ tasks,
     const int rr = t.ctl->rank_raw;
     const bool rank_ok = rr >= 1 && (double)t.mp / rr >= t.s_r - 1e-9 &&
                          (double)t.np / rr >= t.s_c - 1e-9;
-    if (t.ctl->converged && *t.bad == 0 && !rank_ok && rr >= 1) {
-      const long long gm = max((long long)t.mp, llround(t.s_r * rr));
-      const long long gn = max((long long)t.np, llround(t.s_c * rr));
-      skip = !(gm == t.mp && gn == t.np) && 2 * gm <= t.m && 2 * gn <= t.n &&
-             gm <= 512 && gn <= 512;
-    }
+    int gm = 0, gn = 0;
+    if (t.ctl->converged && *t.bad == 0 && !rank_ok)
+      skip = grown_seed_dims(rr, t.mp, t.np, t.m, t.n, t.s_r, t.s_c, &gm, &gn);
   }
   *t.skip = skip;
 }
@@ -188,12 +185,8 @@ std::vector<int64_t> sample_order(int64_t n, uint64_t seed) {
 
 bool grown_seed_size(const pcp_params& q, const pcp_info& inf, int* gm,
                      int* gn) {
-  const int rr = inf.seed_rank_raw;
-  *gm = std::max((int)inf.seed_m, (int)std::llround(q.s_r * rr));
-  *gn = std::max((int)inf.seed_n, (int)std::llround(q.s_c * rr));
-  return rr >= 1 && !(*gm == inf.seed_m && *gn == inf.seed_n) &&
-         2 * (int64_t)*gm <= q.m && 2 * (int64_t)*gn <= q.n && *gm <= 512 &&
-         *gn <= 512;
+  return grown_seed_dims(inf.seed_rank_raw, (int)inf.seed_m, (int)inf.seed_n,
+                         q.m, q.n, q.s_r, q.s_c, gm, gn);
 }
 
 pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi) {

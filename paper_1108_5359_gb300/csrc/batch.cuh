@@ -2,6 +2,7 @@
 // pcp_l1filter_batch and the serving loop.
 #pragma once
 
+#include <cmath>
 #include <vector>
 
 #include "common.cuh"
@@ -47,6 +48,22 @@ struct BatchHandle {
   // on the device, e.g. while the launches are captured into a graph)
   bool size_only = false, prealloc = false, indices_ready = false;
 };
+
+// Section 3.5's grown seed: for a seed of mp x np whose raw rank rr failed
+// Eq. rank_test, the next seed is (s_r rr) x (s_c rr) (never smaller than
+// the current one); false when there is nothing to grow to, or the grown
+// seed would pass half a side or 512.  One definition for the host's
+// growth loop and the device's filter gate, so both decide alike.
+__host__ __device__ inline bool grown_seed_dims(int rr, int mp, int np,
+                                                int64_t m, int64_t n,
+                                                double s_r, double s_c,
+                                                int* gm, int* gn) {
+  const long long a = llround(s_r * rr), b = llround(s_c * rr);
+  *gm = a > mp ? (int)a : mp;
+  *gn = b > np ? (int)b : np;
+  return rr >= 1 && !(*gm == mp && *gn == np) && 2 * (int64_t)*gm <= m &&
+         2 * (int64_t)*gn <= n && *gm <= 512 && *gn <= 512;
+}
 
 pcp_status batch_validate(const pcp_problem& pr, BatchInstance* bi);
 // Section 3.5: the whole sampling order behind the library's seed sample,
