@@ -271,20 +271,25 @@ void pcp_plan_destroy(pcp_plan* plan);
 
 /* Batched form of Algorithm 2 (Section 3.2: the column and row problems of
  * every instance are independent): `count` independent instances of any
- * sizes, each stage one launch over all of them (batched gather; one CTA per
- * seed PCP, so the seeds run side by side; batched factor assembly; one
- * Algorithm 1 launch per kernel shape over every instance's column and row
- * problems), then the S pass per instance.  Every parameter is per
- * instance, and an instance's result does not depend on the other
- * instances of the batch.  The seed PCP here runs on one CTA per instance,
- * so its rounding differs from pcp_l1filter_solve's (whole-GPU seed) by
- * reduction order only.  Workspace is stream-ordered (cudaMallocAsync /
+ * sizes, each stage one launch over all of them (batched gather; all seed
+ * PCPs in one launch, side by side: a large seed on a team of CTAs, the
+ * others one CTA each; batched factor assembly; one Algorithm 1 launch per
+ * kernel shape over every instance's column and row problems), then the S
+ * pass per instance.  Every parameter is per instance, and an instance's
+ * result does not depend on the other instances of the batch (a seed sums
+ * its partials in the same fixed slots on any team); its rounding differs
+ * from pcp_l1filter_solve's (whole-GPU seed, more slots) by reduction
+ * order only.  Workspace is stream-ordered (cudaMallocAsync /
  * cudaFreeAsync on `stream`); the caller's buffers must stay valid until
  * the stream reaches the end of the batch.  With infos (count entries) the
  * call synchronises and fills one pcp_info per instance, including its
- * status; the return value is then the first non-OK status.  Without infos
- * the call is asynchronous.  Limits: count <= 65535, r <= 64, seeds up to
- * 512 x 512; violations give PCP_ERR_ARG before any device work. */
+ * status; the return value is then the first non-OK status.  With infos,
+ * an instance with grow_seed whose seed fails Eq. rank_test grows (Section
+ * 3.5) and runs again, until none grows; its first round's filters are
+ * skipped on the device, so only the last round writes its outputs.
+ * Without infos the call is asynchronous and nothing grows.  Limits: count
+ * <= 65535, r <= 64, seeds up to 512 x 512; violations give PCP_ERR_ARG
+ * before any device work. */
 pcp_status pcp_l1filter_batch(int32_t count, const pcp_problem* probs,
                               pcp_info* infos, void* stream);
 
