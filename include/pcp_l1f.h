@@ -335,9 +335,12 @@ void pcp_batch_plan_destroy(pcp_batch_plan* plan);
  * group instead of waiting for the device to drain.  A request whose
  * workspace alone exceeds the budget completes with PCP_ERR_NOMEM.  The
  * result of a request does not depend on which other requests share its
- * group.  The caller's buffers (pcp_problem pointers) must stay valid and
- * untouched until the request completes; the optional seed index arrays
- * are copied at submission.
+ * group.  A request with grow_seed whose seed fails Eq. rank_test (its
+ * filters skipped on the device) goes back to the head of the queue with
+ * the grown seed (Section 3.5) and completes when a seed passes or the
+ * growth gives up.  The caller's buffers (pcp_problem pointers) must stay
+ * valid and untouched until the request completes; the optional seed index
+ * arrays are copied at submission.
  * ---------------------------------------------------------------------- */
 typedef struct pcp_server pcp_server;
 
