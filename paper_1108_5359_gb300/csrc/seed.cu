@@ -2263,11 +2263,11 @@ pcp_status seed_pcp_batched_async(const SeedTask* tasks, int count,
   // one-CTA cost is above a target T get the smallest team that brings
   // them under T (at most kSeedTeamMax CTAs, and a quarter of the shorter
   // side), and the other seeds are packed, largest first, onto the
-  // remaining CTAs as lists that a CTA solves one after another; T is
-  // taken from a geometric grid between the balanced load and the largest
-  // seed, minimising the longest CTA.  A seed's result does not depend on
-  // its team or list (fixed reduction slots), so the schedule changes no
-  // bits.
+  // remaining CTAs as lists (the packing sizes the number of list CTAs; on
+  // the device those CTAs share one queue of the list seeds); T is taken
+  // from a geometric grid between the balanced load and the largest seed,
+  // minimising the longest CTA.  A seed's result does not depend on its
+  // team or CTA (fixed reduction slots), so the schedule changes no bits.
   const int n = count;
   std::vector<double> c1(n);
   std::vector<int> cap(n);
