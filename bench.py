@@ -183,8 +183,16 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.path = None
+        self.skip = 0
 
-    def start(self):
+    def _lines(self):
+        with open(self.path) as f:
+            return sum(1 for line in f if line.count(",") >= 8)
+
+    def start(self, wait_s=3.0):
+        """Start sampling every 50 ms and wait (at most wait_s) for the
+        first sample, so that the samples cover the timed region; the rows
+        taken before start() returns are left out."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -195,6 +203,12 @@ class ClockSampler:
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while (time.perf_counter() - t0 < wait_s and self.proc.poll() is None
+               and self._lines() == 0):
+            time.sleep(0.01)
+        self.skip = self._lines()
 
     def stop(self):
         if self.proc is None:
@@ -211,6 +225,8 @@ class ClockSampler:
                 if len(parts) >= 9:
                     rows.append(parts)
         os.unlink(self.path)
+        if len(rows) > self.skip:
+            rows = rows[self.skip:]
         if not rows:
             return None
 

@@ -63,3 +63,34 @@ def test_roofline_arithmetic_of_the_default_line(pk):
     assert out["roofline"]["frac"] == pytest.approx(sd["frac"])
     assert out["roofline"]["traffic"] == 1119488
     assert out["gpu_launches"] == 24
+
+
+def test_clock_sampler_covers_the_timed_region(tmp_path, monkeypatch):
+    # a stand-in nvidia-smi that prints one sample line every 50 ms (the
+    # power cap active): the sampler waits for its first line before the
+    # timed region starts, leaves the lines taken before out, and reports
+    # the median clock, the maximum and the active reasons
+    import os
+    import sys
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text(
+        "#!" + sys.executable + "\n"
+        "import sys, time\n"
+        "i = 0\n"
+        "while True:\n"
+        "    sm = 2070 if i else 1200\n"
+        "    print(f'0, {sm}, 2070, 900.0, Active, Not Active, Not Active, "
+        "Not Active, Active', flush=True)\n"
+        "    i += 1\n"
+        "    time.sleep(0.05)\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep +
+                       os.environ.get("PATH", ""))
+    s = bench.ClockSampler(0)
+    s.start()
+    time.sleep(0.4)
+    out = s.stop()
+    assert out is not None and out["samples"] >= 3
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
